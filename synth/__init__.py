@@ -1,0 +1,120 @@
+"""Seeded synthetic inputs for the HDCR hot path.
+
+This module draws random numbers and arranges them into lattice fields.  It
+holds none of the solver's arithmetic: both the CUDA path and the oracle take
+their inputs from here, and neither side imports the other.
+
+Conventions (shared vocabulary, not method arithmetic):
+
+* A 4d lattice is given as ``L = (Lx, Ly, Lz, Lt)``; arrays are stored with
+  ``t`` slowest and ``x`` fastest, i.e. numpy shape ``(Lt, Lz, Ly, Lx, ...)``.
+* Gauge field ``U``: complex128 array of shape ``(4, Lt, Lz, Ly, Lx, 3, 3)``,
+  ``U[mu, t, z, y, x, a, b]`` is the colour matrix element ``U_mu(x)_{ab}`` of
+  the link leaving site ``x`` in direction ``mu`` (0..3 = x, y, z, t).
+* 5d fermion field ``psi``: complex128 array of shape
+  ``(Lt, Lz, Ly, Lx, Ls, 4, 3)`` (site, fifth coordinate s, spin, colour).
+
+The synthetic links follow the recipe U = exp(i*eps*H) with H a traceless
+Hermitian matrix whose complex entries start as Gaussian (Re, Im ~ N(0,1)),
+which stands in for the dynamical ensemble of the paper's Section 5 (the
+ensemble itself is not available here).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "rng",
+    "gauge_field",
+    "random_su3_field",
+    "gaussian_fermion",
+    "point_sources",
+    "unit_gauge",
+    "lattice_shape",
+]
+
+
+def rng(seed: int) -> np.random.Generator:
+    """numpy PCG64 generator for ``seed``."""
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def lattice_shape(L) -> tuple:
+    """numpy shape (Lt, Lz, Ly, Lx) of a 4d lattice L = (Lx, Ly, Lz, Lt)."""
+    Lx, Ly, Lz, Lt = (int(v) for v in L)
+    return (Lt, Lz, Ly, Lx)
+
+
+def _traceless_hermitian(g: np.random.Generator, n: int) -> np.ndarray:
+    G = g.standard_normal((n, 3, 3)) + 1j * g.standard_normal((n, 3, 3))
+    H = 0.5 * (G + np.conj(np.swapaxes(G, -1, -2)))
+    tr = np.trace(H, axis1=-2, axis2=-1).real / 3.0
+    H = H - tr[:, None, None] * np.eye(3)[None]
+    return H
+
+
+def _expm_i_hermitian(H: np.ndarray, eps: float) -> np.ndarray:
+    """exp(i*eps*H) for a stack of Hermitian 3x3 matrices via eigh."""
+    w, V = np.linalg.eigh(H)
+    ph = np.exp(1j * eps * w)
+    U = np.einsum("nab,nb,ncb->nac", V, ph, np.conj(V))
+    # one polar re-unitarisation step keeps |U^dag U - 1| at rounding level
+    u, _, vh = np.linalg.svd(U)
+    U = u @ vh
+    det = np.linalg.det(U)
+    U = U / (det ** (1.0 / 3.0))[:, None, None]
+    return U
+
+
+def random_su3_field(L, seed: int, eps: float = 1.0, n_links: int | None = None) -> np.ndarray:
+    """A field of SU(3) matrices exp(i*eps*H), one per site (shape (Lt,Lz,Ly,Lx,3,3))."""
+    shp = lattice_shape(L)
+    n = int(np.prod(shp)) if n_links is None else n_links
+    g = rng(seed)
+    U = _expm_i_hermitian(_traceless_hermitian(g, n), eps)
+    return U.reshape(shp + (3, 3))
+
+
+def gauge_field(L, eps: float, seed: int) -> np.ndarray:
+    """Synthetic gauge field U_mu(x) = exp(i*eps*H_mu(x)), H Gaussian traceless Hermitian."""
+    shp = lattice_shape(L)
+    n = 4 * int(np.prod(shp))
+    g = rng(seed)
+    U = _expm_i_hermitian(_traceless_hermitian(g, n), eps)
+    return np.ascontiguousarray(U.reshape((4,) + shp + (3, 3)))
+
+
+def unit_gauge(L) -> np.ndarray:
+    """Free field: every link the identity."""
+    shp = lattice_shape(L)
+    U = np.zeros((4,) + shp + (3, 3), dtype=np.complex128)
+    U[..., 0, 0] = U[..., 1, 1] = U[..., 2, 2] = 1.0
+    return U
+
+
+def gaussian_fermion(L, Ls: int, seed: int, count: int | None = None) -> np.ndarray:
+    """Gaussian complex 5d fermion field(s), Re and Im ~ N(0,1).
+
+    Shape ``(Lt,Lz,Ly,Lx,Ls,4,3)``, or ``(count, Lt,Lz,Ly,Lx,Ls,4,3)`` when
+    ``count`` is given (e.g. the noise vectors that seed the subspace).
+    """
+    shp = lattice_shape(L) + (int(Ls), 4, 3)
+    if count is not None:
+        shp = (int(count),) + shp
+    g = rng(seed)
+    return g.standard_normal(shp) + 1j * g.standard_normal(shp)
+
+
+def point_sources(L, Ls: int, site=(0, 0, 0, 0), s: int = 0) -> np.ndarray:
+    """The 12 spin-colour point sources at 4d site ``site`` = (x,y,z,t), fifth coordinate s.
+
+    Shape ``(12, Lt,Lz,Ly,Lx,Ls,4,3)``; source ``3*spin+colour`` is a unit
+    vector in that spin-colour component.
+    """
+    shp = lattice_shape(L) + (int(Ls), 4, 3)
+    out = np.zeros((12,) + shp, dtype=np.complex128)
+    x, y, z, t = site
+    for sp in range(4):
+        for c in range(3):
+            out[3 * sp + c, t, z, y, x, s, sp, c] = 1.0
+    return out

@@ -1,0 +1,19 @@
+"""Shared pytest configuration.
+
+The ``gpu`` marker selects tests that need a CUDA device and the compiled
+library; everything else runs on the CPU (oracle pins, host logic, ABI
+symbol checks).
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the built libhdcr.so")
+    config.addinivalue_line("markers", "slow: CPU test that takes more than a few seconds")

@@ -1,0 +1,199 @@
+"""Planted mistakes in the oracle (on the CPU) must be caught by a pin.
+
+Each test swaps one piece of the oracle for a plausible wrong version (a
+dropped term, a wrong sign, a wrong index, a transposed operand) and checks
+that the corresponding pin reports a large error, so the pins are shown to
+constrain the oracle rather than just agree with it.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dwf, force, krylov, multigrid as mg
+from pins import (covariance_error, hermiticity_error, p0_det_error,
+                  plane_wave_error, relerr, dense_H_from_stencil)
+
+L4, LS = (4, 4, 2, 6), 4
+
+
+def _cov():
+    U = synth.gauge_field(L4, 0.5, 31)
+    Om = synth.random_su3_field(L4, 32)
+    psi = synth.gaussian_fermion(L4, LS, 33)
+    return covariance_error(dwf, U, Om, psi, 1.8, 0.01, -1)
+
+
+def _herm():
+    U = synth.gauge_field(L4, 0.5, 11)
+    x = synth.gaussian_fermion(L4, LS, 12)
+    y = synth.gaussian_fermion(L4, LS, 13)
+    return hermiticity_error(dwf, U, x, y, 1.8, 0.01, -1)
+
+
+def _pw(bc_t=1):
+    chi = synth.gaussian_fermion((1, 1, 1, 1), LS, 21)[0, 0, 0, 0]
+    return plane_wave_error(dwf, (4, 6, 4, 8), LS, 1.8, 0.03, (1, 0, 2, 3), chi, bc_t)
+
+
+def test_unmutated_oracle_passes_all():
+    assert _cov() < 1e-14 and _herm() < 1e-13 and _pw(1) < 1e-14 and _pw(-1) < 1e-14
+    assert p0_det_error(dwf, 8, 1.8, 0.01) < 1e-10
+
+
+def test_backward_hop_with_wrong_link_is_caught(monkeypatch):
+    orig = dwf.hop
+
+    def bad(U, psi, mu, sign, bc_t):
+        if sign > 0:
+            return orig(U, psi, mu, sign, bc_t)
+        t = dwf.color_mul_dag(U[mu], dwf.shift_fermion(psi, mu, -1, bc_t))   # U(x) not U(x-mu)
+        return dwf.spin_mul(dwf.IDENT4 + dwf.GAMMA[mu], t)
+
+    monkeypatch.setattr(dwf, "hop", bad)
+    assert _cov() > 1e-3
+
+
+def test_missing_dagger_on_backward_link_is_caught(monkeypatch):
+    def bad(U, psi, mu, sign, bc_t):
+        if sign > 0:
+            t = dwf.color_mul(U[mu], dwf.shift_fermion(psi, mu, +1, bc_t))
+            return dwf.spin_mul(dwf.IDENT4 - dwf.GAMMA[mu], t)
+        t = dwf.color_mul(dwf.shift_links(U[mu], mu, -1), dwf.shift_fermion(psi, mu, -1, bc_t))
+        return dwf.spin_mul(dwf.IDENT4 + dwf.GAMMA[mu], t)
+
+    monkeypatch.setattr(dwf, "hop", bad)
+    assert _herm() > 1e-3 or _cov() > 1e-3
+
+
+def test_dropped_half_is_caught(monkeypatch):
+    orig = dwf.hop
+    monkeypatch.setattr(dwf, "hop", lambda U, psi, mu, s, bc: 2.0 * orig(U, psi, mu, s, bc))
+    assert _pw() > 1e-3
+
+
+def test_swapped_wilson_projectors_are_caught(monkeypatch):
+    def bad(U, psi, mu, sign, bc_t):                     # (1 + g) forward, (1 - g) backward
+        if sign > 0:
+            t = dwf.color_mul(U[mu], dwf.shift_fermion(psi, mu, +1, bc_t))
+            return dwf.spin_mul(dwf.IDENT4 + dwf.GAMMA[mu], t)
+        t = dwf.color_mul_dag(dwf.shift_links(U[mu], mu, -1), dwf.shift_fermion(psi, mu, -1, bc_t))
+        return dwf.spin_mul(dwf.IDENT4 - dwf.GAMMA[mu], t)
+
+    monkeypatch.setattr(dwf, "hop", bad)
+    assert _pw() > 1e-3
+
+
+def test_missing_R5_is_caught(monkeypatch):
+    monkeypatch.setattr(dwf, "gamma5_r5", lambda psi: dwf.spin_mul(dwf.GAMMA5, psi))
+    assert _herm() > 1e-3
+
+
+def test_wrong_mf_sign_is_caught(monkeypatch):
+    orig = dwf.d5
+    monkeypatch.setattr(dwf, "d5", lambda psi, mf: orig(psi, -mf))
+    assert p0_det_error(dwf, 8, 1.8, 0.01) > 1e-3
+
+
+def test_missing_antiperiodic_phase_is_caught(monkeypatch):
+    orig = dwf.shift_fermion
+    monkeypatch.setattr(dwf, "shift_fermion", lambda psi, mu, s, bc: orig(psi, mu, s, 1))
+    assert _pw(-1) > 1e-3
+
+
+def test_swapped_coarse_legs_are_caught(monkeypatch):
+    g = mg.Geometry((4, 6, 4, 4), 2, (2, 2, 2, 2))           # coarse extent 3 in y
+    U = synth.gauge_field(g.L, 0.5, 90)
+    noise = synth.gaussian_fermion(g.L, g.Ls, 91, count=2)
+    sub = mg.build_subspace(U, noise, g, 1.8, 0.05, smooth_iters=2)
+    orig = mg.leg_index
+    monkeypatch.setattr(mg, "leg_index", lambda mu, s: orig(mu, -s) if mu == 1 else orig(mu, s))
+    A = mg.coarse_op(U, sub, 1.8, 0.05)
+    monkeypatch.setattr(mg, "leg_index", orig)
+    c = synth.gaussian_fermion((1, 1, 1, 1), 1, 92)[0, 0, 0, 0, 0].ravel()
+    c = np.resize(c, (g.Vc, sub.nvec))
+    lhs = mg.coarse_apply(A, g, c)
+    rhs = mg.restrict(sub, dwf.apply_H(U, mg.prolong(sub, c), 1.8, 0.05))
+    assert relerr(lhs, rhs) > 1e-3
+
+
+def test_single_pass_unnormalised_gram_schmidt_is_caught(monkeypatch):
+    def bad(Phi, rank_tol=1e-12):
+        Phi = Phi.copy()
+        for a in range(Phi.shape[1]):
+            for k in range(Phi.shape[0]):
+                for j in range(k):
+                    Phi[k, a] -= np.vdot(Phi[j, a], Phi[k, a]) * Phi[j, a]
+        return Phi
+
+    monkeypatch.setattr(mg, "block_orthonormalise", bad)
+    g = mg.Geometry((4, 4, 4, 4), 2, (2, 2, 2, 2))
+    vs = mg.chiral_split(synth.gaussian_fermion(g.L, g.Ls, 3, count=2))
+    Phi = mg.basis_from_vectors(g, vs).Phi
+    gram = np.einsum("jak,iak->aji", np.conj(Phi), Phi)
+    assert np.abs(gram - np.eye(4)[None]).max() > 1e-3
+
+
+def test_force_without_dagger_on_second_term_is_caught(monkeypatch):
+    def bad(U, x, w, bc_t=1):
+        F = np.zeros_like(U)
+        for mu in range(4):
+            xf = dwf.shift_fermion(x, mu, +1, bc_t)
+            wf = dwf.shift_fermion(w, mu, +1, bc_t)
+            h = dwf.spin_mul(dwf.IDENT4 - dwf.GAMMA[mu], xf)
+            gq = dwf.spin_mul(dwf.IDENT4 + dwf.GAMMA[mu], x)
+            B = np.einsum("...sib,...sia->...ba", h, np.conj(w))
+            C = np.einsum("...sib,...sia->...ba", gq, np.conj(wf))
+            F[mu] = 0.5 * (B + C)
+        return F
+
+    L, Ls = (2, 2, 2, 2), 4
+    U = synth.gauge_field(L, 0.5, 510)
+    b = synth.gaussian_fermion(L, Ls, 511)
+    eta = synth.gaussian_fermion(L, Ls, 512)
+    Hd = dense_H_from_stencil(dwf, U, Ls, 1.8, 0.05)
+    x = np.linalg.solve(Hd, b.ravel()).reshape(b.shape)
+    y = np.linalg.solve(Hd, eta.ravel()).reshape(b.shape)
+    good = force.gauge_force(U, x, dwf.gamma5_r5(y))
+    monkeypatch.setattr(force, "gauge_force", bad)
+    wrong = force.gauge_force(U, x, dwf.gamma5_r5(y))
+    # the directional derivative along a random Lie-algebra direction differs
+    rng = synth.rng(513)
+    G = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    T = 0.5 * (G + np.conj(np.swapaxes(G, -1, -2)))
+    d_good = np.einsum("...ab,...bc,...ca->...", 1j * T, U, good).sum().real
+    d_bad = np.einsum("...ab,...bc,...ca->...", 1j * T, U, wrong).sum().real
+    assert abs(d_good - d_bad) > 1e-3 * abs(d_good)
+
+
+def test_inverted_cr_beta_is_caught(monkeypatch):
+    """A CR with beta = gamma / gamma' no longer reaches the dense solution."""
+    rng = synth.rng(5)
+    n = 40
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Qm, _ = np.linalg.qr(G)
+    A = (Qm * np.linspace(-3, 4, n)) @ Qm.conj().T
+    b = rng.standard_normal(n) + 0j
+
+    def bad_cr(apply, b, tol=1e-10, maxiter=200):
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        Ar = apply(r)
+        Ap = Ar.copy()
+        gam = np.vdot(r, Ar).real
+        for _ in range(maxiter):
+            al = gam / np.vdot(Ap, Ap).real
+            x = x + al * p
+            r = r - al * Ap
+            Ar = apply(r)
+            gn = np.vdot(r, Ar).real
+            beta = gam / gn
+            gam = gn
+            p = r + beta * p
+            Ap = Ar + beta * Ap
+        return x
+
+    x = bad_cr(lambda v: A @ v, b, maxiter=60)
+    assert relerr(x, np.linalg.solve(A, b)) > 1e-3
+    x_ok, _ = krylov.cr(lambda v: A @ v, b, tol=1e-12, maxiter=400)
+    assert relerr(x_ok, np.linalg.solve(A, b)) < 1e-9
