@@ -159,3 +159,39 @@ def apply_H_hop(U, psi, mu: int, sign: int, bc_t: int = 1) -> np.ndarray:
 def apply_D(U, psi, M5, mf, bc_t=1):
     """Alias of ddwf for readability in tests."""
     return ddwf(U, psi, M5, mf, bc_t)
+
+
+def apply_H_at(U, psi, sites, M5: float, mf: float, bc_t: int = 1) -> np.ndarray:
+    """(H psi)(x, s) at a few 5d sites only, written out term by term.
+
+    ``sites``: iterable of (x, y, z, t, s).  Returns an array (len(sites), 4, 3).
+    Used to check full-size lattices where a whole-field apply is too slow.
+    """
+    _, Lt, Lz, Ly, Lx = U.shape[:5]
+    Ls = psi.shape[-3]
+    ext = (Lx, Ly, Lz, Lt)
+    out = []
+    for (x, y, z, t, s) in sites:
+        sd = Ls - 1 - s                      # H reads D_dwf at the reflected s
+        c = [x, y, z, t]
+
+        def f(cc, ss):
+            return psi[cc[3], cc[2], cc[1], cc[0], ss]
+
+        d = (4.0 - M5) * f(c, sd)
+        for mu in range(4):
+            fw = list(c)
+            fw[mu] = (c[mu] + 1) % ext[mu]
+            bw = list(c)
+            bw[mu] = (c[mu] - 1) % ext[mu]
+            ph_f = bc_t if (mu == 3 and c[3] == Lt - 1) else 1
+            ph_b = bc_t if (mu == 3 and c[3] == 0) else 1
+            Uf = U[mu, c[3], c[2], c[1], c[0]]
+            Ub = U[mu, bw[3], bw[2], bw[1], bw[0]]
+            d = d - 0.5 * ph_f * (IDENT4 - GAMMA[mu]) @ (f(fw, sd) @ Uf.T)
+            d = d - 0.5 * ph_b * (IDENT4 + GAMMA[mu]) @ (f(bw, sd) @ np.conj(Ub))
+        up = f(c, sd + 1) if sd + 1 < Ls else -mf * f(c, 0)
+        dn = f(c, sd - 1) if sd >= 1 else -mf * f(c, Ls - 1)
+        d = d + f(c, sd) - P_MINUS @ up - P_PLUS @ dn
+        out.append(GAMMA5 @ d)
+    return np.array(out)

@@ -1,0 +1,80 @@
+"""ctypes declarations of libhdcr's C ABI (include/hdcr.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+library is loaded from ``paper_1611_06944_gb300/lib/libhdcr.so``; if it is
+missing the import fails with an error that says how to build it (there is no
+CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libhdcr.so")
+
+HDCR_OK = 0
+HDCR_C128 = 0
+HDCR_C64 = 1
+
+STATUS_NAMES = {
+    0: "OK", -1: "BAD_ARG", -2: "BAD_GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE",
+    -5: "RANK_DEFICIENT", -6: "CUDA", -7: "TIMEOUT", -8: "NO_MEMORY",
+}
+
+
+class hdcr_geom(C.Structure):
+    _fields_ = [("L", C.c_int * 4), ("Ls", C.c_int), ("bc_t", C.c_int)]
+
+
+class hdcr_dwf_params(C.Structure):
+    _fields_ = [("M5", C.c_double), ("mf", C.c_double)]
+
+
+class hdcr_solve_stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("iters", C.c_int), ("fine_matvecs", C.c_int),
+        ("fine_matvecs_lo", C.c_int), ("coarse_matvecs", C.c_int), ("restarts", C.c_int),
+        ("true_resid", C.c_double), ("t_total", C.c_double), ("t_smoother", C.c_double),
+        ("t_coarse", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_SZ = C.c_size_t
+_G = C.POINTER(hdcr_geom)
+_DP = C.POINTER(hdcr_dwf_params)
+_ST = C.POINTER(hdcr_solve_stats)
+
+# name -> (restype, argtypes); every symbol declared in include/hdcr.h
+SIGNATURES = {
+    "hdcr_strerror": (C.c_char_p, [_I]),
+    "hdcr_last_error": (C.c_char_p, []),
+    "hdcr_version": (_I, []),
+    "hdcr_apply_g5dwf": (_I, [_G, _DP, _P, _P, _P, _I, _I, _P]),
+    "hdcr_apply_gamma5_r5": (_I, [_G, _P, _P, _I, _I, _P]),
+    "hdcr_fermion_to_planes": (_I, [_G, _P, _P, _I, _I, _P]),
+    "hdcr_fermion_from_planes": (_I, [_G, _P, _P, _I, _I, _P]),
+    "hdcr_convert": (_I, [_P, _I, _P, _I, _SZ, _P]),
+    "hdcr_cdot": (_I, [_P, _P, _SZ, _I, _P, _P]),
+    "hdcr_norm2": (_I, [_P, _SZ, _I, _P, _P]),
+    "hdcr_cr_solve": (_I, [_G, _DP, _P, _P, _P, _I, _D, _I, _ST, _P]),
+}
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"libhdcr.so not found at {path}; build it with "
+            "`python -m paper_1611_06944_gb300.build` (needs nvcc). There is no CPU fallback.")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib

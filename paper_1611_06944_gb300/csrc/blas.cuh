@@ -1,0 +1,22 @@
+// Host-side declarations of the kernel launchers shared between translation units.
+#pragma once
+
+#include "reduce.cuh"
+
+namespace hdcr {
+
+template <typename R>
+int launch_g5dwf(const Geom& g, double M5, double mf, const void* U, const void* in, void* out,
+                 int nrhs, cudaStream_t st);
+template <typename R>
+int launch_gamma5_r5(const Geom& g, const void* in, void* out, int nfields, cudaStream_t st);
+int launch_convert(const void* in, int idt, void* out, int odt, long long n, cudaStream_t st);
+
+template <typename R>
+int launch_cdot(const void* u, const void* v, long long n, RedScratch rs, double* result, cudaStream_t st);
+template <typename R>
+int launch_norm2(const void* u, long long n, RedScratch rs, double* result, cudaStream_t st);
+
+int device_red_scratch(RedScratch* out);
+
+}  // namespace hdcr

@@ -1,0 +1,371 @@
+// Conjugate residual on H = Gamma5 D_dwf (Section 3):
+//
+//   r = b - H x,  p = r,  Ar = H r,  Ap = Ar,  gamma = <r, Ar>
+//   repeat:  alpha = gamma / |Ap|^2;  x += alpha p;  r -= alpha Ap
+//            Ar = H r;  gamma' = <r, Ar>;  beta = gamma' / gamma
+//            p = r + beta p;  Ap = Ar + beta Ap
+//
+// Three kernels per iteration: the x/r update (with |r|^2), the stencil with
+// the <r, Ar> reduction fused into it, and the p/Ap update (with |Ap|^2).
+// alpha and beta are formed inside the kernels from device scalars; the
+// reduction epilogues (last block) advance those scalars.
+#include <chrono>
+
+#include "dwf_stencil.cuh"
+#include "krylov.cuh"
+
+namespace hdcr {
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) g5dwf_dot_kernel(Geom g, R diag, R mf,
+                                                                const cpx<R>* __restrict__ U,
+                                                                const cpx<R>* __restrict__ in,
+                                                                cpx<R>* __restrict__ out, RedScratch rs,
+                                                                double* result) {
+  double acc_d[1] = {0.0};
+  for (long long i5 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i5 < g.V5;
+       i5 += (long long)gridDim.x * blockDim.x) {
+    cpx<R> acc[4][3];
+    dwf_site<R>(g, diag, mf, U, in, i5, acc);
+    store_g5r5<R>(g, out, i5, acc);
+    const long long o5 = reflected(g, i5);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const cpx<R> a = ld(in + (3 * sp + c) * g.V5 + o5);
+        const double sgn = sp >= 2 ? -1.0 : 1.0;
+        acc_d[0] += sgn * ((double)a.re * acc[sp][c].re + (double)a.im * acc[sp][c].im);
+      }
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc_d, rs, tot)) *result = tot[0];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) cr_setup_r_kernel(const cpx<R>* __restrict__ b,
+                                                                 const cpx<R>* __restrict__ Hx,
+                                                                 cpx<R>* __restrict__ r,
+                                                                 cpx<R>* __restrict__ p, long long n,
+                                                                 RedScratch rs, CRDev* s) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> bv = ld(b + i);
+    cpx<R> rv = bv;
+    if (Hx) rv = bv - ld(Hx + i);
+    st(r + i, rv);
+    st(p + i, rv);
+    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
+    acc[1] += (double)bv.re * bv.re + (double)bv.im * bv.im;
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, rs, tot)) {
+    s->rr = tot[0];
+    s->bb = tot[1];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) cr_setup_ap_kernel(const cpx<R>* __restrict__ Ar,
+                                                                  cpx<R>* __restrict__ Ap, long long n,
+                                                                  RedScratch rs, CRDev* s) {
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> v = ld(Ar + i);
+    st(Ap + i, v);
+    acc[0] += (double)v.re * v.re + (double)v.im * v.im;
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc, rs, tot)) s->ApAp = tot[0];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) cr_update_xr_kernel(cpx<R>* __restrict__ x,
+                                                                   cpx<R>* __restrict__ r,
+                                                                   const cpx<R>* __restrict__ p,
+                                                                   const cpx<R>* __restrict__ Ap,
+                                                                   long long n, RedScratch rs, CRDev* s) {
+  const double den = s->ApAp;
+  const R alpha = (R)(den > 0.0 ? s->gamma / den : 0.0);
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    cpx<R> xv = ld(x + i), rv = ld(r + i);
+    const cpx<R> pv = ld(p + i), av = ld(Ap + i);
+    xv.re = fma(alpha, pv.re, xv.re);
+    xv.im = fma(alpha, pv.im, xv.im);
+    rv.re = fma(-alpha, av.re, rv.re);
+    rv.im = fma(-alpha, av.im, rv.im);
+    st(x + i, xv);
+    st(r + i, rv);
+    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc, rs, tot)) s->rr = tot[0];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) cr_update_p_kernel(const cpx<R>* __restrict__ r,
+                                                                  cpx<R>* __restrict__ p,
+                                                                  const cpx<R>* __restrict__ Ar,
+                                                                  cpx<R>* __restrict__ Ap, long long n,
+                                                                  RedScratch rs, CRDev* s) {
+  const double gam = s->gamma;
+  const R beta = (R)(gam != 0.0 ? s->gamma_new / gam : 0.0);
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> rv = ld(r + i), arv = ld(Ar + i);
+    cpx<R> pv = ld(p + i), apv = ld(Ap + i);
+    pv.re = fma(beta, pv.re, rv.re);
+    pv.im = fma(beta, pv.im, rv.im);
+    apv.re = fma(beta, apv.re, arv.re);
+    apv.im = fma(beta, apv.im, arv.im);
+    st(p + i, pv);
+    st(Ap + i, apv);
+    acc[0] += (double)apv.re * apv.re + (double)apv.im * apv.im;
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc, rs, tot)) {
+    s->ApAp = tot[0];
+    s->gamma = s->gamma_new;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) diff_norm_kernel(const cpx<R>* __restrict__ b,
+                                                                const cpx<R>* __restrict__ Hx, long long n,
+                                                                RedScratch rs, double* result) {
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> d = ld(b + i) - ld(Hx + i);
+    acc[0] += (double)d.re * d.re + (double)d.im * d.im;
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc, rs, tot)) *result = tot[0];
+}
+
+// ------------------------------------------------------------------- host side
+double* pinned_ring() {
+  static thread_local double* ring = nullptr;
+  if (!ring) {
+    if (cudaHostAlloc((void**)&ring, sizeof(double) * PINNED_RING, cudaHostAllocPortable) != cudaSuccess) {
+      ring = nullptr;
+      cudaGetLastError();
+    }
+  }
+  return ring;
+}
+
+template <typename R>
+int crwork_alloc(CRWork<R>* w, long long n) {
+  void* p = nullptr;
+  const size_t bytes = sizeof(cpx<R>) * (size_t)n * 4;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    set_error("CR workspace: cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return HDCR_ERR_NO_MEMORY;
+  }
+  w->r = (cpx<R>*)p;
+  w->p = w->r + n;
+  w->Ar = w->p + n;
+  w->Ap = w->Ar + n;
+  int s = red_buffers_alloc(&w->rb, (int)(sizeof(CRDev) / sizeof(double)));
+  if (s != HDCR_OK) {
+    cudaFree(p);
+    return s;
+  }
+  return HDCR_OK;
+}
+
+template <typename R>
+void crwork_free(CRWork<R>* w) {
+  if (w->r) cudaFree(w->r);
+  w->r = nullptr;
+  red_buffers_free(&w->rb);
+}
+
+template <typename R>
+int launch_g5dwf_dot(const FineOp<R>& H, const cpx<R>* in, cpx<R>* out, RedScratch rs, double* result,
+                     cudaStream_t st) {
+  g5dwf_dot_kernel<R><<<red_blocks(H.g.V5 * 4), RED_THREADS, 0, st>>>(
+      H.g, (R)(5.0 - H.M5), (R)H.mf, H.U, in, out, rs, result);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+template <typename R>
+int true_residual2(const FineOp<R>& H, const cpx<R>* b, const cpx<R>* x, cpx<R>* tmp, RedScratch rs,
+                   double* result, cudaStream_t st) {
+  HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, H.U, x, tmp, 1, st));
+  const long long n = H.n();
+  diff_norm_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, tmp, n, rs, result);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+template <typename R>
+int cr_run(const FineOp<R>& H, const cpx<R>* b, cpx<R>* x, CRWork<R>& w, const CRConfig& cfg,
+           CRResult* res, cudaStream_t st) {
+  const long long n = H.n();
+  const int nb = red_blocks(n);
+  CRDev* s = w.dev();
+  RedScratch rs = w.rb.rs;
+  CRResult out;
+  const bool fixed = cfg.fixed_iters >= 0;
+  if (!cfg.x_zero) {
+    HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, H.U, x, w.Ar, 1, st));
+    out.matvecs++;
+  }
+  cr_setup_r_kernel<R><<<nb, RED_THREADS, 0, st>>>(b, cfg.x_zero ? nullptr : w.Ar, w.r, w.p, n, rs, s);
+  HDCR_LAUNCH_CHECK();
+  const int niter = fixed ? cfg.fixed_iters : cfg.max_iter;
+  if (niter == 0) {
+    if (res) *res = out;
+    return HDCR_OK;
+  }
+  HDCR_TRY(launch_g5dwf_dot<R>(H, w.r, w.Ar, rs, &s->gamma, st));
+  out.matvecs++;
+  cr_setup_ap_kernel<R><<<nb, RED_THREADS, 0, st>>>(w.Ar, w.Ap, n, rs, s);
+  HDCR_LAUNCH_CHECK();
+
+  double* ring = nullptr;
+  double scale2 = 0.0;
+  if (!fixed) {
+    ring = pinned_ring();
+    if (!ring) {
+      set_error("pinned host buffer unavailable");
+      return HDCR_ERR_NO_MEMORY;
+    }
+    HDCR_CUDA_TRY(cudaMemcpyAsync(ring, &s->rr, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDCR_CUDA_TRY(cudaStreamSynchronize(st));
+    scale2 = ring[1] > 0.0 ? ring[1] : ring[0];  // |b|^2, or |r0|^2 when b = 0
+    if (!(scale2 == scale2) || scale2 > 1e300) {
+      set_error("CR: non-finite right-hand side");
+      return HDCR_ERR_NONFINITE;
+    }
+    if (scale2 == 0.0 || ring[0] <= cfg.tol * cfg.tol * scale2) {
+      out.converged = true;
+      out.rel_resid = scale2 > 0 ? sqrt(ring[0] / scale2) : 0.0;
+      if (res) *res = out;
+      return HDCR_OK;
+    }
+  }
+  const int ck = cfg.check_every > 0 ? (cfg.check_every < PINNED_RING ? cfg.check_every : PINNED_RING) : 1;
+  int pending = 0;
+  for (int k = 0; k < niter; ++k) {
+    cr_update_xr_kernel<R><<<nb, RED_THREADS, 0, st>>>(x, w.r, w.p, w.Ap, n, rs, s);
+    HDCR_LAUNCH_CHECK();
+    out.iters = k + 1;
+    if (!fixed) {
+      HDCR_CUDA_TRY(cudaMemcpyAsync(ring + pending, &s->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+      ++pending;
+      if (pending == ck || k == niter - 1) {
+        HDCR_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int i = 0; i < pending; ++i) {
+          const double rr = ring[i];
+          if (!(rr == rr) || rr > 1e300) {
+            set_error("CR: non-finite residual at iteration %d", k + 1 - pending + i + 1);
+            if (res) *res = out;
+            return HDCR_ERR_NONFINITE;
+          }
+          out.rel_resid = sqrt(rr / scale2);
+          if (rr <= cfg.tol * cfg.tol * scale2) {
+            out.converged = true;
+            break;
+          }
+        }
+        pending = 0;
+        if (out.converged) break;
+      }
+    }
+    if (k == niter - 1) break;
+    HDCR_TRY(launch_g5dwf_dot<R>(H, w.r, w.Ar, rs, &s->gamma_new, st));
+    out.matvecs++;
+    cr_update_p_kernel<R><<<nb, RED_THREADS, 0, st>>>(w.r, w.p, w.Ar, w.Ap, n, rs, s);
+    HDCR_LAUNCH_CHECK();
+  }
+  if (res) *res = out;
+  return HDCR_OK;
+}
+
+#define HDCR_INST_CR(R)                                                                              \
+  template int crwork_alloc<R>(CRWork<R>*, long long);                                              \
+  template void crwork_free<R>(CRWork<R>*);                                                         \
+  template int launch_g5dwf_dot<R>(const FineOp<R>&, const cpx<R>*, cpx<R>*, RedScratch, double*,   \
+                                   cudaStream_t);                                                   \
+  template int true_residual2<R>(const FineOp<R>&, const cpx<R>*, const cpx<R>*, cpx<R>*,           \
+                                 RedScratch, double*, cudaStream_t);                                \
+  template int cr_run<R>(const FineOp<R>&, const cpx<R>*, cpx<R>*, CRWork<R>&, const CRConfig&,     \
+                         CRResult*, cudaStream_t);
+HDCR_INST_CR(double)
+HDCR_INST_CR(float)
+
+template <typename R>
+static int cr_solve_impl(const Geom& g, const hdcr_dwf_params* p, const void* U, const void* b, void* x,
+                         double tol, int max_iter, hdcr_solve_stats* stats, cudaStream_t st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  FineOp<R> H{g, p->M5, p->mf, (const cpx<R>*)U};
+  CRWork<R> w;
+  HDCR_TRY(crwork_alloc<R>(&w, H.n()));
+  CRConfig cfg;
+  cfg.tol = tol;
+  cfg.max_iter = max_iter;
+  cfg.check_every = sizeof(R) == 8 ? 2 : 8;
+  CRResult res;
+  int s = cr_run<R>(H, (const cpx<R>*)b, (cpx<R>*)x, w, cfg, &res, st);
+  double tr = -1.0;
+  if (s == HDCR_OK) {
+    s = true_residual2<R>(H, (const cpx<R>*)b, (const cpx<R>*)x, w.Ar, w.rb.rs, &w.dev()->tr, st);
+    double* ring = pinned_ring();
+    if (s == HDCR_OK && ring) {
+      cudaError_t e = cudaMemcpyAsync(ring, &w.dev()->bb, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess)
+        s = cuda_status(e, "CR true residual");
+      else
+        tr = ring[0] > 0 ? sqrt(ring[1] / ring[0]) : 0.0;
+    }
+  }
+  cudaStreamSynchronize(st);
+  crwork_free<R>(&w);
+  if (s == HDCR_OK && !res.converged) {
+    set_error("CR: not converged after %d iterations (|r|/|b| = %g)", res.iters, res.rel_resid);
+    s = HDCR_ERR_NOT_CONVERGED;
+  }
+  if (stats) {
+    stats->status = s;
+    stats->iters = res.iters;
+    stats->fine_matvecs = res.matvecs + 1;
+    stats->fine_matvecs_lo = 0;
+    stats->coarse_matvecs = 0;
+    stats->restarts = 0;
+    stats->true_resid = tr;
+    stats->t_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->t_smoother = 0.0;
+    stats->t_coarse = 0.0;
+  }
+  return s;
+}
+
+}  // namespace hdcr
+
+using namespace hdcr;
+
+extern "C" int hdcr_cr_solve(const hdcr_geom* gp, const hdcr_dwf_params* p, const void* U, const void* b,
+                             void* x, int dtype, double tol, int max_iter, hdcr_solve_stats* stats,
+                             void* stream) {
+  Geom g;
+  HDCR_TRY(make_geom(gp, &g));
+  if (!p || !U || !b || !x || b == x || !(tol > 0.0) || max_iter < 1) {
+    set_error("hdcr_cr_solve: bad pointer, tol or max_iter");
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (dtype == HDCR_C128) return cr_solve_impl<double>(g, p, U, b, x, tol, max_iter, stats, as_stream(stream));
+  if (dtype == HDCR_C64) return cr_solve_impl<float>(g, p, U, b, x, tol, max_iter, stats, as_stream(stream));
+  set_error("hdcr_cr_solve: unknown dtype %d", dtype);
+  return HDCR_ERR_BAD_ARG;
+}

@@ -1,0 +1,70 @@
+"""GPU conjugate residual (Section 3) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dwf
+from oracle.krylov import cr
+from gpu_util import dev, host, links, natural, planes, relerr
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_1611_06944_gb300 as hd
+    return hd
+
+
+def test_cr_fp64_tiny_workload_matches_oracle(hd):
+    """4^4 x 8, eps = 0.3, M5 = 1.8, mf = 0.01: unpreconditioned CR to 1e-10."""
+    L, Ls = (4, 4, 4, 4), 8
+    U = synth.gauge_field(L, 0.3, 1000)
+    b = synth.gaussian_fermion(L, Ls, 2000)
+    lat = hd.Lattice(L, Ls)
+    x, st = hd.cr_solve(lat, dev(links(U)), dev(planes(b)), 1.8, 0.01, tol=1e-10, max_iter=20000)
+    assert st["status"] == 0 and st["true_resid"] <= 1e-10
+    xg = natural(host(x), L, Ls)
+    # the true residual recomputed by the oracle agrees
+    r = b - dwf.apply_H(U, xg, 1.8, 0.01)
+    assert np.sqrt(dwf.norm2(r) / dwf.norm2(b)) <= 1.01e-10
+    xo, io = cr(lambda v: dwf.apply_H(U, v, 1.8, 0.01), b, tol=1e-10, maxiter=40000)
+    # both solve the same system: differences are bounded by cond * tol
+    assert relerr(xg, xo) < 1e-6
+    # same recursion, different summation order and a convergence test every
+    # 2 iterations: the iteration counts agree closely
+    assert abs(st["iters"] - io.iters) <= max(8, 0.02 * io.iters)
+
+
+def test_cr_fp32_reaches_single_precision(hd):
+    L, Ls = (4, 4, 4, 4), 8
+    U = synth.gauge_field(L, 0.3, 1000)
+    b = synth.gaussian_fermion(L, Ls, 2001)
+    lat = hd.Lattice(L, Ls)
+    x, st = hd.cr_solve(lat, dev(links(U), torch.complex64), dev(planes(b), torch.complex64),
+                        1.8, 0.01, tol=1e-5, max_iter=20000)
+    assert st["status"] == 0
+    xg = natural(host(x).astype(np.complex128), L, Ls)
+    r = b - dwf.apply_H(U, xg, 1.8, 0.01)
+    assert np.sqrt(dwf.norm2(r) / dwf.norm2(b)) <= 2e-5
+
+
+def test_cr_reports_non_convergence(hd):
+    L, Ls = (4, 4, 4, 4), 4
+    U = synth.gauge_field(L, 0.3, 1000)
+    b = synth.gaussian_fermion(L, Ls, 2002)
+    with pytest.raises(hd.HDCRError) as e:
+        hd.cr_solve(hd.Lattice(L, Ls), dev(links(U)), dev(planes(b)), 1.8, 0.01, tol=1e-10, max_iter=3)
+    assert e.value.status == -3
+
+
+def test_cr_reports_nonfinite_source(hd):
+    L, Ls = (4, 4, 4, 4), 4
+    U = synth.gauge_field(L, 0.3, 1000)
+    b = planes(synth.gaussian_fermion(L, Ls, 2003))
+    b[3, 17] = np.nan
+    with pytest.raises(hd.HDCRError) as e:
+        hd.cr_solve(hd.Lattice(L, Ls), dev(links(U)), dev(b), 1.8, 0.01, tol=1e-10, max_iter=100)
+    assert e.value.status == -4

@@ -84,3 +84,16 @@ def test_synthetic_links_are_su3():
     err_u = np.abs(M @ np.conj(np.swapaxes(M, -1, -2)) - np.eye(3)).max()
     err_d = np.abs(np.linalg.det(M) - 1).max()
     assert err_u < 1e-14 and err_d < 1e-14
+
+
+def test_sitewise_evaluation_matches_field_apply():
+    L, Ls = (3, 4, 2, 5), 4
+    U = synth.gauge_field(L, 0.5, 61)
+    psi = synth.gaussian_fermion(L, Ls, 62)
+    full = dwf.apply_H(U, psi, 1.8, 0.02, -1)
+    rng = synth.rng(63)
+    sites = [tuple(int(rng.integers(0, e)) for e in L + (Ls,)) for _ in range(40)]
+    sites += [(0, 0, 0, 0, 0), (2, 3, 1, 4, Ls - 1)]
+    got = dwf.apply_H_at(U, psi, sites, 1.8, 0.02, -1)
+    want = np.array([full[t, z, y, x, s] for (x, y, z, t, s) in sites])
+    assert relerr(got, want) < 1e-15
