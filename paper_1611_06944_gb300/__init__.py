@@ -4,7 +4,8 @@ Thin layer over the C ABI declared in ``include/hdcr.h``: it checks tensor
 shapes, dtypes and devices, passes raw device pointers and the current CUDA
 stream, and turns a nonzero status into ``HDCRError``.  PyTorch supplies
 device memory and streams only; every step of the method runs in the CUDA
-library, and importing this package fails when the library is missing.
+library.  The library is loaded on first use; every call raises ImportError
+when it has not been built (there is no CPU fallback).
 
 Tensor layouts (see ``include/hdcr.h``):
   gauge      (4, V4, 3, 3) complex, or any contiguous tensor of that size
@@ -20,7 +21,24 @@ import torch
 
 from . import _lib
 
-_L = _lib.load()
+
+class _LazyLib:
+    """Loads libhdcr.so on first attribute access (ImportError if it is missing)."""
+
+    _handle = None
+
+    def __getattr__(self, name):
+        if _LazyLib._handle is None:
+            _LazyLib._handle = _lib.load()
+        return getattr(_LazyLib._handle, name)
+
+
+_L = _LazyLib()
+
+
+def load_library():
+    """Load libhdcr.so now (raises ImportError if it has not been built)."""
+    return _L.hdcr_version()
 
 __all__ = [
     "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "to_planes", "from_planes",

@@ -189,118 +189,64 @@ void crwork_free(CRWork<R>* w) {
 }
 
 template <typename R>
-int launch_g5dwf_dot(const FineOp<R>& H, const cpx<R>* in, cpx<R>* out, RedScratch rs, double* result,
+int launch_g5dwf_dot(const Geom& g, double M5, double mf, const cpx<R>* U, const cpx<R>* in,
+                     cpx<R>* out, RedScratch rs, double* result, cudaStream_t st) {
+  g5dwf_dot_kernel<R><<<red_blocks(g.V5 * 4), RED_THREADS, 0, st>>>(g, (R)(5.0 - M5), (R)mf, U, in, out,
+                                                                      rs, result);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+template <typename R>
+int launch_cr_setup_r(const cpx<R>* b, const cpx<R>* Hx, cpx<R>* r, cpx<R>* p, long long n,
+                      RedScratch rs, CRDev* s, cudaStream_t st) {
+  cr_setup_r_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, Hx, r, p, n, rs, s);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+template <typename R>
+int launch_cr_setup_ap(const cpx<R>* Ar, cpx<R>* Ap, long long n, RedScratch rs, CRDev* s, cudaStream_t st) {
+  cr_setup_ap_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(Ar, Ap, n, rs, s);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+template <typename R>
+int launch_cr_update_xr(cpx<R>* x, cpx<R>* r, const cpx<R>* p, const cpx<R>* Ap, long long n,
+                        RedScratch rs, CRDev* s, cudaStream_t st) {
+  cr_update_xr_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(x, r, p, Ap, n, rs, s);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+template <typename R>
+int launch_cr_update_p(const cpx<R>* r, cpx<R>* p, const cpx<R>* Ar, cpx<R>* Ap, long long n,
+                       RedScratch rs, CRDev* s, cudaStream_t st) {
+  cr_update_p_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(r, p, Ar, Ap, n, rs, s);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+template <typename R>
+int launch_diff_norm(const cpx<R>* b, const cpx<R>* y, long long n, RedScratch rs, double* result,
                      cudaStream_t st) {
-  g5dwf_dot_kernel<R><<<red_blocks(H.g.V5 * 4), RED_THREADS, 0, st>>>(
-      H.g, (R)(5.0 - H.M5), (R)H.mf, H.U, in, out, rs, result);
+  diff_norm_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, y, n, rs, result);
   HDCR_LAUNCH_CHECK();
-  return HDCR_OK;
-}
-
-template <typename R>
-int true_residual2(const FineOp<R>& H, const cpx<R>* b, const cpx<R>* x, cpx<R>* tmp, RedScratch rs,
-                   double* result, cudaStream_t st) {
-  HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, H.U, x, tmp, 1, st));
-  const long long n = H.n();
-  diff_norm_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, tmp, n, rs, result);
-  HDCR_LAUNCH_CHECK();
-  return HDCR_OK;
-}
-
-template <typename R>
-int cr_run(const FineOp<R>& H, const cpx<R>* b, cpx<R>* x, CRWork<R>& w, const CRConfig& cfg,
-           CRResult* res, cudaStream_t st) {
-  const long long n = H.n();
-  const int nb = red_blocks(n);
-  CRDev* s = w.dev();
-  RedScratch rs = w.rb.rs;
-  CRResult out;
-  const bool fixed = cfg.fixed_iters >= 0;
-  if (!cfg.x_zero) {
-    HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, H.U, x, w.Ar, 1, st));
-    out.matvecs++;
-  }
-  cr_setup_r_kernel<R><<<nb, RED_THREADS, 0, st>>>(b, cfg.x_zero ? nullptr : w.Ar, w.r, w.p, n, rs, s);
-  HDCR_LAUNCH_CHECK();
-  const int niter = fixed ? cfg.fixed_iters : cfg.max_iter;
-  if (niter == 0) {
-    if (res) *res = out;
-    return HDCR_OK;
-  }
-  HDCR_TRY(launch_g5dwf_dot<R>(H, w.r, w.Ar, rs, &s->gamma, st));
-  out.matvecs++;
-  cr_setup_ap_kernel<R><<<nb, RED_THREADS, 0, st>>>(w.Ar, w.Ap, n, rs, s);
-  HDCR_LAUNCH_CHECK();
-
-  double* ring = nullptr;
-  double scale2 = 0.0;
-  if (!fixed) {
-    ring = pinned_ring();
-    if (!ring) {
-      set_error("pinned host buffer unavailable");
-      return HDCR_ERR_NO_MEMORY;
-    }
-    HDCR_CUDA_TRY(cudaMemcpyAsync(ring, &s->rr, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    HDCR_CUDA_TRY(cudaStreamSynchronize(st));
-    scale2 = ring[1] > 0.0 ? ring[1] : ring[0];  // |b|^2, or |r0|^2 when b = 0
-    if (!(scale2 == scale2) || scale2 > 1e300) {
-      set_error("CR: non-finite right-hand side");
-      return HDCR_ERR_NONFINITE;
-    }
-    if (scale2 == 0.0 || ring[0] <= cfg.tol * cfg.tol * scale2) {
-      out.converged = true;
-      out.rel_resid = scale2 > 0 ? sqrt(ring[0] / scale2) : 0.0;
-      if (res) *res = out;
-      return HDCR_OK;
-    }
-  }
-  const int ck = cfg.check_every > 0 ? (cfg.check_every < PINNED_RING ? cfg.check_every : PINNED_RING) : 1;
-  int pending = 0;
-  for (int k = 0; k < niter; ++k) {
-    cr_update_xr_kernel<R><<<nb, RED_THREADS, 0, st>>>(x, w.r, w.p, w.Ap, n, rs, s);
-    HDCR_LAUNCH_CHECK();
-    out.iters = k + 1;
-    if (!fixed) {
-      HDCR_CUDA_TRY(cudaMemcpyAsync(ring + pending, &s->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
-      ++pending;
-      if (pending == ck || k == niter - 1) {
-        HDCR_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int i = 0; i < pending; ++i) {
-          const double rr = ring[i];
-          if (!(rr == rr) || rr > 1e300) {
-            set_error("CR: non-finite residual at iteration %d", k + 1 - pending + i + 1);
-            if (res) *res = out;
-            return HDCR_ERR_NONFINITE;
-          }
-          out.rel_resid = sqrt(rr / scale2);
-          if (rr <= cfg.tol * cfg.tol * scale2) {
-            out.converged = true;
-            break;
-          }
-        }
-        pending = 0;
-        if (out.converged) break;
-      }
-    }
-    if (k == niter - 1) break;
-    HDCR_TRY(launch_g5dwf_dot<R>(H, w.r, w.Ar, rs, &s->gamma_new, st));
-    out.matvecs++;
-    cr_update_p_kernel<R><<<nb, RED_THREADS, 0, st>>>(w.r, w.p, w.Ar, w.Ap, n, rs, s);
-    HDCR_LAUNCH_CHECK();
-  }
-  if (res) *res = out;
   return HDCR_OK;
 }
 
 #define HDCR_INST_CR(R)                                                                              \
   template int crwork_alloc<R>(CRWork<R>*, long long);                                              \
   template void crwork_free<R>(CRWork<R>*);                                                         \
-  template int launch_g5dwf_dot<R>(const FineOp<R>&, const cpx<R>*, cpx<R>*, RedScratch, double*,   \
-                                   cudaStream_t);                                                   \
-  template int true_residual2<R>(const FineOp<R>&, const cpx<R>*, const cpx<R>*, cpx<R>*,           \
-                                 RedScratch, double*, cudaStream_t);                                \
-  template int cr_run<R>(const FineOp<R>&, const cpx<R>*, cpx<R>*, CRWork<R>&, const CRConfig&,     \
-                         CRResult*, cudaStream_t);
+  template int launch_g5dwf_dot<R>(const Geom&, double, double, const cpx<R>*, const cpx<R>*,        \
+                                   cpx<R>*, RedScratch, double*, cudaStream_t);                     \
+  template int launch_cr_setup_r<R>(const cpx<R>*, const cpx<R>*, cpx<R>*, cpx<R>*, long long,      \
+                                    RedScratch, CRDev*, cudaStream_t);                              \
+  template int launch_cr_setup_ap<R>(const cpx<R>*, cpx<R>*, long long, RedScratch, CRDev*,          \
+                                     cudaStream_t);                                                 \
+  template int launch_cr_update_xr<R>(cpx<R>*, cpx<R>*, const cpx<R>*, const cpx<R>*, long long,    \
+                                      RedScratch, CRDev*, cudaStream_t);                            \
+  template int launch_cr_update_p<R>(const cpx<R>*, cpx<R>*, const cpx<R>*, cpx<R>*, long long,     \
+                                     RedScratch, CRDev*, cudaStream_t);                             \
+  template int launch_diff_norm<R>(const cpx<R>*, const cpx<R>*, long long, RedScratch, double*,    \
+                                   cudaStream_t);
 HDCR_INST_CR(double)
 HDCR_INST_CR(float)
 

@@ -7,12 +7,25 @@
 
 namespace hdcr {
 
+// out = H in, and Re <in, out> into *result (device double).
+template <typename R>
+int launch_g5dwf_dot(const Geom& g, double M5, double mf, const cpx<R>* U, const cpx<R>* in,
+                     cpx<R>* out, RedScratch rs, double* result, cudaStream_t st);
+
+// An operator usable by cr_run: n() complex entries per vector, apply, and
+// apply with Re <in, out> reduced into a device double.
 template <typename R>
 struct FineOp {
   Geom g;
   double M5, mf;
   const cpx<R>* U;
   long long n() const { return g.V5 * 12; }  // complex entries of one field
+  int apply(const cpx<R>* in, cpx<R>* out, cudaStream_t st) const {
+    return launch_g5dwf<R>(g, M5, mf, U, in, out, 1, st);
+  }
+  int apply_dot(const cpx<R>* in, cpx<R>* out, RedScratch rs, double* res, cudaStream_t st) const {
+    return launch_g5dwf_dot<R>(g, M5, mf, U, in, out, rs, res, st);
+  }
 };
 
 // device scalars of one CR run
@@ -56,21 +69,114 @@ struct CRResult {
   double rel_resid = -1.0;  // recursive |r|/|b| at the last check
 };
 
-template <typename R>
-int cr_run(const FineOp<R>& H, const cpx<R>* b, cpx<R>* x, CRWork<R>& w, const CRConfig& cfg,
-           CRResult* res, cudaStream_t st);
-
-// |b - H x|^2 into *result (device double), using tmp as workspace.
-template <typename R>
-int true_residual2(const FineOp<R>& H, const cpx<R>* b, const cpx<R>* x, cpx<R>* tmp, RedScratch rs,
-                   double* result, cudaStream_t st);
-
-// out = H in, and Re <in, out> into *result (device double).
-template <typename R>
-int launch_g5dwf_dot(const FineOp<R>& H, const cpx<R>* in, cpx<R>* out, RedScratch rs, double* result,
-                     cudaStream_t st);
-
 double* pinned_ring();  // per host thread, 1024 doubles of pinned memory
 constexpr int PINNED_RING = 1024;
+
+// BLAS steps of CR (cr.cu), n complex entries, scalars in CRDev
+template <typename R>
+int launch_cr_setup_r(const cpx<R>* b, const cpx<R>* Hx, cpx<R>* r, cpx<R>* p, long long n,
+                      RedScratch rs, CRDev* s, cudaStream_t st);
+template <typename R>
+int launch_cr_setup_ap(const cpx<R>* Ar, cpx<R>* Ap, long long n, RedScratch rs, CRDev* s, cudaStream_t st);
+template <typename R>
+int launch_cr_update_xr(cpx<R>* x, cpx<R>* r, const cpx<R>* p, const cpx<R>* Ap, long long n,
+                        RedScratch rs, CRDev* s, cudaStream_t st);
+template <typename R>
+int launch_cr_update_p(const cpx<R>* r, cpx<R>* p, const cpx<R>* Ar, cpx<R>* Ap, long long n,
+                       RedScratch rs, CRDev* s, cudaStream_t st);
+// |b - y|^2 into *result
+template <typename R>
+int launch_diff_norm(const cpx<R>* b, const cpx<R>* y, long long n, RedScratch rs, double* result,
+                     cudaStream_t st);
+
+// |b - A x|^2 into *result (device double), using tmp as workspace.
+template <typename R, class Op>
+int true_residual2(const Op& A, const cpx<R>* b, const cpx<R>* x, cpx<R>* tmp, RedScratch rs,
+                   double* result, cudaStream_t st) {
+  HDCR_TRY(A.apply(x, tmp, st));
+  return launch_diff_norm<R>(b, tmp, A.n(), rs, result, st);
+}
+
+// Conjugate residual on A x = b (Section 3).  In convergence mode the host
+// reads |r|^2 every cfg.check_every iterations; with cfg.fixed_iters >= 0 the
+// run is a fixed sequence of launches with no host synchronisation.
+template <typename R, class Op>
+int cr_run(const Op& A, const cpx<R>* b, cpx<R>* x, CRWork<R>& w, const CRConfig& cfg, CRResult* res,
+           cudaStream_t st) {
+  const long long n = A.n();
+  CRDev* s = w.dev();
+  RedScratch rs = w.rb.rs;
+  CRResult out;
+  const bool fixed = cfg.fixed_iters >= 0;
+  if (!cfg.x_zero) {
+    HDCR_TRY(A.apply(x, w.Ar, st));
+    out.matvecs++;
+  }
+  HDCR_TRY(launch_cr_setup_r<R>(b, cfg.x_zero ? nullptr : w.Ar, w.r, w.p, n, rs, s, st));
+  const int niter = fixed ? cfg.fixed_iters : cfg.max_iter;
+  if (niter == 0) {
+    if (res) *res = out;
+    return HDCR_OK;
+  }
+  double* ring = nullptr;
+  double scale2 = 0.0;
+  if (!fixed) {
+    ring = pinned_ring();
+    if (!ring) {
+      set_error("pinned host buffer unavailable");
+      return HDCR_ERR_NO_MEMORY;
+    }
+    HDCR_CUDA_TRY(cudaMemcpyAsync(ring, &s->rr, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDCR_CUDA_TRY(cudaStreamSynchronize(st));
+    scale2 = ring[1] > 0.0 ? ring[1] : ring[0];  // |b|^2, or |r0|^2 when b = 0
+    if (!(scale2 == scale2) || scale2 > 1e300) {
+      set_error("CR: non-finite right-hand side or initial residual");
+      return HDCR_ERR_NONFINITE;
+    }
+    if (scale2 == 0.0 || ring[0] <= cfg.tol * cfg.tol * scale2) {
+      out.converged = true;
+      out.rel_resid = scale2 > 0 ? sqrt(ring[0] / scale2) : 0.0;
+      if (res) *res = out;
+      return HDCR_OK;
+    }
+  }
+  HDCR_TRY(A.apply_dot(w.r, w.Ar, rs, &s->gamma, st));
+  out.matvecs++;
+  HDCR_TRY(launch_cr_setup_ap<R>(w.Ar, w.Ap, n, rs, s, st));
+  const int ck = cfg.check_every > 0 ? (cfg.check_every < PINNED_RING ? cfg.check_every : PINNED_RING) : 1;
+  int pending = 0;
+  for (int k = 0; k < niter; ++k) {
+    HDCR_TRY(launch_cr_update_xr<R>(x, w.r, w.p, w.Ap, n, rs, s, st));
+    out.iters = k + 1;
+    if (!fixed) {
+      HDCR_CUDA_TRY(cudaMemcpyAsync(ring + pending, &s->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+      ++pending;
+      if (pending == ck || k == niter - 1) {
+        HDCR_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int i = 0; i < pending; ++i) {
+          const double rr = ring[i];
+          if (!(rr == rr) || rr > 1e300) {
+            set_error("CR: non-finite residual at iteration %d", k + 2 - pending + i);
+            if (res) *res = out;
+            return HDCR_ERR_NONFINITE;
+          }
+          out.rel_resid = sqrt(rr / scale2);
+          if (rr <= cfg.tol * cfg.tol * scale2) {
+            out.converged = true;
+            break;
+          }
+        }
+        pending = 0;
+        if (out.converged) break;
+      }
+    }
+    if (k == niter - 1) break;
+    HDCR_TRY(A.apply_dot(w.r, w.Ar, rs, &s->gamma_new, st));
+    out.matvecs++;
+    HDCR_TRY(launch_cr_update_p<R>(w.r, w.p, w.Ar, w.Ap, n, rs, s, st));
+  }
+  if (res) *res = out;
+  return HDCR_OK;
+}
 
 }  // namespace hdcr
