@@ -42,7 +42,7 @@ def load_library():
 
 __all__ = [
     "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "to_planes", "from_planes",
-    "convert", "cdot", "norm2", "cr_solve", "library_path",
+    "convert", "cdot", "norm2", "cr_solve", "cr_solve_into", "library_path",
 ]
 
 library_path = _lib.LIB_PATH
@@ -207,6 +207,20 @@ def cr_solve(lat: Lattice, U: torch.Tensor, b: torch.Tensor, M5: float, mf: floa
     _check(_L.hdcr_cr_solve(C_ref(g), C_ref(p), _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), _code(b),
                             float(tol), int(max_iter), C_ref(st), _stream(stream)), "cr_solve")
     return x, st.as_dict()
+
+
+def cr_solve_into(lat: Lattice, U: torch.Tensor, b: torch.Tensor, x: torch.Tensor, M5: float,
+                  mf: float, tol: float = 1e-10, max_iter: int = 100000, stream=None) -> dict:
+    """cr_solve with a caller-owned x (initial guess in, iterate out, also when the
+    iteration cap is reached and HDCRError(NOT_CONVERGED) is raised)."""
+    if U.dtype != b.dtype or x.dtype != b.dtype or x.numel() != b.numel():
+        raise TypeError("U, b and x must share a dtype and b, x a size")
+    st = _lib.hdcr_solve_stats()
+    g = lat.c_geom()
+    p = _params(M5, mf)
+    _check(_L.hdcr_cr_solve(C_ref(g), C_ref(p), _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), _code(b),
+                            float(tol), int(max_iter), C_ref(st), _stream(stream)), "cr_solve")
+    return st.as_dict()
 
 
 def C_ref(obj):
