@@ -26,9 +26,11 @@
  *  Gauge field    U[mu][x4][a][b], mu = 0..3 <-> x, y, z, t, a 3x3 colour
  *                 matrix U_mu(x)_{ab} per link, row-major; the link leaves x
  *                 in the +mu direction.  4 * V4 * 9 complex.
- *  Fermion field  psi[c][i5]: 12 planes c = 3*spin + colour, each holding
- *                 V5 complex, i5 = x4*Ls + s.  Several fields (nrhs, nvec)
- *                 follow one another, each 12*V5 complex.
+ *  Fermion field  psi[x4][c][s]: for each 4d site the 12 components
+ *                 c = 3*spin + colour, each a run of Ls complex numbers over
+ *                 the fifth coordinate s (element offset (x4*12 + c)*Ls + s).
+ *                 The 5d site index is i5 = x4*Ls + s.  Several fields
+ *                 (nrhs, nvec) follow one another, each 12*V5 complex.
  *  Spin basis     chiral: gamma_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = x,y,z),
  *                 gamma_t = [[0, 1], [1, 0]], gamma5 = diag(1, 1, -1, -1).
  *  Coarse field   c[a][k], a = ((tc*Zc + zc)*Yc + yc)*Xc + xc, k < nvec.
@@ -106,11 +108,11 @@ int hdcr_apply_gamma5_r5(const hdcr_geom* g, const void* in, void* out, int dtyp
                          int nfields, void* stream);
 
 /* Layout conversion between the natural array layout psi[x4][s][spin][colour]
- * (complex, as a (Lt,Lz,Ly,Lx,Ls,4,3) tensor) and the plane layout above. */
-int hdcr_fermion_to_planes(const hdcr_geom* g, const void* natural, void* planes,
-                           int dtype, int nfields, void* stream);
-int hdcr_fermion_from_planes(const hdcr_geom* g, const void* planes, void* natural,
-                             int dtype, int nfields, void* stream);
+ * (complex, a (Lt,Lz,Ly,Lx,Ls,4,3) tensor) and the library layout above. */
+int hdcr_fermion_pack(const hdcr_geom* g, const void* natural, void* packed, int dtype,
+                      int nfields, void* stream);
+int hdcr_fermion_unpack(const hdcr_geom* g, const void* packed, void* natural, int dtype,
+                        int nfields, void* stream);
 
 /* Precision conversion of n complex numbers (device to device). */
 int hdcr_convert(const void* in, int in_dtype, void* out, int out_dtype, size_t n,
@@ -132,13 +134,100 @@ int hdcr_norm2(const void* u, size_t n, int dtype, double* result, void* stream)
  * Conjugate residual (Section 3) on H x = b, unpreconditioned, all in ``dtype``
  * (inner products in FP64).  x holds the initial guess on entry.  Stops when the
  * recursively updated residual satisfies |r| <= tol |b| and then recomputes the
- * true residual in FP64 into stats->true_resid.  max_iter caps the iterations
- * (NOT_CONVERGED when reached).  Synchronises ``stream``.  Workspace (5 fields)
- * is allocated and freed by the call.
+ * true residual |b - H x| / |b| (FP64 accumulation) into stats->true_resid.
+ * max_iter caps the iterations (NOT_CONVERGED when reached; x then holds the
+ * last iterate).  Synchronises ``stream``.  Workspace (4 fields) is allocated
+ * and freed by the call.
  */
 int hdcr_cr_solve(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
                   const void* b, void* x, int dtype, double tol, int max_iter,
                   hdcr_solve_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------- subspace
+ * hdcr_build_subspace: the near-null-space basis of Section 4.
+ *   1. each of the nvec/2 Gaussian noise fields (``noise``: nvec/2 C128
+ *      fields, drawn by the caller) gets ``smooth_iters`` conjugate-residual
+ *      steps on H x = 0 ("inverse iteration applied to Gaussian noise") and is
+ *      normalised;
+ *   2. chiral split with Gamma5 = gamma5 R5: v -> (1 + Gamma5) v / 2 and
+ *      (1 - Gamma5) v / 2 (the nvec/2 "+" vectors first, then the "-" ones);
+ *   3. restriction to blocks of block[0..3] sites times the full fifth
+ *      dimension (Eq. 4.1);
+ *   4. modified Gram-Schmidt, applied twice, in each block in the order
+ *      k = 0..nvec-1 (FP64), so that P_S of Eq. 4.3 is a projector.
+ * The basis is stored in ``store_dtype``.  U is C128.  Every L[mu] must be a
+ * multiple of block[mu] with L[mu]/block[mu] >= 2; nvec even, 2..256.
+ * Errors: BAD_ARG, BAD_GEOMETRY, RANK_DEFICIENT (a vector has nothing left
+ * after orthogonalisation: |v| < 1e-12 |v0|), CUDA, NO_MEMORY.
+ * Synchronises ``stream``.  On success *out receives a new handle.
+ */
+typedef struct hdcr_subspace hdcr_subspace;
+int hdcr_build_subspace(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
+                        const void* noise, int nvec, const int block[4], int smooth_iters,
+                        int store_dtype, void* stream, hdcr_subspace** out);
+/* The same from nvec given fields (C128, already split): steps 3-4 only. */
+int hdcr_subspace_from_vectors(const hdcr_geom* g, const int block[4], int nvec,
+                               const void* vectors, int store_dtype, void* stream,
+                               hdcr_subspace** out);
+int hdcr_subspace_info(const hdcr_subspace* sub, int* nvec, int coarse_L[4], int* dtype);
+/* Copies the nvec block-orthonormal basis fields (C128) into ``out`` (device). */
+int hdcr_subspace_get_vectors(const hdcr_subspace* sub, void* out, void* stream);
+void hdcr_subspace_destroy(hdcr_subspace* sub);
+
+/* P^dag and P of Eq. 4.3: coarse[r][a][k] = <phi_k^a, fine_r> and
+ * fine_r = sum_{a,k} coarse[r][a][k] phi_k^a, for nrhs fields.  ``dtype`` must
+ * equal the basis storage dtype. */
+int hdcr_restrict(const hdcr_subspace* sub, const void* fine, void* coarse, int dtype, int nrhs,
+                  void* stream);
+int hdcr_prolong(const hdcr_subspace* sub, const void* coarse, void* fine, int dtype, int nrhs,
+                 void* stream);
+
+/* ---------------------------------------------------------------- coarse operator
+ * hdcr_build_coarse_op: little Dirac operator A^{ab}_{jk} = <phi_j^a | H | phi_k^b>
+ * (Eq. 4.5), nonzero only for b = a and the 8 nearest coarse neighbours (the
+ * sparsity noted after Eq. 4.6), stored as A[a][leg][j][k] in ``op_dtype``.  Leg
+ * (mu, +-) collects the fine hops from block a into block a +- mu; on a coarse
+ * extent of 2 the two legs of mu reach the same coarse site and both apply.  U
+ * is C128 (converted internally when op_dtype is C64).  The subspace handle is
+ * borrowed and must outlive the coarse handle.  Synchronises ``stream``.
+ * Errors: BAD_ARG (nvec > 64), CUDA, NO_MEMORY.
+ */
+typedef struct hdcr_coarse hdcr_coarse;
+int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_params* p, const void* U,
+                         int op_dtype, void* stream, hdcr_coarse** out);
+/* Copies A (C128, [Vc][9][nvec][nvec]) into ``out`` (device). */
+int hdcr_coarse_get_op(const hdcr_coarse* co, void* out, void* stream);
+/* out[r][a] = sum_leg A[a][leg] in[r][a + leg], 9-point coarse stencil; dtype = op dtype. */
+int hdcr_apply_coarse(const hdcr_coarse* co, const void* in, void* out, int dtype, int nrhs,
+                      void* stream);
+void hdcr_coarse_destroy(hdcr_coarse* co);
+
+/* ---------------------------------------------------------------- HDCR solve
+ * hdcr_solve: H x = b (Section 4) by flexible GCR(restart) in FP64 on H,
+ * preconditioned by the two-level V-cycle
+ *     z1 = S r;  z2 = z1 + P A^{-1} P^dag (r - H z1);  z = z2 + S (r - H z2),
+ * S = ``smoother_steps`` CR steps from zero, A^{-1} = CR on the coarse operator
+ * to ``coarse_tol`` (cap ``coarse_max``).  For a fixed linear smoother and an
+ * exact coarse solve this is the composite M_outer = S P_L + P_R S + Q - S P_L H S
+ * of Section 4.  inner_dtype C128 runs the preconditioner in FP64; C64 runs
+ * it in FP32 (FP32 links, FP32 basis and coarse operator required) while the
+ * outer FGCR, its orthogonalisation and the true residual stay FP64.  The
+ * solve ends when the true residual |b - H x| / |b| <= tol.  U and b, x are
+ * C128; x holds the initial guess.  Synchronises ``stream``.
+ * Errors: BAD_ARG, NOT_CONVERGED (max_outer reached), NONFINITE, CUDA, NO_MEMORY.
+ */
+typedef struct {
+  double tol;         /* true relative residual target, e.g. 1e-10           */
+  int max_outer;      /* cap on outer iterations                             */
+  int restart;        /* FGCR restart length (1..64)                         */
+  int smoother_steps; /* CR steps of the smoother (>= 0)                     */
+  double coarse_tol;  /* relative residual of the coarse solve, e.g. 1e-4    */
+  int coarse_max;     /* cap on coarse CR iterations                         */
+  int inner_dtype;    /* HDCR_C128 or HDCR_C64                               */
+} hdcr_solve_params;
+
+int hdcr_solve(const hdcr_coarse* co, const void* U, const void* b, void* x,
+               const hdcr_solve_params* params, hdcr_solve_stats* stats, void* stream);
 
 #ifdef __cplusplus
 }

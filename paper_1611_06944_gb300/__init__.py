@@ -9,12 +9,13 @@ when it has not been built (there is no CPU fallback).
 
 Tensor layouts (see ``include/hdcr.h``):
   gauge      (4, V4, 3, 3) complex, or any contiguous tensor of that size
-  fermion    (..., 12, V5) complex "planes", component c = 3*spin + colour,
-             5d site i5 = x4*Ls + s
-  natural    (..., Lt, Lz, Ly, Lx, Ls, 4, 3) complex (converted by to_planes)
+  fermion    (..., V4, 12, Ls) complex "packed": for each 4d site the 12
+             components c = 3*spin + colour, each a run over s
+  natural    (..., Lt, Lz, Ly, Lx, Ls, 4, 3) complex (converted by pack/unpack)
 """
 from __future__ import annotations
 
+import ctypes
 from dataclasses import dataclass
 
 import torch
@@ -41,8 +42,10 @@ def load_library():
     return _L.hdcr_version()
 
 __all__ = [
-    "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "to_planes", "from_planes",
+    "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "norm2", "cr_solve", "cr_solve_into", "library_path",
+    "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
+    "CoarseOperator", "build_coarse_op", "apply_coarse", "hdcr_solve",
 ]
 
 library_path = _lib.LIB_PATH
@@ -143,26 +146,29 @@ def apply_gamma5_r5(lat: Lattice, psi: torch.Tensor, out: torch.Tensor | None = 
     return out
 
 
-def to_planes(lat: Lattice, natural: torch.Tensor, stream=None) -> torch.Tensor:
-    """(..., Lt, Lz, Ly, Lx, Ls, 4, 3) -> (..., 12, V5)."""
+def pack(lat: Lattice, natural: torch.Tensor, stream=None) -> torch.Tensor:
+    """(..., Lt, Lz, Ly, Lx, Ls, 4, 3) -> packed (..., V4, 12, Ls)."""
     n = _nfields(lat, natural, "natural")
     lead = natural.shape[:-7]
-    out = torch.empty(lead + (12, lat.V5), dtype=natural.dtype, device=natural.device)
+    out = torch.empty(lead + (lat.V4, 12, lat.Ls), dtype=natural.dtype, device=natural.device)
     g = lat.c_geom()
-    _check(_L.hdcr_fermion_to_planes(C_ref(g), _dev(natural, "natural"), _dev(out, "out"),
-                                     _code(natural), n, _stream(stream)), "to_planes")
+    _check(_L.hdcr_fermion_pack(C_ref(g), _dev(natural, "natural"), _dev(out, "out"),
+                                _code(natural), n, _stream(stream)), "pack")
     return out
 
 
-def from_planes(lat: Lattice, planes: torch.Tensor, stream=None) -> torch.Tensor:
-    """(..., 12, V5) -> (..., Lt, Lz, Ly, Lx, Ls, 4, 3)."""
-    n = _nfields(lat, planes, "planes")
-    lead = planes.shape[:-2]
+def unpack(lat: Lattice, packed: torch.Tensor, stream=None) -> torch.Tensor:
+    """packed (..., V4, 12, Ls) -> (..., Lt, Lz, Ly, Lx, Ls, 4, 3)."""
+    n = _nfields(lat, packed, "packed")
+    if packed.dim() >= 3 and tuple(packed.shape[-3:]) == (lat.V4, 12, lat.Ls):
+        lead = tuple(packed.shape[:-3])
+    else:
+        lead = (n,) if n > 1 else ()
     Lx, Ly, Lz, Lt = lat.L
-    out = torch.empty(lead + (Lt, Lz, Ly, Lx, lat.Ls, 4, 3), dtype=planes.dtype, device=planes.device)
+    out = torch.empty(lead + (Lt, Lz, Ly, Lx, lat.Ls, 4, 3), dtype=packed.dtype, device=packed.device)
     g = lat.c_geom()
-    _check(_L.hdcr_fermion_from_planes(C_ref(g), _dev(planes, "planes"), _dev(out, "out"),
-                                       _code(planes), n, _stream(stream)), "from_planes")
+    _check(_L.hdcr_fermion_unpack(C_ref(g), _dev(packed, "packed"), _dev(out, "out"),
+                                  _code(packed), n, _stream(stream)), "unpack")
     return out
 
 
@@ -224,5 +230,176 @@ def cr_solve_into(lat: Lattice, U: torch.Tensor, b: torch.Tensor, x: torch.Tenso
 
 
 def C_ref(obj):
-    import ctypes
     return ctypes.byref(obj)
+
+
+# ------------------------------------------------------------------ two-level
+class Subspace:
+    """Block-orthonormal subspace basis (Section 4), owned by the library."""
+
+    def __init__(self, handle, lat: Lattice, block, nvec: int, dtype: torch.dtype, device):
+        self._h = handle
+        self.lat = lat
+        self.block = tuple(block)
+        self.nvec = nvec
+        self.dtype = dtype
+        self.device = device
+        self.coarse_L = tuple(lat.L[i] // self.block[i] for i in range(4))
+        self.Vc = self.coarse_L[0] * self.coarse_L[1] * self.coarse_L[2] * self.coarse_L[3]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def vectors(self, stream=None) -> torch.Tensor:
+        """The nvec basis fields as complex128, packed layout (nvec, V4, 12, Ls)."""
+        out = torch.empty((self.nvec, self.lat.V4, 12, self.lat.Ls), dtype=torch.complex128,
+                          device=self.device)
+        _check(_L.hdcr_subspace_get_vectors(self._h, out.data_ptr(), _stream(stream)), "subspace vectors")
+        return out
+
+    def close(self):
+        if self._h:
+            _L.hdcr_subspace_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _block_arr(block):
+    arr = (ctypes.c_int * 4)(*[int(b) for b in block])
+    return arr
+
+
+def build_subspace(lat: Lattice, U: torch.Tensor, noise: torch.Tensor, M5: float, mf: float, block,
+                   smooth_iters: int = 10, store_dtype: torch.dtype = torch.complex128,
+                   stream=None) -> Subspace:
+    """Subspace from nvec/2 noise fields (complex128, packed): smoothing by CR on H x = 0,
+    Gamma5 chiral split, block orthonormalisation (Section 4)."""
+    if U.dtype != torch.complex128 or noise.dtype != torch.complex128:
+        raise TypeError("build_subspace takes complex128 links and noise")
+    half = _nfields(lat, noise, "noise")
+    h = ctypes.c_void_p()
+    g = lat.c_geom()
+    p = _params(M5, mf)
+    code = _lib.HDCR_C128 if store_dtype == torch.complex128 else _lib.HDCR_C64
+    _check(_L.hdcr_build_subspace(C_ref(g), C_ref(p), _dev(U, "U"), _dev(noise, "noise"), 2 * half,
+                                  _block_arr(block), int(smooth_iters), code, _stream(stream),
+                                  ctypes.byref(h)), "build_subspace")
+    return Subspace(h, lat, block, 2 * half, store_dtype, U.device)
+
+
+def subspace_from_vectors(lat: Lattice, block, vectors: torch.Tensor,
+                          store_dtype: torch.dtype = torch.complex128, stream=None) -> Subspace:
+    """Subspace from given (already split) complex128 fields: block orthonormalisation only."""
+    if vectors.dtype != torch.complex128:
+        raise TypeError("vectors must be complex128")
+    nvec = _nfields(lat, vectors, "vectors")
+    h = ctypes.c_void_p()
+    g = lat.c_geom()
+    code = _lib.HDCR_C128 if store_dtype == torch.complex128 else _lib.HDCR_C64
+    _check(_L.hdcr_subspace_from_vectors(C_ref(g), _block_arr(block), nvec, _dev(vectors, "vectors"),
+                                         code, _stream(stream), ctypes.byref(h)), "subspace_from_vectors")
+    return Subspace(h, lat, block, nvec, store_dtype, vectors.device)
+
+
+def restrict(sub: Subspace, fine: torch.Tensor, stream=None) -> torch.Tensor:
+    """P^dag fine: (nrhs, Vc, nvec) coarse vectors."""
+    n = _nfields(sub.lat, fine, "fine")
+    out = torch.empty((n, sub.Vc, sub.nvec), dtype=fine.dtype, device=fine.device)
+    _check(_L.hdcr_restrict(sub.handle, _dev(fine, "fine"), out.data_ptr(), _code(fine), n,
+                            _stream(stream)), "restrict")
+    return out
+
+
+def prolong(sub: Subspace, coarse: torch.Tensor, stream=None) -> torch.Tensor:
+    """P coarse: (nrhs, V4, 12, Ls) fine fields."""
+    per = sub.Vc * sub.nvec
+    if coarse.numel() % per:
+        raise ValueError("coarse vectors must hold a multiple of Vc*nvec entries")
+    n = coarse.numel() // per
+    out = torch.empty((n, sub.lat.V4, 12, sub.lat.Ls), dtype=coarse.dtype, device=coarse.device)
+    _check(_L.hdcr_prolong(sub.handle, _dev(coarse, "coarse"), out.data_ptr(), _code(coarse), n,
+                           _stream(stream)), "prolong")
+    return out
+
+
+class CoarseOperator:
+    """Little Dirac operator (Eq. 4.5) on the coarse lattice; keeps its subspace alive."""
+
+    def __init__(self, handle, sub: Subspace, dtype: torch.dtype, M5: float, mf: float):
+        self._h = handle
+        self.sub = sub
+        self.dtype = dtype
+        self.M5 = M5
+        self.mf = mf
+
+    @property
+    def handle(self):
+        return self._h
+
+    def op(self, stream=None) -> torch.Tensor:
+        """A as complex128 (Vc, 9, nvec, nvec)."""
+        s = self.sub
+        out = torch.empty((s.Vc, 9, s.nvec, s.nvec), dtype=torch.complex128, device=s.device)
+        _check(_L.hdcr_coarse_get_op(self._h, out.data_ptr(), _stream(stream)), "coarse op")
+        return out
+
+    def close(self):
+        if self._h:
+            _L.hdcr_coarse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_coarse_op(sub: Subspace, U: torch.Tensor, M5: float, mf: float,
+                    op_dtype: torch.dtype = torch.complex128, stream=None) -> CoarseOperator:
+    """A^{ab}_{jk} = <phi_j^a|H|phi_k^b> for the 9 legs of every coarse site (Eq. 4.5)."""
+    if U.dtype != torch.complex128:
+        raise TypeError("build_coarse_op takes complex128 links")
+    h = ctypes.c_void_p()
+    p = _params(M5, mf)
+    code = _lib.HDCR_C128 if op_dtype == torch.complex128 else _lib.HDCR_C64
+    _check(_L.hdcr_build_coarse_op(sub.handle, C_ref(p), _dev(U, "U"), code, _stream(stream),
+                                   ctypes.byref(h)), "build_coarse_op")
+    return CoarseOperator(h, sub, op_dtype, M5, mf)
+
+
+def apply_coarse(co: CoarseOperator, c: torch.Tensor, stream=None) -> torch.Tensor:
+    """9-point coarse stencil applied to (nrhs, Vc, nvec) coarse vectors."""
+    per = co.sub.Vc * co.sub.nvec
+    if c.numel() % per:
+        raise ValueError("coarse vectors must hold a multiple of Vc*nvec entries")
+    out = torch.empty_like(c)
+    _check(_L.hdcr_apply_coarse(co.handle, _dev(c, "c"), _dev(out, "out"), _code(c), c.numel() // per,
+                                _stream(stream)), "apply_coarse")
+    return out
+
+
+def hdcr_solve(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x0: torch.Tensor | None = None,
+               tol: float = 1e-10, max_outer: int = 500, restart: int = 8, smoother_steps: int = 8,
+               coarse_tol: float = 1e-4, coarse_max: int = 1000,
+               inner_dtype: torch.dtype = torch.complex128, stream=None):
+    """H x = b by flexible GCR preconditioned with the two-level V-cycle (Section 4).
+    Returns (x, stats dict); raises HDCRError when the solve fails."""
+    if U.dtype != torch.complex128 or b.dtype != torch.complex128:
+        raise TypeError("hdcr_solve takes complex128 links and source")
+    if _nfields(co.sub.lat, b, "b") != 1:
+        raise ValueError("hdcr_solve takes one right-hand side")
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    prm = _lib.hdcr_solve_params(float(tol), int(max_outer), int(restart), int(smoother_steps),
+                                 float(coarse_tol), int(coarse_max),
+                                 _lib.HDCR_C128 if inner_dtype == torch.complex128 else _lib.HDCR_C64)
+    st = _lib.hdcr_solve_stats()
+    _check(_L.hdcr_solve(co.handle, _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), C_ref(prm), C_ref(st),
+                         _stream(stream)), "hdcr_solve")
+    return x, st.as_dict()

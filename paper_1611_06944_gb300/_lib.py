@@ -43,6 +43,14 @@ class hdcr_solve_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hdcr_solve_params(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("max_outer", C.c_int), ("restart", C.c_int),
+        ("smoother_steps", C.c_int), ("coarse_tol", C.c_double), ("coarse_max", C.c_int),
+        ("inner_dtype", C.c_int),
+    ]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -58,12 +66,24 @@ SIGNATURES = {
     "hdcr_version": (_I, []),
     "hdcr_apply_g5dwf": (_I, [_G, _DP, _P, _P, _P, _I, _I, _P]),
     "hdcr_apply_gamma5_r5": (_I, [_G, _P, _P, _I, _I, _P]),
-    "hdcr_fermion_to_planes": (_I, [_G, _P, _P, _I, _I, _P]),
-    "hdcr_fermion_from_planes": (_I, [_G, _P, _P, _I, _I, _P]),
+    "hdcr_fermion_pack": (_I, [_G, _P, _P, _I, _I, _P]),
+    "hdcr_fermion_unpack": (_I, [_G, _P, _P, _I, _I, _P]),
     "hdcr_convert": (_I, [_P, _I, _P, _I, _SZ, _P]),
     "hdcr_cdot": (_I, [_P, _P, _SZ, _I, _P, _P]),
     "hdcr_norm2": (_I, [_P, _SZ, _I, _P, _P]),
     "hdcr_cr_solve": (_I, [_G, _DP, _P, _P, _P, _I, _D, _I, _ST, _P]),
+    "hdcr_build_subspace": (_I, [_G, _DP, _P, _P, _I, C.POINTER(C.c_int), _I, _I, _P, C.POINTER(_P)]),
+    "hdcr_subspace_from_vectors": (_I, [_G, C.POINTER(C.c_int), _I, _P, _I, _P, C.POINTER(_P)]),
+    "hdcr_subspace_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "hdcr_subspace_get_vectors": (_I, [_P, _P, _P]),
+    "hdcr_subspace_destroy": (None, [_P]),
+    "hdcr_restrict": (_I, [_P, _P, _P, _I, _I, _P]),
+    "hdcr_prolong": (_I, [_P, _P, _P, _I, _I, _P]),
+    "hdcr_build_coarse_op": (_I, [_P, _DP, _P, _I, _P, C.POINTER(_P)]),
+    "hdcr_coarse_get_op": (_I, [_P, _P, _P]),
+    "hdcr_apply_coarse": (_I, [_P, _P, _P, _I, _I, _P]),
+    "hdcr_coarse_destroy": (None, [_P]),
+    "hdcr_solve": (_I, [_P, _P, _P, _P, C.POINTER(hdcr_solve_params), _ST, _P]),
 }
 
 

@@ -43,8 +43,8 @@ int make_geom(const hdcr_geom* gp, Geom* g) {
     set_error("bc_t = %d must be +1 or -1", gp->bc_t);
     return HDCR_ERR_BAD_GEOMETRY;
   }
-  if (v4 > (1LL << 30) || v4 * gp->Ls > (1LL << 40)) {
-    set_error("lattice too large");
+  if (v4 * gp->Ls * 12 >= (1LL << 31)) {
+    set_error("lattice too large: a field must hold fewer than 2^31 complex numbers");
     return HDCR_ERR_BAD_GEOMETRY;
   }
   g->Ls = gp->Ls;

@@ -1,0 +1,538 @@
+// Little Dirac operator A^{ab}_{jk} = <phi_j^a | H | phi_k^b> (Eq. 4.5), its
+// 9-point application, and the restriction / prolongation P^dag, P (Eq. 4.3).
+//
+// Build: for every leg d the stencil is applied to all nvec basis vectors with
+// only the hops that belong to that leg (leg 0: the local terms and the hops
+// that stay inside the block; leg (mu, +-): the single hop that leaves the
+// block towards a +- mu, evaluated on the block face only), then each block
+// projects: A[a][d][j][k] = sum_{x in block a} phi_j(x)^dag Y_k^{(d)}(x).
+// Blocks span the whole fifth dimension, so the s-hops and Gamma5's R5 stay
+// inside a block.  On a coarse extent of 2 the legs +mu and -mu reach the same
+// coarse site and are both kept.
+#include "coarse.cuh"
+#include "dwf_stencil.cuh"
+
+namespace hdcr {
+
+int coarse_check(const hdcr_coarse* co) {
+  if (!co || !co->A || !co->nbr || !co->sub) {
+    set_error("invalid coarse-operator handle");
+    return HDCR_ERR_BAD_ARG;
+  }
+  return HDCR_OK;
+}
+
+// ------------------------------------------------------------ leg stencil
+template <typename R>
+__device__ __forceinline__ bool crosses(const BlockGeom& bg, const int co[4], int mu, int sign) {
+  const int r = co[mu] % bg.b[mu];
+  return sign > 0 ? (r == bg.b[mu] - 1) : (r == 0);
+}
+
+// leg 0: local terms + hops that stay inside the block, every site
+template <typename R>
+__global__ void __launch_bounds__(256) leg_self_kernel(Geom g, BlockGeom bg, R diag, R mf,
+                                                       const cpx<R>* __restrict__ U,
+                                                       const cpx<R>* __restrict__ vecs,
+                                                       cpx<R>* __restrict__ Y, int nvec) {
+  const long long total = g.V5 * nvec;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx / g.V5);
+  const long long i5 = idx - (long long)k * g.V5;
+  const cpx<R>* in = vecs + (long long)k * 12 * g.V5;
+  const int x4 = (int)(i5 / g.Ls);
+  const int s = (int)(i5 - (long long)x4 * g.Ls);
+  int co[4];
+  x4_coords(g, x4, co);
+  cpx<R> acc[4][3];
+  local_part<R, 0>(g, diag, mf, in + fidx(g, 0, i5), s, acc);
+  if (!crosses<R>(bg, co, 0, +1)) hop_full<R, 0, 0, +1>(g, U, in, x4, s, co, acc);
+  if (!crosses<R>(bg, co, 0, -1)) hop_full<R, 0, 0, -1>(g, U, in, x4, s, co, acc);
+  if (!crosses<R>(bg, co, 1, +1)) hop_full<R, 0, 1, +1>(g, U, in, x4, s, co, acc);
+  if (!crosses<R>(bg, co, 1, -1)) hop_full<R, 0, 1, -1>(g, U, in, x4, s, co, acc);
+  if (!crosses<R>(bg, co, 2, +1)) hop_full<R, 0, 2, +1>(g, U, in, x4, s, co, acc);
+  if (!crosses<R>(bg, co, 2, -1)) hop_full<R, 0, 2, -1>(g, U, in, x4, s, co, acc);
+  if (!crosses<R>(bg, co, 3, +1)) hop_full<R, 0, 3, +1>(g, U, in, x4, s, co, acc);
+  if (!crosses<R>(bg, co, 3, -1)) hop_full<R, 0, 3, -1>(g, U, in, x4, s, co, acc);
+  store_g5r5<R, 0>(g, Y + (long long)k * 12 * g.V5, x4, s, acc);
+}
+
+// face site f of leg (MU, SIGN): sites whose MU coordinate is the last (SIGN > 0)
+// or first (SIGN < 0) of its block; f runs over (Lc[MU] * other extents) * Ls
+template <int MU, int SIGN>
+__device__ __forceinline__ long long face_site(const Geom& g, const BlockGeom& bg, long long f, int co[4]) {
+  const int s = (int)(f % g.Ls);
+  long long r = f / g.Ls;
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    const int ext = nu == MU ? bg.Lc[nu] : g.L[nu];
+    int c = (int)(r % ext);
+    r /= ext;
+    if (nu == MU) c = c * bg.b[nu] + (SIGN > 0 ? bg.b[nu] - 1 : 0);
+    co[nu] = c;
+  }
+  return (long long)x4_index(g, co) * g.Ls + s;
+}
+
+template <typename R, int MU, int SIGN>
+__global__ void __launch_bounds__(256) leg_face_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ U,
+                                                       const cpx<R>* __restrict__ vecs,
+                                                       cpx<R>* __restrict__ Y, int nvec) {
+  const long long nf = g.V5 / bg.b[MU];
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nf * nvec) return;
+  const int k = (int)(idx / nf);
+  const long long f = idx - (long long)k * nf;
+  int co[4];
+  const long long i5 = face_site<MU, SIGN>(g, bg, f, co);
+  const int x4 = (int)(i5 / g.Ls);
+  const int s = (int)(i5 - (long long)x4 * g.Ls);
+  const cpx<R>* in = vecs + (long long)k * 12 * g.V5;
+  cpx<R> acc[4][3];
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[sp][c] = cpx<R>((R)0, (R)0);
+  hop_full<R, 0, MU, SIGN>(g, U, in, x4, s, co, acc);
+  store_g5r5<R, 0>(g, Y + (long long)k * 12 * g.V5, x4, s, acc);
+}
+
+// ------------------------------------------------------------ projection
+// local site index l (0 <= l < nsites) of the leg's site set in block a -> fine 5d index
+__device__ __forceinline__ long long leg_local_site(const Geom& g, const BlockGeom& bg, int a, int leg,
+                                                    long long l) {
+  if (leg == 0) return block_site(g, bg, a, l);
+  const int mu = (leg - 1) >> 1;
+  const int sign = ((leg - 1) & 1) ? -1 : +1;
+  // enumerate the block with extent 1 in mu, then place the mu coordinate on the face
+  const int s = (int)(l % g.Ls);
+  long long r = l / g.Ls;
+  int ac[4];
+  coarse_coords(bg, a, ac);
+  int c[4];
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    const int ext = nu == mu ? 1 : bg.b[nu];
+    const int loc = (int)(r % ext);
+    r /= ext;
+    c[nu] = ac[nu] * bg.b[nu] + (nu == mu ? (sign > 0 ? bg.b[nu] - 1 : 0) : loc);
+  }
+  return (long long)x4_index(g, c) * g.Ls + s;
+}
+
+constexpr int PROJ_THREADS = 256;
+constexpr int PROJ_MAXP = 16;  // (j, k) pairs per thread: nvec <= 64
+
+template <typename R>
+__global__ void __launch_bounds__(PROJ_THREADS) project_kernel(Geom g, BlockGeom bg,
+                                                               const cpx<R>* __restrict__ phi,
+                                                               const cpx<R>* __restrict__ Y,
+                                                               cpx<R>* __restrict__ A, int nvec, int leg,
+                                                               int T) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<R>* sphi = reinterpret_cast<cpx<R>*>(smem_raw);   // [nvec][12][T]
+  cpx<R>* sy = sphi + (size_t)nvec * 12 * T;            // [nvec][12][T]
+  const int a = blockIdx.x;
+  const long long fs = g.V5 * 12;
+  const long long nsites = leg == 0 ? bg.K5 : bg.K5 / bg.b[(leg - 1) >> 1];
+  const int npairs = nvec * nvec;
+  double acc[PROJ_MAXP][2];
+#pragma unroll
+  for (int i = 0; i < PROJ_MAXP; ++i) acc[i][0] = acc[i][1] = 0.0;
+  const int nload = nvec * 12 * T;
+  for (long long l0 = 0; l0 < nsites; l0 += T) {
+    const int tn = (int)min((long long)T, nsites - l0);
+    for (int e = threadIdx.x; e < nload; e += PROJ_THREADS) {
+      const int t = e % T;
+      const int c = (e / T) % 12;
+      const int v = e / (12 * T);
+      cpx<R> p((R)0, (R)0), q((R)0, (R)0);
+      if (t < tn) {
+        const long long i5 = leg_local_site(g, bg, a, leg, l0 + t);
+        const long long off = (long long)v * fs + fidx(g, c, i5);
+        p = ld(phi + off);
+        q = ld(Y + off);
+      }
+      sphi[e] = p;
+      sy[e] = q;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PROJ_MAXP; ++i) {
+      const int pr = threadIdx.x + i * PROJ_THREADS;
+      if (pr < npairs) {
+        const int j = pr / nvec, k = pr % nvec;
+        const cpx<R>* pj = sphi + (size_t)j * 12 * T;
+        const cpx<R>* yk = sy + (size_t)k * 12 * T;
+        cpx<R> sum((R)0, (R)0);
+        for (int e = 0; e < 12 * T; ++e) sum = cjmadd(sum, pj[e], yk[e]);
+        acc[i][0] += (double)sum.re;
+        acc[i][1] += (double)sum.im;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < PROJ_MAXP; ++i) {
+    const int pr = threadIdx.x + i * PROJ_THREADS;
+    if (pr < npairs) {
+      const int j = pr / nvec, k = pr % nvec;
+      A[(((long long)a * NLEGS + leg) * nvec + j) * nvec + k] = cpx<R>((R)acc[i][0], (R)acc[i][1]);
+    }
+  }
+}
+
+// ------------------------------------------------------------ coarse apply
+template <typename R>
+__global__ void coarse_apply_kernel(const cpx<R>* __restrict__ A, const int* __restrict__ nbr,
+                                    const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, int Vc, int nvec,
+                                    int nrhs) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)Vc * nvec;
+  if (idx >= n * nrhs) return;
+  const int r = (int)(idx / n);
+  const long long rem = idx - (long long)r * n;
+  const int a = (int)(rem / nvec);
+  const int j = (int)(rem - (long long)a * nvec);
+  const cpx<R>* x = in + (long long)r * n;
+  cpx<R> acc((R)0, (R)0);
+  for (int d = 0; d < NLEGS; ++d) {
+    const cpx<R>* row = A + (((long long)a * NLEGS + d) * nvec + j) * nvec;
+    const cpx<R>* xb = x + (long long)nbr[a * NLEGS + d] * nvec;
+    for (int k = 0; k < nvec; ++k) acc = cmadd(acc, ld(row + k), ld(xb + k));
+  }
+  st(out + idx, acc);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) cdot_re_kernel(const cpx<R>* __restrict__ u,
+                                                              const cpx<R>* __restrict__ v, long long n,
+                                                              RedScratch rs, double* result) {
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> a = ld(u + i), b = ld(v + i);
+    acc[0] += (double)a.re * b.re + (double)a.im * b.im;
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc, rs, tot)) *result = tot[0];
+}
+
+// ------------------------------------------------------------ restrict / prolong
+constexpr int RP_KC = 8;  // basis vectors per restrict CTA
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) restrict_kernel(Geom g, BlockGeom bg,
+                                                               const cpx<R>* __restrict__ phi,
+                                                               const cpx<R>* __restrict__ fine,
+                                                               cpx<R>* __restrict__ coarse, int nvec) {
+  const int a = blockIdx.x;
+  const int k0 = blockIdx.y * RP_KC;
+  const int r = blockIdx.z;
+  const long long fs = g.V5 * 12;
+  const cpx<R>* v = fine + (long long)r * fs;
+  double acc[2 * RP_KC];
+#pragma unroll
+  for (int i = 0; i < 2 * RP_KC; ++i) acc[i] = 0.0;
+  const long long nel = bg.K5 * 12;
+  for (long long e = threadIdx.x; e < nel; e += RED_THREADS) {
+    const int c = (int)(e / bg.K5);
+    const long long l = e - (long long)c * bg.K5;
+    const long long off = fidx(g, c, block_site(g, bg, a, l));
+    const cpx<R> q = ld(v + off);
+#pragma unroll
+    for (int i = 0; i < RP_KC; ++i) {
+      if (k0 + i < nvec) {
+        const cpx<R> p = ld(phi + (long long)(k0 + i) * fs + off);
+        acc[2 * i] += (double)p.re * q.re + (double)p.im * q.im;
+        acc[2 * i + 1] += (double)p.re * q.im - (double)p.im * q.re;
+      }
+    }
+  }
+  block_reduce<2 * RP_KC>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < RP_KC; ++i)
+      if (k0 + i < nvec)
+        coarse[((long long)r * bg.Vc + a) * nvec + k0 + i] = cpx<R>((R)acc[2 * i], (R)acc[2 * i + 1]);
+  }
+}
+
+// fine = fine_in + sum_k phi_k c[a][k]   (fine_in may be null)
+template <typename R>
+__global__ void prolong_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ phi,
+                               const cpx<R>* __restrict__ coarse, const cpx<R>* __restrict__ fine_in,
+                               cpx<R>* __restrict__ fine, int nvec, int nrhs) {
+  const long long fs = g.V5 * 12;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= fs * nrhs) return;
+  const int r = (int)(idx / fs);
+  const long long e = idx - (long long)r * fs;   // element (x4*12 + c)*Ls + s
+  const int x4 = (int)(e / (12LL * g.Ls));
+  int co[4];
+  x4_coords(g, x4, co);
+  int ac[4];
+  for (int mu = 0; mu < 4; ++mu) ac[mu] = co[mu] / bg.b[mu];
+  const int a = ((ac[3] * bg.Lc[2] + ac[2]) * bg.Lc[1] + ac[1]) * bg.Lc[0] + ac[0];
+  const cpx<R>* cf = coarse + ((long long)r * bg.Vc + a) * nvec;
+  cpx<R> acc((R)0, (R)0);
+  if (fine_in) acc = ld(fine_in + idx);
+  for (int k = 0; k < nvec; ++k) acc = cmadd(acc, ld(phi + (long long)k * fs + e), ld(cf + k));
+  st(fine + idx, acc);
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename R>
+int launch_restrict(const hdcr_subspace* sub, const cpx<R>* fine, cpx<R>* coarse, int nrhs, cudaStream_t st) {
+  dim3 grid(sub->bg.Vc, (sub->nvec + RP_KC - 1) / RP_KC, nrhs);
+  restrict_kernel<R><<<grid, RED_THREADS, 0, st>>>(sub->g, sub->bg, (const cpx<R>*)sub->vecs, fine, coarse,
+                                                   sub->nvec);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+template <typename R>
+int launch_prolong(const hdcr_subspace* sub, const cpx<R>* coarse, const cpx<R>* fine_in, cpx<R>* fine,
+                   int nrhs, cudaStream_t st) {
+  const long long n = sub->g.V5 * 12 * nrhs;
+  prolong_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(sub->g, sub->bg, (const cpx<R>*)sub->vecs, coarse,
+                                                        fine_in, fine, sub->nvec, nrhs);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+template <typename R>
+int launch_coarse_apply(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st) {
+  const long long n = (long long)co->bg.Vc * co->nvec * nrhs;
+  coarse_apply_kernel<R><<<num_blocks(n, 128), 128, 0, st>>>((const cpx<R>*)co->A, co->nbr, in, out,
+                                                             co->bg.Vc, co->nvec, nrhs);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+template <typename R>
+int CoarseOp<R>::apply_dot(const cpx<R>* in, cpx<R>* out, RedScratch rs, double* res, cudaStream_t st) const {
+  HDCR_TRY(launch_coarse_apply<R>(co, in, out, 1, st));
+  const long long n = this->n();
+  cdot_re_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(in, out, n, rs, res);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+#define HDCR_INST_COARSE(R)                                                                            \
+  template int launch_restrict<R>(const hdcr_subspace*, const cpx<R>*, cpx<R>*, int, cudaStream_t);   \
+  template int launch_prolong<R>(const hdcr_subspace*, const cpx<R>*, const cpx<R>*, cpx<R>*, int,    \
+                                 cudaStream_t);                                                       \
+  template int launch_coarse_apply<R>(const hdcr_coarse*, const cpx<R>*, cpx<R>*, int, cudaStream_t); \
+  template struct CoarseOp<R>;
+HDCR_INST_COARSE(double)
+HDCR_INST_COARSE(float)
+
+template <typename R, int MU, int SIGN>
+static void launch_leg_face(const Geom& g, const BlockGeom& bg, const cpx<R>* U, const cpx<R>* vecs, cpx<R>* Y,
+                            int nvec, cudaStream_t st) {
+  const long long n = g.V5 / bg.b[MU] * nvec;
+  leg_face_kernel<R, MU, SIGN><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, vecs, Y, nvec);
+}
+
+template <typename R>
+static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>* U, const cpx<R>* phi,
+                    cpx<R>* Y, cpx<R>* A, cudaStream_t st) {
+  const Geom& g = sub->g;
+  const BlockGeom& bg = sub->bg;
+  const int nvec = sub->nvec;
+  int T = (int)(48 * 1024 / (2 * (size_t)nvec * 12 * sizeof(cpx<R>)));
+  if (T < 1) T = 1;
+  if (T > 16) T = 16;
+  const size_t smem = 2 * (size_t)nvec * 12 * T * sizeof(cpx<R>);
+  for (int leg = 0; leg < NLEGS; ++leg) {
+    if (leg == 0) {
+      const long long n = g.V5 * nvec;
+      leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec);
+    } else {
+      switch (leg) {
+        case 1: launch_leg_face<R, 0, +1>(g, bg, U, phi, Y, nvec, st); break;
+        case 2: launch_leg_face<R, 0, -1>(g, bg, U, phi, Y, nvec, st); break;
+        case 3: launch_leg_face<R, 1, +1>(g, bg, U, phi, Y, nvec, st); break;
+        case 4: launch_leg_face<R, 1, -1>(g, bg, U, phi, Y, nvec, st); break;
+        case 5: launch_leg_face<R, 2, +1>(g, bg, U, phi, Y, nvec, st); break;
+        case 6: launch_leg_face<R, 2, -1>(g, bg, U, phi, Y, nvec, st); break;
+        case 7: launch_leg_face<R, 3, +1>(g, bg, U, phi, Y, nvec, st); break;
+        default: launch_leg_face<R, 3, -1>(g, bg, U, phi, Y, nvec, st); break;
+      }
+    }
+    HDCR_LAUNCH_CHECK();
+    project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, leg, T);
+    HDCR_LAUNCH_CHECK();
+  }
+  return HDCR_OK;
+}
+
+}  // namespace hdcr
+
+using namespace hdcr;
+
+extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_params* p, const void* U,
+                                    int op_dtype, void* stream, hdcr_coarse** out) {
+  HDCR_TRY(subspace_check(sub));
+  if (!p || !U || !out) {
+    set_error("hdcr_build_coarse_op: null pointer");
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (op_dtype != HDCR_C128 && op_dtype != HDCR_C64) {
+    set_error("hdcr_build_coarse_op: unknown dtype %d", op_dtype);
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (sub->nvec > 64) {
+    set_error("hdcr_build_coarse_op: nvec = %d above the supported 64", sub->nvec);
+    return HDCR_ERR_BAD_ARG;
+  }
+  *out = nullptr;
+  cudaStream_t st = as_stream(stream);
+  const Geom& g = sub->g;
+  const BlockGeom& bg = sub->bg;
+  const int nvec = sub->nvec;
+  const size_t cb = dtype_complex_bytes(op_dtype);
+  const long long fs = g.V5 * 12;
+  // workspace: Y (nvec fields), and basis / links converted to the build precision when needed
+  const bool conv_phi = sub->dtype != op_dtype;
+  const bool conv_u = op_dtype != HDCR_C128;
+  size_t bytes = cb * (size_t)fs * nvec;
+  if (conv_phi) bytes += cb * (size_t)fs * nvec;
+  if (conv_u) bytes += cb * (size_t)g.V4 * 36;
+  void* work = nullptr;
+  HDCR_CUDA_TRY(cudaMalloc(&work, bytes));
+  char* wp = (char*)work;
+  void* Y = wp;
+  wp += cb * (size_t)fs * nvec;
+  const void* phi = sub->vecs;
+  if (conv_phi) {
+    phi = wp;
+    launch_convert(sub->vecs, sub->dtype, wp, op_dtype, fs * nvec, st);
+    wp += cb * (size_t)fs * nvec;
+  }
+  const void* Ub = U;
+  if (conv_u) {
+    Ub = wp;
+    launch_convert(U, HDCR_C128, wp, op_dtype, (long long)g.V4 * 36, st);
+  }
+  hdcr_coarse* co = new hdcr_coarse();
+  co->sub = sub;
+  co->g = g;
+  co->bg = bg;
+  co->nvec = nvec;
+  co->dtype = op_dtype;
+  co->M5 = p->M5;
+  co->mf = p->mf;
+  cudaGetDevice(&co->device);
+  int s = HDCR_OK;
+  cudaError_t e = cudaMalloc(&co->A, cb * (size_t)bg.Vc * NLEGS * nvec * nvec);
+  if (e == cudaSuccess) e = cudaMalloc(&co->nbr, sizeof(int) * bg.Vc * NLEGS);
+  if (e != cudaSuccess) s = cuda_status(e, "coarse operator storage");
+  if (s == HDCR_OK) {
+    int* hn = new int[bg.Vc * NLEGS];
+    for (int a = 0; a < bg.Vc; ++a) {
+      int c[4];
+      coarse_coords(bg, a, c);
+      hn[a * NLEGS] = a;
+      for (int mu = 0; mu < 4; ++mu)
+        for (int sg = 0; sg < 2; ++sg) {
+          int d[4] = {c[0], c[1], c[2], c[3]};
+          d[mu] = (c[mu] + (sg == 0 ? 1 : -1) + bg.Lc[mu]) % bg.Lc[mu];
+          hn[a * NLEGS + leg_of(mu, sg == 0 ? 1 : -1)] = ((d[3] * bg.Lc[2] + d[2]) * bg.Lc[1] + d[1]) * bg.Lc[0] + d[0];
+        }
+    }
+    e = cudaMemcpyAsync(co->nbr, hn, sizeof(int) * bg.Vc * NLEGS, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    delete[] hn;
+    if (e != cudaSuccess) s = cuda_status(e, "coarse neighbour table");
+  }
+  if (s == HDCR_OK) {
+    if (op_dtype == HDCR_C128)
+      s = build_op<double>(sub, p->M5, p->mf, (const cpx<double>*)Ub, (const cpx<double>*)phi, (cpx<double>*)Y,
+                           (cpx<double>*)co->A, st);
+    else
+      s = build_op<float>(sub, p->M5, p->mf, (const cpx<float>*)Ub, (const cpx<float>*)phi, (cpx<float>*)Y,
+                          (cpx<float>*)co->A, st);
+  }
+  if (s == HDCR_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "coarse operator build");
+  }
+  cudaFree(work);
+  if (s != HDCR_OK) {
+    hdcr_coarse_destroy(co);
+    return s;
+  }
+  *out = co;
+  return HDCR_OK;
+}
+
+extern "C" int hdcr_coarse_get_op(const hdcr_coarse* co, void* out, void* stream) {
+  HDCR_TRY(coarse_check(co));
+  if (!out) {
+    set_error("hdcr_coarse_get_op: null output");
+    return HDCR_ERR_BAD_ARG;
+  }
+  const long long n = (long long)co->bg.Vc * NLEGS * co->nvec * co->nvec;
+  return launch_convert(co->A, co->dtype, out, HDCR_C128, n, as_stream(stream));
+}
+
+extern "C" int hdcr_apply_coarse(const hdcr_coarse* co, const void* in, void* out, int dtype, int nrhs,
+                                 void* stream) {
+  HDCR_TRY(coarse_check(co));
+  if (!in || !out || in == out || nrhs < 1) {
+    set_error("hdcr_apply_coarse: bad pointers or nrhs");
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (dtype != co->dtype) {
+    set_error("hdcr_apply_coarse: vector dtype %d differs from the operator's %d", dtype, co->dtype);
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (dtype == HDCR_C128)
+    return launch_coarse_apply<double>(co, (const cpx<double>*)in, (cpx<double>*)out, nrhs, as_stream(stream));
+  return launch_coarse_apply<float>(co, (const cpx<float>*)in, (cpx<float>*)out, nrhs, as_stream(stream));
+}
+
+extern "C" int hdcr_restrict(const hdcr_subspace* sub, const void* fine, void* coarse, int dtype, int nrhs,
+                             void* stream) {
+  HDCR_TRY(subspace_check(sub));
+  if (!fine || !coarse || nrhs < 1 || nrhs > 65535) {
+    set_error("hdcr_restrict: bad pointers or nrhs");
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (dtype != sub->dtype) {
+    set_error("hdcr_restrict: vector dtype %d differs from the basis storage %d", dtype, sub->dtype);
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (dtype == HDCR_C128)
+    return launch_restrict<double>(sub, (const cpx<double>*)fine, (cpx<double>*)coarse, nrhs, as_stream(stream));
+  return launch_restrict<float>(sub, (const cpx<float>*)fine, (cpx<float>*)coarse, nrhs, as_stream(stream));
+}
+
+extern "C" int hdcr_prolong(const hdcr_subspace* sub, const void* coarse, void* fine, int dtype, int nrhs,
+                            void* stream) {
+  HDCR_TRY(subspace_check(sub));
+  if (!fine || !coarse || nrhs < 1) {
+    set_error("hdcr_prolong: bad pointers or nrhs");
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (dtype != sub->dtype) {
+    set_error("hdcr_prolong: vector dtype %d differs from the basis storage %d", dtype, sub->dtype);
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (dtype == HDCR_C128)
+    return launch_prolong<double>(sub, (const cpx<double>*)coarse, nullptr, (cpx<double>*)fine, nrhs,
+                                  as_stream(stream));
+  return launch_prolong<float>(sub, (const cpx<float>*)coarse, nullptr, (cpx<float>*)fine, nrhs,
+                               as_stream(stream));
+}
+
+extern "C" void hdcr_coarse_destroy(hdcr_coarse* co) {
+  if (!co) return;
+  solve_cache_release(co);
+  if (co->A) cudaFree(co->A);
+  if (co->nbr) cudaFree(co->nbr);
+  delete co;
+}

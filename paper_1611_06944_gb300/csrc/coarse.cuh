@@ -1,0 +1,103 @@
+// Block geometry, subspace and coarse-operator handles (Section 4).
+//
+// A block is b = (bx, by, bz, bt) 4d sites times the whole fifth dimension.
+// Coarse site a = ((tc*Zc + zc)*Yc + yc)*Xc + xc; inside block a the local
+// 5d site l runs with s fastest, then x, y, z, t (so a block row of bx*Ls
+// fine sites is contiguous in every plane).
+#pragma once
+
+#include "krylov.cuh"
+
+namespace hdcr {
+
+constexpr int NLEGS = 9;  // self + 8 nearest coarse neighbours
+
+struct BlockGeom {
+  int b[4];
+  int Lc[4];
+  int Vc;
+  int bvol;
+  long long K5;  // fine 5d sites per block
+};
+
+int make_block_geom(const Geom& g, const int block[4], BlockGeom* out);
+
+__host__ __device__ inline void coarse_coords(const BlockGeom& bg, int a, int c[4]) {
+  c[0] = a % bg.Lc[0];
+  int r = a / bg.Lc[0];
+  c[1] = r % bg.Lc[1];
+  r /= bg.Lc[1];
+  c[2] = r % bg.Lc[2];
+  c[3] = r / bg.Lc[2];
+}
+
+// fine 5d index of local site l of block a
+__host__ __device__ inline long long block_site(const Geom& g, const BlockGeom& bg, int a, long long l) {
+  const int s = (int)(l % g.Ls);
+  long long r = l / g.Ls;
+  int ac[4];
+  coarse_coords(bg, a, ac);
+  int c[4];
+  c[0] = ac[0] * bg.b[0] + (int)(r % bg.b[0]);
+  r /= bg.b[0];
+  c[1] = ac[1] * bg.b[1] + (int)(r % bg.b[1]);
+  r /= bg.b[1];
+  c[2] = ac[2] * bg.b[2] + (int)(r % bg.b[2]);
+  c[3] = ac[3] * bg.b[3] + (int)(r / bg.b[2]);
+  return (long long)x4_index(g, c) * g.Ls + s;
+}
+
+// leg index of the hop to coarse neighbour a + sign*mu
+__host__ __device__ inline int leg_of(int mu, int sign) { return 1 + 2 * mu + (sign > 0 ? 0 : 1); }
+
+}  // namespace hdcr
+
+// Opaque handles of the C ABI.
+struct hdcr_subspace {
+  hdcr::Geom g;
+  hdcr::BlockGeom bg;
+  int nvec;
+  int dtype;      // storage of the basis vectors (HDCR_C128 / HDCR_C64)
+  void* vecs;     // nvec fields, plane layout, block-orthonormal
+  int device;
+};
+
+struct hdcr_coarse {
+  const hdcr_subspace* sub;  // borrowed: must outlive the coarse handle
+  hdcr::Geom g;
+  hdcr::BlockGeom bg;
+  int nvec;
+  int dtype;    // of A
+  void* A;      // [Vc][9][nvec][nvec]
+  int* nbr;     // [Vc][9] coarse site reached by each leg
+  double M5, mf;
+  int device;
+};
+
+namespace hdcr {
+
+// restrict / prolong with vector precision R and basis precision R (same dtype)
+template <typename R>
+int launch_restrict(const hdcr_subspace* sub, const cpx<R>* fine, cpx<R>* coarse, int nrhs, cudaStream_t st);
+// fine = (add ? fine_in : 0) + P coarse
+template <typename R>
+int launch_prolong(const hdcr_subspace* sub, const cpx<R>* coarse, const cpx<R>* fine_in, cpx<R>* fine,
+                   int nrhs, cudaStream_t st);
+template <typename R>
+int launch_coarse_apply(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st);
+
+template <typename R>
+struct CoarseOp {
+  const hdcr_coarse* co;
+  long long n() const { return (long long)co->bg.Vc * co->nvec; }
+  int apply(const cpx<R>* in, cpx<R>* out, cudaStream_t st) const {
+    return launch_coarse_apply<R>(co, in, out, 1, st);
+  }
+  int apply_dot(const cpx<R>* in, cpx<R>* out, RedScratch rs, double* res, cudaStream_t st) const;
+};
+
+int coarse_check(const hdcr_coarse* co);
+void solve_cache_release(const hdcr_coarse* co);  // frees the cached solve workspace
+int subspace_check(const hdcr_subspace* sub);
+
+}  // namespace hdcr

@@ -16,24 +16,28 @@
 
 namespace hdcr {
 
-template <typename R>
-__global__ void __launch_bounds__(RED_THREADS) g5dwf_dot_kernel(Geom g, R diag, R mf,
-                                                                const cpx<R>* __restrict__ U,
-                                                                const cpx<R>* __restrict__ in,
-                                                                cpx<R>* __restrict__ out, RedScratch rs,
-                                                                double* result) {
+template <typename R, int LS>
+__global__ void __launch_bounds__(RED_THREADS, 2) g5dwf_dot_kernel(Geom g, R diag, R mf,
+                                                                   const cpx<R>* __restrict__ U,
+                                                                   const cpx<R>* __restrict__ in,
+                                                                   cpx<R>* __restrict__ out, RedScratch rs,
+                                                                   double* result) {
+  const int ls = ls_of<LS>(g);
   double acc_d[1] = {0.0};
   for (long long i5 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i5 < g.V5;
        i5 += (long long)gridDim.x * blockDim.x) {
+    const int x4 = (int)(i5 / ls);
+    const int s = (int)(i5 - (long long)x4 * ls);
     cpx<R> acc[4][3];
-    dwf_site<R>(g, diag, mf, U, in, i5, acc);
-    store_g5r5<R>(g, out, i5, acc);
-    const long long o5 = reflected(g, i5);
+    dwf_site<R, LS>(g, diag, mf, U, in, x4, s, acc);
+    store_g5r5<R, LS>(g, out, x4, s, acc);
+    // <in, out> at the output site (x4, Ls-1-s), where out = gamma5 acc
+    const cpx<R>* o = in + (unsigned)(x4 * 12 * ls + (ls - 1 - s));
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const cpx<R> a = ld(in + (3 * sp + c) * g.V5 + o5);
+        const cpx<R> a = ld(o + (3 * sp + c) * ls);
         const double sgn = sp >= 2 ? -1.0 : 1.0;
         acc_d[0] += sgn * ((double)a.re * acc[sp][c].re + (double)a.im * acc[sp][c].im);
       }
@@ -191,8 +195,8 @@ void crwork_free(CRWork<R>* w) {
 template <typename R>
 int launch_g5dwf_dot(const Geom& g, double M5, double mf, const cpx<R>* U, const cpx<R>* in,
                      cpx<R>* out, RedScratch rs, double* result, cudaStream_t st) {
-  g5dwf_dot_kernel<R><<<red_blocks(g.V5 * 4), RED_THREADS, 0, st>>>(g, (R)(5.0 - M5), (R)mf, U, in, out,
-                                                                      rs, result);
+  HDCR_DISPATCH_LS(g.Ls, (g5dwf_dot_kernel<R, LSC><<<red_blocks(g.V5 * 4), RED_THREADS, 0, st>>>(
+                             g, (R)(5.0 - M5), (R)mf, U, in, out, rs, result)));
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }

@@ -3,8 +3,10 @@
 //
 // One thread per 5d site (x4, s) with s fastest, so the Ls threads of a 4d
 // site are neighbours in a warp: each gauge link is fetched once per warp
-// (broadcast) and reused across the fifth dimension, and every spinor plane
-// load is a coalesced 8/16-byte access across the warp.  The 4d hops use the
+// (broadcast) and reused across the fifth dimension.  In the field layout
+// psi[x4][c][s] every component load is a run of Ls consecutive complex
+// numbers across those threads (coalesced), at an immediate offset c*Ls from
+// one base address per site when Ls is a compile-time constant.  The 4d hops use the
 // chiral-basis spin projection (two spin components go through the SU(3)
 // multiply instead of four) and the s-hops read only the projected half of
 // the neighbour spinor (P_+ = upper, P_- = lower spins in the chiral basis).
@@ -12,62 +14,63 @@
 
 namespace hdcr {
 
-template <typename R>
-__global__ void __launch_bounds__(256) g5dwf_kernel(Geom g, R diag, R mf,
-                                                    const cpx<R>* __restrict__ U,
-                                                    const cpx<R>* __restrict__ in,
-                                                    cpx<R>* __restrict__ out, int nrhs) {
+template <typename R, int LS>
+__global__ void __launch_bounds__(256, 2) g5dwf_kernel(Geom g, R diag, R mf, const cpx<R>* __restrict__ U,
+                                                       const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
+                                                       int nrhs) {
+  const int ls = ls_of<LS>(g);
   const long long V5 = g.V5;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= V5 * nrhs) return;
   const int r = (int)(idx / V5);
-  const long long i5 = idx - (long long)r * V5;
+  const int i5 = (int)(idx - (long long)r * V5);
+  const int x4 = i5 / ls;
+  const int s = i5 - x4 * ls;
   in += (long long)r * 12 * V5;
   out += (long long)r * 12 * V5;
   cpx<R> acc[4][3];
-  dwf_site<R>(g, diag, mf, U, in, i5, acc);
-  store_g5r5<R>(g, out, i5, acc);
+  dwf_site<R, LS>(g, diag, mf, U, in, x4, s, acc);
+  store_g5r5<R, LS>(g, out, x4, s, acc);
 }
 
 template <typename R>
 __global__ void gamma5_r5_kernel(Geom g, const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
                                  int nfields) {
-  const long long V5 = g.V5;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= V5 * 12 * nfields) return;
-  const long long f = idx / (12 * V5);
-  const long long rem = idx - f * 12 * V5;
-  const int c = (int)(rem / V5);
-  const long long i5 = rem - (long long)c * V5;
-  const int s = (int)(i5 % g.Ls);
-  const long long o5 = i5 - s + (g.Ls - 1 - s);
-  cpx<R> v = ld(in + f * 12 * V5 + rem);
+  // element e = ((f*V4 + x4)*12 + c)*Ls + s in the field layout
+  const long long n = g.V5 * 12 * nfields;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int s = (int)(e % g.Ls);
+  const long long row = e / g.Ls;      // (f*V4 + x4)*12 + c
+  const int c = (int)(row % 12);
+  cpx<R> v = ld(in + e);
   if (c >= 6) v = cpx<R>(-v.re, -v.im);
-  st(out + f * 12 * V5 + (long long)c * V5 + o5, v);
+  st(out + row * g.Ls + (g.Ls - 1 - s), v);
+}
+
+// natural[f][x4][s][c] <-> field[f][x4][c][s]
+template <typename R>
+__global__ void pack_kernel(Geom g, const cpx<R>* __restrict__ nat, cpx<R>* __restrict__ pl, int nfields) {
+  const long long n = g.V5 * 12 * nfields;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // natural order
+  if (idx >= n) return;
+  const int c = (int)(idx % 12);
+  const long long fi5 = idx / 12;     // f*V5 + i5
+  const int s = (int)(fi5 % g.Ls);
+  const long long fx4 = fi5 / g.Ls;   // f*V4 + x4
+  st(pl + (fx4 * 12 + c) * g.Ls + s, ld(nat + idx));
 }
 
 template <typename R>
-__global__ void to_planes_kernel(long long V5, const cpx<R>* __restrict__ nat, cpx<R>* __restrict__ pl,
-                                 int nfields) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // natural order
-  if (idx >= V5 * 12 * nfields) return;
-  const long long f = idx / (12 * V5);
-  const long long rem = idx - f * 12 * V5;
-  const long long i5 = rem / 12;
-  const int c = (int)(rem - i5 * 12);
-  st(pl + f * 12 * V5 + (long long)c * V5 + i5, ld(nat + idx));
-}
-
-template <typename R>
-__global__ void from_planes_kernel(long long V5, const cpx<R>* __restrict__ pl, cpx<R>* __restrict__ nat,
-                                   int nfields) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // natural order
-  if (idx >= V5 * 12 * nfields) return;
-  const long long f = idx / (12 * V5);
-  const long long rem = idx - f * 12 * V5;
-  const long long i5 = rem / 12;
-  const int c = (int)(rem - i5 * 12);
-  st(nat + idx, ld(pl + f * 12 * V5 + (long long)c * V5 + i5));
+__global__ void unpack_kernel(Geom g, const cpx<R>* __restrict__ pl, cpx<R>* __restrict__ nat, int nfields) {
+  const long long n = g.V5 * 12 * nfields;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // natural order
+  if (idx >= n) return;
+  const int c = (int)(idx % 12);
+  const long long fi5 = idx / 12;
+  const int s = (int)(fi5 % g.Ls);
+  const long long fx4 = fi5 / g.Ls;
+  st(nat + idx, ld(pl + (fx4 * 12 + c) * g.Ls + s));
 }
 
 template <typename Ri, typename Ro>
@@ -84,8 +87,8 @@ int launch_g5dwf(const Geom& g, double M5, double mf, const void* U, const void*
                  int nrhs, cudaStream_t st) {
   const int threads = 256;
   const long long n = g.V5 * nrhs;
-  g5dwf_kernel<R><<<num_blocks(n, threads), threads, 0, st>>>(
-      g, (R)(5.0 - M5), (R)mf, (const cpx<R>*)U, (const cpx<R>*)in, (cpx<R>*)out, nrhs);
+  HDCR_DISPATCH_LS(g.Ls, (g5dwf_kernel<R, LSC><<<num_blocks(n, threads), threads, 0, st>>>(
+                             g, (R)(5.0 - M5), (R)mf, (const cpx<R>*)U, (const cpx<R>*)in, (cpx<R>*)out, nrhs)));
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -173,33 +176,33 @@ static int planes_common(const hdcr_geom* gp, const void* a, void* b, int dtype,
   return HDCR_OK;
 }
 
-extern "C" int hdcr_fermion_to_planes(const hdcr_geom* gp, const void* natural, void* planes,
+extern "C" int hdcr_fermion_pack(const hdcr_geom* gp, const void* natural, void* packed,
                                       int dtype, int nfields, void* stream) {
   Geom g;
-  HDCR_TRY(planes_common(gp, natural, planes, dtype, nfields, &g));
+  HDCR_TRY(planes_common(gp, natural, packed, dtype, nfields, &g));
   const long long n = g.V5 * 12 * nfields;
   cudaStream_t st = as_stream(stream);
   if (dtype == HDCR_C128)
-    to_planes_kernel<double><<<num_blocks(n, 256), 256, 0, st>>>(g.V5, (const cpx<double>*)natural,
-                                                                 (cpx<double>*)planes, nfields);
+    pack_kernel<double><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<double>*)natural,
+                                                                 (cpx<double>*)packed, nfields);
   else
-    to_planes_kernel<float><<<num_blocks(n, 256), 256, 0, st>>>(g.V5, (const cpx<float>*)natural,
-                                                                (cpx<float>*)planes, nfields);
+    pack_kernel<float><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<float>*)natural,
+                                                                (cpx<float>*)packed, nfields);
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
 
-extern "C" int hdcr_fermion_from_planes(const hdcr_geom* gp, const void* planes, void* natural,
+extern "C" int hdcr_fermion_unpack(const hdcr_geom* gp, const void* packed, void* natural,
                                         int dtype, int nfields, void* stream) {
   Geom g;
-  HDCR_TRY(planes_common(gp, planes, natural, dtype, nfields, &g));
+  HDCR_TRY(planes_common(gp, packed, natural, dtype, nfields, &g));
   const long long n = g.V5 * 12 * nfields;
   cudaStream_t st = as_stream(stream);
   if (dtype == HDCR_C128)
-    from_planes_kernel<double><<<num_blocks(n, 256), 256, 0, st>>>(g.V5, (const cpx<double>*)planes,
+    unpack_kernel<double><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<double>*)packed,
                                                                    (cpx<double>*)natural, nfields);
   else
-    from_planes_kernel<float><<<num_blocks(n, 256), 256, 0, st>>>(g.V5, (const cpx<float>*)planes,
+    unpack_kernel<float><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<float>*)packed,
                                                                   (cpx<float>*)natural, nfields);
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;

@@ -12,11 +12,20 @@
 //   (1 - gamma_t) psi = (h, -h),            h = u - d
 //   (1 + gamma_t) psi = (h, +h),            h = u + d
 // so each hop multiplies only the two components of h by the link.
+//
+// Field layout psi[x4][c][s] (see hdcr_internal.cuh): a pointer to component 0
+// of site (x4, s) reaches component c at offset c*Ls.  The Ls template
+// parameter LS makes those offsets immediates (LS = 0: runtime Ls).
 #pragma once
 
 #include "hdcr_internal.cuh"
 
 namespace hdcr {
+
+template <int LS>
+__device__ __forceinline__ int ls_of(const Geom& g) {
+  return LS > 0 ? LS : g.Ls;
+}
 
 // (o0, o1) = i sigma_K (w0, w1) for colour vectors w0, w1
 template <typename R, int K>
@@ -58,20 +67,21 @@ __device__ __forceinline__ int neighbour(const Geom& g, const int co[4], int* ph
   return x4_index(g, nc);
 }
 
-// acc += coef * [(1 -+ gamma_mu) U psi(nbr)] for the hop (MU, SIGN) whose neighbour
-// 5d site is j5 and link is Ul (U_mu(x) for SIGN>0, U_mu(x-mu) used as its adjoint for SIGN<0)
+// acc += coef * [(1 -+ gamma_mu) U psi(nbr)] for the hop (MU, SIGN); nb points at
+// component 0 of the neighbour site, Ul at the link (U_mu(x) for SIGN > 0,
+// U_mu(x-mu), used as its adjoint, for SIGN < 0)
 template <typename R, int MU, int SIGN>
-__device__ __forceinline__ void wilson_hop(const cpx<R>* __restrict__ Ul, const cpx<R>* __restrict__ in,
-                                           long long V5, long long j5, R coef, cpx<R> (&acc)[4][3]) {
+__device__ __forceinline__ void wilson_hop(const cpx<R>* __restrict__ Ul, const cpx<R>* __restrict__ nb, int ls,
+                                           R coef, cpx<R> (&acc)[4][3]) {
   cpx<R> h[2][3];
   {
     cpx<R> u0[3], u1[3], d0[3], d1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      u0[c] = ld(in + (0 + c) * V5 + j5);
-      u1[c] = ld(in + (3 + c) * V5 + j5);
-      d0[c] = ld(in + (6 + c) * V5 + j5);
-      d1[c] = ld(in + (9 + c) * V5 + j5);
+      u0[c] = ld(nb + (0 + c) * ls);
+      u1[c] = ld(nb + (3 + c) * ls);
+      d0[c] = ld(nb + (6 + c) * ls);
+      d1[c] = ld(nb + (9 + c) * ls);
     }
     if (MU == 3) {
 #pragma unroll
@@ -132,92 +142,103 @@ __device__ __forceinline__ void wilson_hop(const cpx<R>* __restrict__ Ul, const 
     }
 }
 
-template <typename R, int MU, int SIGN>
+template <typename R, int LS, int MU, int SIGN>
 __device__ __forceinline__ void hop_full(const Geom& g, const cpx<R>* __restrict__ U,
                                          const cpx<R>* __restrict__ in, int x4, int s, const int co[4],
                                          cpx<R> (&acc)[4][3]) {
   int ph;
+  const int ls = ls_of<LS>(g);
   const int y4 = neighbour<MU, SIGN>(g, co, &ph);
-  const cpx<R>* Ul = U + ((long long)MU * g.V4 + (SIGN > 0 ? x4 : y4)) * 9;
-  wilson_hop<R, MU, SIGN>(Ul, in, g.V5, (long long)y4 * g.Ls + s, (R)(-0.5 * ph), acc);
+  const cpx<R>* Ul = U + (unsigned)((MU * g.V4 + (SIGN > 0 ? x4 : y4)) * 9);
+  const cpx<R>* nb = in + (unsigned)(y4 * 12 * ls + s);
+  wilson_hop<R, MU, SIGN>(Ul, nb, ls, (R)(-0.5 * ph), acc);
 }
 
 // The diagonal and fifth-dimension part: acc = (5 - M5) psi(x,s) - P_- psi(x,s+1) - P_+ psi(x,s-1).
-template <typename R>
-__device__ __forceinline__ void local_part(const Geom& g, R diag, R mf, const cpx<R>* __restrict__ in,
-                                           long long i5, int s, cpx<R> (&acc)[4][3]) {
-  const long long V5 = g.V5;
+// self points at component 0 of site (x4, s).
+template <typename R, int LS>
+__device__ __forceinline__ void local_part(const Geom& g, R diag, R mf, const cpx<R>* __restrict__ self, int s,
+                                           cpx<R> (&acc)[4][3]) {
+  const int ls = ls_of<LS>(g);
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[sp][c] = diag * ld(in + (3 * sp + c) * V5 + i5);
+    for (int c = 0; c < 3; ++c) acc[sp][c] = diag * ld(self + (3 * sp + c) * ls);
   {
-    const bool wall = (s + 1 == g.Ls);
-    const long long j = wall ? i5 - (g.Ls - 1) : i5 + 1;
+    const bool wall = (s + 1 == ls);
+    const cpx<R>* p = wall ? self - (ls - 1) : self + 1;
     const R w = wall ? -mf : (R)1;
 #pragma unroll
     for (int sp = 2; sp < 4; ++sp)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        cpx<R> v = ld(in + (3 * sp + c) * V5 + j);
+        cpx<R> v = ld(p + (3 * sp + c) * ls);
         acc[sp][c].re = fma(-w, v.re, acc[sp][c].re);
         acc[sp][c].im = fma(-w, v.im, acc[sp][c].im);
       }
   }
   {
     const bool wall = (s == 0);
-    const long long j = wall ? i5 + (g.Ls - 1) : i5 - 1;
+    const cpx<R>* p = wall ? self + (ls - 1) : self - 1;
     const R w = wall ? -mf : (R)1;
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        cpx<R> v = ld(in + (3 * sp + c) * V5 + j);
+        cpx<R> v = ld(p + (3 * sp + c) * ls);
         acc[sp][c].re = fma(-w, v.re, acc[sp][c].re);
         acc[sp][c].im = fma(-w, v.im, acc[sp][c].im);
       }
   }
 }
 
-// acc = (D_dwf psi)(x4, s) for the 5d site i5 = x4*Ls + s
-template <typename R>
+// acc = (D_dwf psi)(x4, s) for the 5d site (x4, s)
+template <typename R, int LS>
 __device__ __forceinline__ void dwf_site(const Geom& g, R diag, R mf, const cpx<R>* __restrict__ U,
-                                         const cpx<R>* __restrict__ in, long long i5,
-                                         cpx<R> (&acc)[4][3]) {
-  const int s = (int)(i5 % g.Ls);
-  const int x4 = (int)(i5 / g.Ls);
+                                         const cpx<R>* __restrict__ in, int x4, int s, cpx<R> (&acc)[4][3]) {
+  const int ls = ls_of<LS>(g);
   int co[4];
   x4_coords(g, x4, co);
-  local_part<R>(g, diag, mf, in, i5, s, acc);
-  hop_full<R, 0, +1>(g, U, in, x4, s, co, acc);
-  hop_full<R, 0, -1>(g, U, in, x4, s, co, acc);
-  hop_full<R, 1, +1>(g, U, in, x4, s, co, acc);
-  hop_full<R, 1, -1>(g, U, in, x4, s, co, acc);
-  hop_full<R, 2, +1>(g, U, in, x4, s, co, acc);
-  hop_full<R, 2, -1>(g, U, in, x4, s, co, acc);
-  hop_full<R, 3, +1>(g, U, in, x4, s, co, acc);
-  hop_full<R, 3, -1>(g, U, in, x4, s, co, acc);
-}
-
-// 5d index receiving the Gamma5-reflected result of site i5
-__device__ __forceinline__ long long reflected(const Geom& g, long long i5) {
-  const int s = (int)(i5 % g.Ls);
-  return i5 - s + (g.Ls - 1 - s);
+  local_part<R, LS>(g, diag, mf, in + (unsigned)(x4 * 12 * ls + s), s, acc);
+  hop_full<R, LS, 0, +1>(g, U, in, x4, s, co, acc);
+  hop_full<R, LS, 0, -1>(g, U, in, x4, s, co, acc);
+  hop_full<R, LS, 1, +1>(g, U, in, x4, s, co, acc);
+  hop_full<R, LS, 1, -1>(g, U, in, x4, s, co, acc);
+  hop_full<R, LS, 2, +1>(g, U, in, x4, s, co, acc);
+  hop_full<R, LS, 2, -1>(g, U, in, x4, s, co, acc);
+  hop_full<R, LS, 3, +1>(g, U, in, x4, s, co, acc);
+  hop_full<R, LS, 3, -1>(g, U, in, x4, s, co, acc);
 }
 
 // out(x4, Ls-1-s) = gamma5 acc
-template <typename R>
-__device__ __forceinline__ void store_g5r5(const Geom& g, cpx<R>* __restrict__ out, long long i5,
+template <typename R, int LS>
+__device__ __forceinline__ void store_g5r5(const Geom& g, cpx<R>* __restrict__ out, int x4, int s,
                                            const cpx<R> (&acc)[4][3]) {
-  const long long o5 = reflected(g, i5);
+  const int ls = ls_of<LS>(g);
+  cpx<R>* o = out + (unsigned)(x4 * 12 * ls + (ls - 1 - s));
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       cpx<R> v = acc[sp][c];
       if (sp >= 2) v = cpx<R>(-v.re, -v.im);
-      st(out + (3 * sp + c) * g.V5 + o5, v);
+      st(o + (3 * sp + c) * ls, v);
     }
 }
+
+// Dispatch a kernel template on the fifth-dimension extent: LS = 16, 8 or runtime.
+#define HDCR_DISPATCH_LS(ls, KERNEL_CALL) \
+  do {                                    \
+    if ((ls) == 16) {                     \
+      constexpr int LSC = 16;             \
+      KERNEL_CALL;                        \
+    } else if ((ls) == 8) {               \
+      constexpr int LSC = 8;              \
+      KERNEL_CALL;                        \
+    } else {                              \
+      constexpr int LSC = 0;              \
+      KERNEL_CALL;                        \
+    }                                     \
+  } while (0)
 
 }  // namespace hdcr

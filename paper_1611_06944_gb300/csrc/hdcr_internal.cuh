@@ -2,9 +2,11 @@
 // complex arithmetic, error reporting and launch helpers.
 //
 // Field layouts (the C ABI documents the same):
-//   fermion  psi[c][i5], c = 3*spin + colour (12 planes), i5 = x4*Ls + s,
-//            x4 = ((t*Lz + z)*Ly + y)*Lx + x; every entry an interleaved complex.
-//            nrhs fields are stored one after another.
+//   fermion  psi[x4][c][s]: for every 4d site x4 = ((t*Lz + z)*Ly + y)*Lx + x
+//            the 12 components c = 3*spin + colour, each a run of Ls
+//            interleaved complex numbers over the fifth coordinate s.  The
+//            logical 5d site index is i5 = x4*Ls + s; element (c, i5) sits at
+//            fidx(c, i5) = (x4*12 + c)*Ls + s.  nrhs fields follow one another.
 //   gauge    U[mu][x4][a][b], a 3x3 colour matrix per link, row-major.
 //   coarse   c[a][k] (coarse site a, basis index k), op A[a][leg][j][k].
 #pragma once
@@ -58,6 +60,14 @@ __host__ __device__ inline void x4_coords(const Geom& g, int x4, int c[4]) {
 
 __host__ __device__ inline int x4_index(const Geom& g, const int c[4]) {
   return ((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0];
+}
+
+// offset of component c of 5d site i5 in a fermion field (fits in 32 bits: make_geom
+// rejects fields of 2^31 complex numbers or more)
+__host__ __device__ inline unsigned fidx(const Geom& g, int c, long long i5) {
+  const unsigned x4 = (unsigned)(i5 / g.Ls);
+  const unsigned s = (unsigned)(i5 - (long long)x4 * g.Ls);
+  return (x4 * 12u + (unsigned)c) * (unsigned)g.Ls + s;
 }
 
 // --------------------------------------------------------------- complex

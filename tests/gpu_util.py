@@ -7,17 +7,25 @@ import numpy as np
 
 
 def planes(psi: np.ndarray) -> np.ndarray:
-    """natural (..., Lt, Lz, Ly, Lx, Ls, 4, 3) -> planes (..., 12, V5)."""
+    """natural (..., Lt, Lz, Ly, Lx, Ls, 4, 3) -> library layout (..., V4, 12, Ls)."""
     lead = psi.shape[:-7]
-    a = psi.reshape(lead + (-1, 12))
+    Ls = psi.shape[-3]
+    a = psi.reshape(lead + (-1, Ls, 12))
     return np.ascontiguousarray(np.swapaxes(a, -1, -2))
 
 
 def natural(pl: np.ndarray, L, Ls) -> np.ndarray:
-    """planes (..., 12, V5) -> natural (..., Lt, Lz, Ly, Lx, Ls, 4, 3)."""
+    """library layout (..., V4, 12, Ls) -> natural (..., Lt, Lz, Ly, Lx, Ls, 4, 3).
+
+    An array without the (V4, 12, Ls) trailing shape is read as n such fields."""
     Lx, Ly, Lz, Lt = L
-    lead = pl.shape[:-2]
-    a = np.swapaxes(pl, -1, -2)
+    V4 = Lx * Ly * Lz * Lt
+    n = pl.size // (V4 * 12 * Ls)
+    if pl.ndim >= 3 and pl.shape[-3:] == (V4, 12, Ls):
+        lead = pl.shape[:-3]
+    else:
+        lead = (n,) if n > 1 else ()
+    a = np.swapaxes(pl.reshape(lead + (V4, 12, Ls)), -1, -2)
     return np.ascontiguousarray(a.reshape(lead + (Lt, Lz, Ly, Lx, Ls, 4, 3)))
 
 

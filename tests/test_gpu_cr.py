@@ -44,7 +44,8 @@ def test_cr_iterates_match_oracle_step_by_step(hd):
     U = synth.gauge_field(L, 0.3, 1000)
     b = synth.gaussian_fermion(L, Ls, 2000)
     H = lambda v: dwf.apply_H(U, v, 1.8, 0.01)
-    for k in (1, 2, 7, 30):
+    # rounding differences grow with the number of steps on this cond ~ 1e3 system
+    for k, tol in ((1, 1e-14), (2, 1e-14), (7, 1e-13), (30, 1e-11)):
         # the not-converged call leaves its k-th iterate in x
         xd = dev(np.zeros_like(planes(b)))
         with pytest.raises(hd.HDCRError) as e:
@@ -52,7 +53,7 @@ def test_cr_iterates_match_oracle_step_by_step(hd):
                              tol=1e-14, max_iter=k)
         assert e.value.status == -3
         xo, _ = cr(H, b, fixed_iters=k)
-        assert relerr(natural(host(xd), L, Ls), xo) < 1e-12
+        assert relerr(natural(host(xd), L, Ls), xo) < tol
 
 
 def test_cr_fp32_reaches_single_precision(hd):

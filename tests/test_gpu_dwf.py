@@ -112,8 +112,8 @@ def test_gamma5_r5_and_layouts(hd):
     for r in range(2):
         assert relerr(g[r], dwf.gamma5_r5(psi[r])) == 0.0
     nat = dev(psi)
-    assert np.array_equal(host(hd.to_planes(lat, nat)), planes(psi))
-    assert np.array_equal(host(hd.from_planes(lat, pd)), psi)
+    assert np.array_equal(host(hd.pack(lat, nat)), planes(psi))
+    assert np.array_equal(host(hd.unpack(lat, pd)), psi)
     c = hd.convert(pd, torch.complex64)
     assert np.array_equal(host(c), planes(psi).astype(np.complex64))
 

@@ -1,0 +1,187 @@
+"""GPU parity of the two-level pieces (Section 4) against the FP64 oracle:
+subspace, P^dag / P, the little Dirac operator and its 9-point application,
+and the HDCR solve."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dwf, multigrid as mg
+from oracle.krylov import cr
+from gpu_util import dev, host, links, natural, planes, relerr
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+M5 = 1.8
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_1611_06944_gb300 as hd
+    return hd
+
+
+def _oracle_sub(L, Ls, block, nvec, eps, mf, seed, iters=10, bc=1):
+    g = mg.Geometry(L, Ls, block)
+    U = synth.gauge_field(L, eps, seed)
+    noise = synth.gaussian_fermion(L, Ls, seed + 1, count=nvec // 2)
+    sub = mg.build_subspace(U, noise, g, M5, mf, bc, smooth_iters=iters)
+    return g, U, noise, sub
+
+
+# config-1 size (2^4 coarse, legs alias) and a ragged block shape
+SUBSPACE_CASES = [
+    ((4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.3, 0.01, 1),
+    ((6, 4, 2, 4), 5, (3, 2, 1, 2), 4, 0.5, 0.05, -1),
+]
+
+
+@pytest.mark.parametrize("L,Ls,block,nvec,eps,mf,bc", SUBSPACE_CASES)
+def test_build_subspace_matches_oracle(hd, L, Ls, block, nvec, eps, mf, bc):
+    g, U, noise, sub = _oracle_sub(L, Ls, block, nvec, eps, mf, 3000, bc=bc)
+    lat = hd.Lattice(L, Ls, bc)
+    gsub = hd.build_subspace(lat, dev(links(U)), dev(planes(noise)), M5, mf, block, smooth_iters=10)
+    got = natural(host(gsub.vectors()), L, Ls)
+    want = mg.from_blocks(g, sub.Phi)
+    for k in range(nvec):
+        assert relerr(got[k], want[k]) < 1e-10, k
+
+
+def _gpu_sub_from_oracle(hd, lat, g, sub, dtype=None):
+    vec = planes(mg.from_blocks(g, sub.Phi))
+    return hd.subspace_from_vectors(lat, g.block, dev(vec),
+                                    store_dtype=torch.complex128 if dtype is None else dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_restrict_prolong_match_oracle(hd, dtype):
+    L, Ls, block = (4, 6, 4, 4), 4, (2, 3, 2, 2)
+    g, U, noise, sub = _oracle_sub(L, Ls, block, 6, 0.5, 0.05, 3100, iters=3)
+    lat = hd.Lattice(L, Ls)
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    gsub = _gpu_sub_from_oracle(hd, lat, g, sub, tdt)
+    v = synth.gaussian_fermion(L, Ls, 3101, count=2)
+    vd = dev(planes(v), tdt)
+    c = host(hd.restrict(gsub, vd)).astype(np.complex128)
+    tol = 1e-13 if dtype == "c128" else 1e-5
+    for r in range(2):
+        assert relerr(c[r], mg.restrict(sub, v[r])) < tol
+    rng = synth.rng(3102)
+    cc = rng.standard_normal((g.Vc, 6)) + 1j * rng.standard_normal((g.Vc, 6))
+    f = natural(host(hd.prolong(gsub, dev(cc, tdt))).astype(np.complex128), L, Ls)
+    assert relerr(f, mg.prolong(sub, cc)) < tol
+    # P^dag P = 1: restricting the basis itself gives the identity in every block
+    basis = gsub.vectors().to(tdt)
+    gram = host(hd.restrict(gsub, basis)).astype(np.complex128)       # (k, a, j)
+    assert np.abs(gram - np.eye(6)[:, None, :]).max() < (1e-13 if dtype == "c128" else 1e-5)
+
+
+COARSE_CASES = [
+    ((4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.3, 0.01, 1),       # 2^4 coarse: +mu and -mu legs alias
+    ((6, 6, 4, 4), 4, (2, 2, 2, 2), 4, 0.5, 0.05, -1),      # extents 3 and 2 mixed
+]
+
+
+@pytest.mark.parametrize("L,Ls,block,nvec,eps,mf,bc", COARSE_CASES)
+def test_coarse_op_matches_oracle(hd, L, Ls, block, nvec, eps, mf, bc):
+    g, U, noise, sub = _oracle_sub(L, Ls, block, nvec, eps, mf, 3200, iters=4, bc=bc)
+    lat = hd.Lattice(L, Ls, bc)
+    gsub = _gpu_sub_from_oracle(hd, lat, g, sub)
+    A = mg.coarse_op(U, sub, M5, mf, bc)
+    co = hd.build_coarse_op(gsub, dev(links(U)), M5, mf)
+    assert relerr(host(co.op()), A) < 1e-12
+    # the 9-point application
+    rng = synth.rng(3201)
+    c = rng.standard_normal((g.Vc, nvec)) + 1j * rng.standard_normal((g.Vc, nvec))
+    y = host(hd.apply_coarse(co, dev(c)))
+    assert relerr(y, mg.coarse_apply(A, g, c)) < 1e-13
+    # FP32 build from the same basis
+    gsub32 = _gpu_sub_from_oracle(hd, lat, g, sub, torch.complex64)
+    co32 = hd.build_coarse_op(gsub32, dev(links(U)), M5, mf, op_dtype=torch.complex64)
+    assert relerr(host(co32.op()), A) < 1e-5
+    y32 = host(hd.apply_coarse(co32, dev(c, torch.complex64))).astype(np.complex128)
+    assert relerr(y32, mg.coarse_apply(A, g, c)) < 1e-5
+
+
+def test_coarse_op_properties_full_size(hd):
+    """16^4 x 16, 4^4 blocks, nvec = 24 (the two-level FP64 workload): properties
+    that hold at any size -- Galerkin identity A c = P^dag H P c, Hermitian legs,
+    orthonormal blocks."""
+    L, Ls, block, nvec = (16, 16, 16, 16), 16, (4, 4, 4, 4), 24
+    lat = hd.Lattice(L, Ls)
+    U = dev(links(synth.gauge_field(L, 0.5, 3300)))
+    noise = dev(planes(synth.gaussian_fermion(L, Ls, 3301, count=nvec // 2)))
+    sub = hd.build_subspace(lat, U, noise, M5, 0.01, block, smooth_iters=10)
+    del noise
+    co = hd.build_coarse_op(sub, U, M5, 0.01)
+    A = host(co.op())
+    gc = mg.Geometry(L, Ls, block)
+    idx = np.arange(gc.Vc)
+    assert np.abs(A[:, 0] - np.conj(np.swapaxes(A[:, 0], -1, -2))).max() < 1e-12 * np.abs(A).max()
+    for mu in range(4):
+        nb = mg.coarse_neighbour(idx[:, None], gc, mu, +1)[:, 0]
+        d = A[:, mg.leg_index(mu, 1)] - np.conj(np.swapaxes(A[nb, mg.leg_index(mu, -1)], -1, -2))
+        assert np.abs(d).max() < 1e-12 * np.abs(A).max()
+    rng = synth.rng(3302)
+    c = rng.standard_normal((gc.Vc, nvec)) + 1j * rng.standard_normal((gc.Vc, nvec))
+    cd = dev(c)
+    lhs = host(hd.apply_coarse(co, cd))
+    rhs = host(hd.restrict(sub, hd.apply_g5dwf(lat, U, hd.prolong(sub, cd), M5, 0.01)))
+    assert relerr(lhs, rhs) < 1e-12
+    gram = host(hd.restrict(sub, sub.vectors()))
+    assert np.abs(gram - np.eye(nvec)[:, None, :]).max() < 1e-12
+
+
+def test_subspace_errors(hd):
+    L, Ls = (4, 4, 4, 4), 4
+    lat = hd.Lattice(L, Ls)
+    U = dev(links(synth.gauge_field(L, 0.3, 1)))
+    noise = dev(planes(synth.gaussian_fermion(L, Ls, 2, count=2)))
+    with pytest.raises(hd.HDCRError) as e:
+        hd.build_subspace(lat, U, noise, M5, 0.01, (3, 2, 2, 2))
+    assert e.value.status == -2
+    with pytest.raises(hd.HDCRError) as e:
+        hd.build_subspace(lat, U, noise, M5, 0.01, (4, 2, 2, 2))      # coarse extent 1
+    assert e.value.status == -2
+    v = synth.gaussian_fermion(L, Ls, 3, count=1)
+    dup = planes(np.concatenate([v, v]))
+    with pytest.raises(hd.HDCRError) as e:
+        hd.subspace_from_vectors(lat, (2, 2, 2, 2), dev(dup))
+    assert e.value.status == -5
+
+
+@pytest.mark.parametrize("inner", ["c128", "c64"])
+def test_hdcr_solve_tiny_workload(hd, inner):
+    """4^4 x 8, eps = 0.3, mf = 0.01, 2^4 blocks, nvec = 8: HDCR to a true residual of
+    1e-10 (checked by the oracle) and the same solution as the oracle's CR."""
+    L, Ls, block, nvec, mf = (4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.01
+    lat = hd.Lattice(L, Ls)
+    Uh = synth.gauge_field(L, 0.3, 1000)
+    U = dev(links(Uh))
+    noise = dev(planes(synth.gaussian_fermion(L, Ls, 3001, count=nvec // 2)))
+    tdt = torch.complex128 if inner == "c128" else torch.complex64
+    sub = hd.build_subspace(lat, U, noise, M5, mf, block, smooth_iters=10, store_dtype=tdt)
+    co = hd.build_coarse_op(sub, U, M5, mf, op_dtype=tdt)
+    b = synth.gaussian_fermion(L, Ls, 2000)
+    x, st = hd.hdcr_solve(co, U, dev(planes(b)), tol=1e-10, inner_dtype=tdt)
+    assert st["status"] == 0 and st["true_resid"] <= 1e-10
+    xg = natural(host(x), L, Ls)
+    r = b - dwf.apply_H(Uh, xg, M5, mf)
+    assert np.sqrt(dwf.norm2(r) / dwf.norm2(b)) <= 1.01e-10
+    xo, _ = cr(lambda v: dwf.apply_H(Uh, v, M5, mf), b, tol=1e-12, maxiter=50000)
+    assert relerr(xg, xo) < 1e-6
+    assert st["coarse_matvecs"] > 0 and st["iters"] > 0
+
+
+def test_hdcr_solve_reports_cap(hd):
+    L, Ls, block, nvec, mf = (4, 4, 4, 4), 4, (2, 2, 2, 2), 4, 0.01
+    lat = hd.Lattice(L, Ls)
+    U = dev(links(synth.gauge_field(L, 0.3, 1000)))
+    noise = dev(planes(synth.gaussian_fermion(L, Ls, 3001, count=2)))
+    sub = hd.build_subspace(lat, U, noise, M5, mf, block)
+    co = hd.build_coarse_op(sub, U, M5, mf)
+    b = dev(planes(synth.gaussian_fermion(L, Ls, 2000)))
+    with pytest.raises(hd.HDCRError) as e:
+        hd.hdcr_solve(co, U, b, tol=1e-12, max_outer=2)
+    assert e.value.status == -3
