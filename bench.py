@@ -1,0 +1,445 @@
+#!/usr/bin/env python
+"""Benchmark: HDCR time-to-1e-10 against plain FP64 CR, and the fine-stencil bandwidth.
+
+Workload (the two-level FP64 configuration): 16^4 lattice, Ls = 16, synthetic
+links U = exp(i eps H) with eps = 0.5, M5 = 1.8, mf = 0.01, one Gaussian
+source; nvec = 24 subspace vectors on 4^4 blocks (a 4^4 coarse lattice).
+
+One step = one pass of the whole hot path on that input:
+  subspace (Chebyshev low-pass filter of 12 Gaussian noise fields, Gamma5 split,
+  FP64 block Gram-Schmidt) -> little Dirac operator (FP64 build, dense inverse)
+  -> HDCR solve (FP64 flexible GCR, V-cycle with the order-10 Chebyshev
+  smoother and the exact coarse solve) to a true residual of 1e-10
+  -> the gauge-link force of the solution.
+``value`` is seconds per step (lower is better).  Beside it the JSON line
+reports plain FP64 CR to the same tolerance on the same GPU, the FP32-inner
+variant, the FP32 stencil bandwidth against the measured HBM peak, the
+roofline of the dominant kernel, the CPU oracle baseline, the end-to-end time
+through host buffers, SM clocks during the timed region and the number of
+library kernels launched.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (the solve does not
+shard across GPUs here); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HDCR time-to-1e-10 vs plain FP64 CR on same GB300; Γ5Ddwf GB/s as % HBM peak"
+L_FINE = (16, 16, 16, 16)
+LS = 16
+EPS = 0.5
+M5 = 1.8
+MF = 0.01
+NVEC = 24
+BLOCK = (4, 4, 4, 4)
+SEED_GAUGE, SEED_SRC, SEED_NOISE = 1001, 2001, 3001
+FILTER = dict(kind="chebyshev", order=300, lam_cut=0.3, lam_max=8.0)
+SOLVE = dict(tol=1e-10, restart=8, smoother="chebyshev", smoother_order=10, cheb_lo=1.0, cheb_hi=64.0,
+             coarse_solver="dense", max_outer=200)
+# floating-point operations per 5d site of one application of H as the kernel
+# executes them (FMA = 2): 8 hops x (12 projection + 144 SU(3) + 48 accumulate)
+# + 72 for the diagonal and the fifth-dimension hops
+FLOPS_PER_SITE = 8 * (12 + 144 + 48) + 72
+# algorithmic bytes per 5d site of one application (read psi, write H psi, links / Ls)
+def bytes_per_site(real_bytes: int, Ls: int) -> float:
+    return 2 * 12 * 2 * real_bytes + 4 * 9 * 2 * real_bytes / Ls
+FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal, profiling recipe)
+# DRAM traffic of one FP64 / FP32 stencil launch at 16^4 x 16 from ncu, with the hash of
+# the stencil sources it was measured on (reported as null once the sources change)
+NCU_TRAFFIC = {"f64": None, "f32": None, "src_hash": None}
+
+
+def stencil_src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("dwf_stencil.cuh", "dwf.cu", "hdcr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1611_06944_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def _cuda() -> bool:
+    import torch
+    return torch.cuda.is_available()
+
+
+def aggregate(elapsed_s: float, units: int, world: int) -> dict:
+    """Whole-job figures from this rank's timed seconds: the max over ranks, and the
+    total units processed by all ranks (each rank runs ``units`` steps)."""
+    t = elapsed_s
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        x = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    total_units = units * world
+    return {"max_seconds": t, "total_units": total_units, "seconds_per_unit": t / total_units}
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ workload
+def make_inputs(device: str):
+    import numpy as np
+    import torch
+
+    import synth
+    lat_L = L_FINE
+    U = synth.gauge_field(lat_L, EPS, SEED_GAUGE)
+    plaq = synth.plaquette(U)
+    Uh = torch.from_numpy(np.ascontiguousarray(U.reshape(4, -1, 3, 3)))
+    b = synth.gaussian_fermion(lat_L, LS, SEED_SRC)
+    noise = synth.gaussian_fermion(lat_L, LS, SEED_NOISE, count=NVEC // 2)
+    # natural (…, Lt, Lz, Ly, Lx, Ls, 4, 3) -> library layout (…, V4, 12, Ls)
+    def pack(a):
+        lead = a.shape[:-7]
+        return np.ascontiguousarray(np.swapaxes(a.reshape(lead + (-1, LS, 12)), -1, -2))
+    bh = torch.from_numpy(pack(b))
+    nh = torch.from_numpy(pack(noise))
+    return Uh, bh, nh, plaq
+
+
+def hdcr_step(hd, lat, U, b, noise, inner="f64"):
+    """One pass of the hot path; returns (x, stats dict)."""
+    import torch
+    tdt = torch.complex128 if inner == "f64" else torch.complex64
+    sub = hd.build_subspace(lat, U, noise, M5, MF, BLOCK, filter_dtype=torch.complex64, store_dtype=tdt,
+                            **FILTER)
+    co = hd.build_coarse_op(sub, U, M5, MF, op_dtype=tdt)
+    hd.coarse_invert(co)
+    x, st = hd.hdcr_solve(co, U, b, inner_dtype=tdt, **SOLVE)
+    F = hd.gauge_force(lat, x, hd.apply_gamma5_r5(lat, x))
+    co.close()
+    sub.close()
+    return x, F, st
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1611_06944_gb300 as hd
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    lat = hd.Lattice(L_FINE, LS, 1)
+    Uh, bh, nh, plaq = make_inputs(dev)
+    U, b, noise = Uh.to(dev), bh.to(dev), nh.to(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        hdcr_step(hd, lat, U, b, noise)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    hd.stencil_timer(True)
+    n0 = hd.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        x, F, st = hdcr_step(hd, lat, U, b, noise)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = hd.launch_count() - n0
+    clk = clocks.stop()
+    st64 = hd.stencil_timer_read(torch.complex128)
+    st32 = hd.stencil_timer_read(torch.complex64)
+    hd.stencil_timer(False)
+    barrier(world)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    agg = aggregate(elapsed, args.steps, world)
+    if rank != 0:
+        return None
+    # ---------------------------------------------------------- comparisons (outside the timed region)
+    x_cr = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x_cr, st_cr = hd.cr_solve(lat, U, b, M5, MF, tol=1e-10, max_iter=100000)
+    torch.cuda.synchronize()
+    t_cr = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, st_mixed = hdcr_step(hd, lat, U, b, noise, inner="f32")
+    torch.cuda.synchronize()
+    t_mixed = time.perf_counter() - t0
+    sol_diff = float(torch.linalg.vector_norm(x - x_cr) / torch.linalg.vector_norm(x_cr))
+    # FP32 stencil bandwidth (the second half of the metric)
+    U32, b32 = U.to(torch.complex64), b.to(torch.complex64)
+    y32 = torch.empty_like(b32)
+    for _ in range(3):
+        hd.apply_g5dwf(lat, U32, b32, M5, MF, out=y32)
+    torch.cuda.synchronize()
+    hd.stencil_timer(True)
+    for _ in range(50):
+        hd.apply_g5dwf(lat, U32, b32, M5, MF, out=y32)
+    torch.cuda.synchronize()
+    s32 = hd.stencil_timer_read(torch.complex64)
+    hd.stencil_timer(False)
+    pk = peaks()
+    bps32 = bytes_per_site(4, LS)
+    gbs32 = s32["sites"] * bps32 / (s32["ms"] * 1e-3) / 1e9
+    # ---------------------------------------------------------- roofline of the dominant kernel
+    same_src = NCU_TRAFFIC["src_hash"] == stencil_src_hash()
+    ms64 = st64["ms"] / max(st64["launches"], 1)
+    sites64 = st64["sites"] / max(st64["launches"], 1)
+    achieved = FLOPS_PER_SITE * sites64 / (ms64 * 1e-3) / 1e12
+    share64 = st64["ms"] / (elapsed * 1e3)
+    roofline = {"bound": "alu", "kernel": "g5dwf FP64 (H = Gamma5 D_dwf)", "achieved": round(achieved, 4),
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": NCU_TRAFFIC["f64"] if same_src else None,
+                "flops_per_site": FLOPS_PER_SITE, "avg_launch_ms": round(ms64, 4),
+                "share_of_step": round(share64, 3),
+                "peak_note": "FP64 nominal of the profiling recipe (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+    # ---------------------------------------------------------- e2e through host buffers
+    e2e = run_e2e(hd, lat, Uh, bh, nh, stream)
+    mv_step = stats[-1]["fine_matvecs"] + stats[-1]["fine_matvecs_lo"]
+    cpu = cpu_baseline(args, mv_step) if world == 1 else None
+    line = {
+        "metric": METRIC,
+        "value": round(agg["seconds_per_unit"], 4),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(agg["max_seconds"] * 1e3 / args.steps, 2),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "two-level FP64: 16^4 x 16 DWF, eps=0.5, M5=1.8, mf=0.01, 1 Gaussian source, "
+                        "nvec=24, 4^4 blocks (4^4 coarse)",
+            "plaquette": round(plaq, 4),
+            "step": "Chebyshev-filter subspace (order 300, FP32 filter, FP64 Gram-Schmidt) + FP64 coarse op "
+                    "+ dense coarse inverse + FP64 HDCR solve to 1e-10 + gauge force",
+            "l2": "inputs larger than L2 (201 MB per FP64 field)",
+            "parallelism": f"replicas x{world}",
+        },
+        "hdcr": {"outer_iters": stats[-1]["iters"], "fine_matvecs": stats[-1]["fine_matvecs"],
+                 "coarse_solves": stats[-1]["coarse_matvecs"], "true_resid": stats[-1]["true_resid"],
+                 "solve_s": round(stats[-1]["t_total"], 4), "smoother_s": round(stats[-1]["t_smoother"], 4),
+                 "coarse_s": round(stats[-1]["t_coarse"], 4)},
+        "plain_fp64_cr": {"seconds": round(t_cr, 4), "iters": st_cr["iters"], "true_resid": st_cr["true_resid"],
+                          "speedup_of_hdcr_step": round(t_cr / agg["seconds_per_unit"], 3),
+                          "solution_rel_diff": sol_diff},
+        "hdcr_fp32_inner": {"seconds": round(t_mixed, 4), "outer_iters": st_mixed["iters"],
+                            "true_resid": st_mixed["true_resid"], "fine_matvecs_f64": st_mixed["fine_matvecs"],
+                            "fine_matvecs_f32": st_mixed["fine_matvecs_lo"]},
+        "g5dwf_fp32": {"GBs": round(gbs32, 1), "frac_of_hbm": round(gbs32 / pk["hbm_gbs"], 4),
+                       "hbm_peak_gbs": pk["hbm_gbs"], "peak_source": pk["source"],
+                       "bytes_per_site": bps32, "avg_launch_us": round(s32["ms"] / s32["launches"] * 1e3, 2),
+                       "traffic": NCU_TRAFFIC["f32"] if same_src else None},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    return line
+
+
+def run_e2e(hd, lat, Uh, bh, nh, stream) -> dict:
+    """The same step through host buffers: pinned host -> device copies of the step's
+    inputs and a device -> host read of the solution inside the timed region."""
+    import torch
+    Up, bp, npin = Uh.pin_memory(), bh.pin_memory(), nh.pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    U = Up.to(dev, non_blocking=True)
+    b = bp.to(dev, non_blocking=True)
+    noise = npin.to(dev, non_blocking=True)
+    x, F, st = hdcr_step(hd, lat, U, b, noise)
+    xh.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    h2d = (Uh.numel() + bh.numel() + nh.numel()) * 16
+    return {"value": round(t, 4), "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(bh.numel() * 16)}
+
+
+def cpu_baseline(args, mv_step: int) -> dict:
+    """The FP64 numpy oracle on this host: a bounded sample (applications of H on the
+    full lattice) scaled to one step by the step's fine-matvec count."""
+    import numpy as np
+
+    import synth
+    from oracle import dwf
+    U = synth.gauge_field(L_FINE, EPS, SEED_GAUGE)
+    b = synth.gaussian_fermion(L_FINE, LS, SEED_SRC)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        dwf.apply_H(U, b, M5, MF)
+        reps += 1
+        if time.perf_counter() - t0 > 10.0 or reps >= 8:
+            break
+    per = (time.perf_counter() - t0) / reps
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": round(per * mv_step, 2), "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} oracle applications of H at 16^4x16 ({per:.2f} s each) x {mv_step} fine matvecs "
+                      "per GPU step (lower bound: the oracle's setup and BLAS are not counted)",
+            "threads_note": "numpy, single process"}
+
+
+def run_reference(args, world, rank):
+    """The oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import synth
+    from oracle import dwf
+    U = synth.gauge_field(L_FINE, EPS, SEED_GAUGE)
+    b = synth.gaussian_fermion(L_FINE, LS, SEED_SRC)
+    # matvecs of one HDCR step: the subspace filter (NVEC/2 x 2 x order), the solve
+    # (measured about 45 per outer iteration, ~15 outer iterations) and the coarse build
+    mv_step = NVEC // 2 * 2 * FILTER["order"] + 45 * 15 + 2 * NVEC
+    for _ in range(args.warmup):
+        dwf.apply_H(U, b, M5, MF)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        dwf.apply_H(U, b, M5, MF)
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    v = round(per * mv_step, 2)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 2),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "two-level FP64: 16^4 x 16 DWF, eps=0.5, M5=1.8, mf=0.01, nvec=24, 4^4 blocks"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: one oracle application of H at 16^4x16, scaled by "
+                                       f"{mv_step} matvecs per HDCR step"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args(argv)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        import __graft_entry__  # noqa: F401  (puts the repo on sys.path)
+        line = run_ours(args, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

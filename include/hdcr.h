@@ -89,6 +89,17 @@ typedef struct {
 const char* hdcr_strerror(int status);
 const char* hdcr_last_error(void);
 int hdcr_version(void); /* 10000*major + 100*minor + patch */
+/* Number of CUDA kernels the library has launched in this process (all
+ * devices, all threads); a diagnostic for counting launches per step. */
+unsigned long long hdcr_launch_count(void);
+/* Stencil timer: hdcr_stencil_timer(1) resets and starts recording CUDA
+ * events around every application of H (on the launching stream, at most
+ * 16384 launches); hdcr_stencil_timer(0) stops.  hdcr_stencil_timer_read adds
+ * up the recorded launches of one precision (HDCR_C128 or HDCR_C64): total
+ * device milliseconds, number of launches and 5d sites processed.  It waits
+ * for the recorded events. */
+int hdcr_stencil_timer(int enable);
+int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* launches, long long* sites);
 
 /* ---------------------------------------------------------------- fine operator
  * hdcr_apply_g5dwf: out = H in with H = Gamma5 D_dwf = gamma5 R5 D_dwf
@@ -146,9 +157,15 @@ int hdcr_cr_solve(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
 /* ---------------------------------------------------------------- subspace
  * hdcr_build_subspace: the near-null-space basis of Section 4.
  *   1. each of the nvec/2 Gaussian noise fields (``noise``: nvec/2 C128
- *      fields, drawn by the caller) gets ``smooth_iters`` conjugate-residual
- *      steps on H x = 0 ("inverse iteration applied to Gaussian noise") and is
- *      normalised;
+ *      fields, drawn by the caller) is filtered towards the low modes of H and
+ *      normalised, by one of the paper's approaches (Section 4):
+ *        HDCR_SUBSPACE_CR_SMOOTH  ``order`` conjugate-residual steps on H x = 0
+ *                                 from the noise ("inverse iteration applied to
+ *                                 Gaussian noise");
+ *        HDCR_SUBSPACE_CHEBYSHEV  the Chebyshev low-pass filter of Fig. 1,
+ *                                 T_order(t(H^2)) x with t mapping
+ *                                 [lam_cut^2, lam_max^2] onto [-1, 1];
+ *      in ``filter_dtype`` precision;
  *   2. chiral split with Gamma5 = gamma5 R5: v -> (1 + Gamma5) v / 2 and
  *      (1 - Gamma5) v / 2 (the nvec/2 "+" vectors first, then the "-" ones);
  *   3. restriction to blocks of block[0..3] sites times the full fifth
@@ -161,11 +178,25 @@ int hdcr_cr_solve(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
  * after orthogonalisation: |v| < 1e-12 |v0|), CUDA, NO_MEMORY.
  * Synchronises ``stream``.  On success *out receives a new handle.
  */
+#define HDCR_SUBSPACE_CR_SMOOTH 0
+#define HDCR_SUBSPACE_CHEBYSHEV 1
+
+typedef struct {
+  int nvec;           /* basis size after the chiral split (even)            */
+  int block[4];       /* block extents bx, by, bz, bt                        */
+  int kind;           /* HDCR_SUBSPACE_CR_SMOOTH or HDCR_SUBSPACE_CHEBYSHEV  */
+  int order;          /* CR steps, or Chebyshev polynomial order (>= 1)      */
+  double lam_cut;     /* Chebyshev filter: |lambda| below which modes grow   */
+  double lam_max;     /* Chebyshev filter: upper edge of the spectrum of |H| */
+  int filter_dtype;   /* precision of step 1: HDCR_C128 or HDCR_C64          */
+  int store_dtype;    /* storage of the basis: HDCR_C128 or HDCR_C64         */
+} hdcr_subspace_params;
+
 typedef struct hdcr_subspace hdcr_subspace;
 int hdcr_build_subspace(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
-                        const void* noise, int nvec, const int block[4], int smooth_iters,
-                        int store_dtype, void* stream, hdcr_subspace** out);
-/* The same from nvec given fields (C128, already split): steps 3-4 only. */
+                        const void* noise, const hdcr_subspace_params* sp, void* stream,
+                        hdcr_subspace** out);
+/* A subspace from nvec given fields (C128, already split): steps 3-4 only. */
 int hdcr_subspace_from_vectors(const hdcr_geom* g, const int block[4], int nvec,
                                const void* vectors, int store_dtype, void* stream,
                                hdcr_subspace** out);
@@ -200,34 +231,74 @@ int hdcr_coarse_get_op(const hdcr_coarse* co, void* out, void* stream);
 /* out[r][a] = sum_leg A[a][leg] in[r][a + leg], 9-point coarse stencil; dtype = op dtype. */
 int hdcr_apply_coarse(const hdcr_coarse* co, const void* in, void* out, int dtype, int nrhs,
                       void* stream);
+/* Dense inverse of the coarse operator (the whole (Vc*nvec)^2 matrix, FP32
+ * complex, Gauss-Jordan elimination with partial pivoting), kept in the handle
+ * and used by hdcr_solve's HDCR_COARSE_DENSE solver.  Q = P A^{-1} P^dag of
+ * Eq. 4.6 applied exactly up to FP32 rounding.  Memory: 8 (Vc*nvec)^2 bytes.
+ * Synchronises ``stream``.  Errors: BAD_ARG (Vc*nvec > 32768), NONFINITE
+ * (singular pivot), CUDA, NO_MEMORY. */
+int hdcr_coarse_invert(hdcr_coarse* co, void* stream);
+/* out = A^{-1} in (C64, nrhs coarse vectors) with the dense inverse. */
+int hdcr_coarse_solve_dense(const hdcr_coarse* co, const void* in, void* out, int nrhs,
+                            void* stream);
 void hdcr_coarse_destroy(hdcr_coarse* co);
 
 /* ---------------------------------------------------------------- HDCR solve
  * hdcr_solve: H x = b (Section 4) by flexible GCR(restart) in FP64 on H,
  * preconditioned by the two-level V-cycle
- *     z1 = S r;  z2 = z1 + P A^{-1} P^dag (r - H z1);  z = z2 + S (r - H z2),
- * S = ``smoother_steps`` CR steps from zero, A^{-1} = CR on the coarse operator
- * to ``coarse_tol`` (cap ``coarse_max``).  For a fixed linear smoother and an
- * exact coarse solve this is the composite M_outer = S P_L + P_R S + Q - S P_L H S
- * of Section 4.  inner_dtype C128 runs the preconditioner in FP64; C64 runs
- * it in FP32 (FP32 links, FP32 basis and coarse operator required) while the
- * outer FGCR, its orthogonalisation and the true residual stay FP64.  The
+ *     z1 = S r;  z2 = z1 + P A^{-1} P^dag (r - H z1);  z = z2 + S (r - H z2).
+ * For a linear smoother and an exact coarse solve this is the composite
+ * M_outer = S P_L + P_R S + Q - S P_L H S of Section 4.  Smoothers:
+ *   HDCR_SMOOTHER_CR         ``smoother_order`` CR steps from zero (nonlinear);
+ *   HDCR_SMOOTHER_CHEBYSHEV  S = H p(H^2), p the order-``smoother_order``
+ *                            Chebyshev approximation of 1/y on
+ *                            [cheb_lo, cheb_hi] (Section 4: order 10 on [1, 64]).
+ * Coarse solvers: HDCR_COARSE_CR (CR on A to ``coarse_tol``, cap
+ * ``coarse_max``) or HDCR_COARSE_DENSE (the dense inverse of
+ * hdcr_coarse_invert, computed on first use).  inner_dtype C128 runs the
+ * smoother and coarse correction in FP64 (the dense inverse is FP32 in either
+ * case); C64 runs them in FP32 (FP32 basis and coarse operator required) while
+ * the outer FGCR, its orthogonalisation and the true residual stay FP64.  The
  * solve ends when the true residual |b - H x| / |b| <= tol.  U and b, x are
- * C128; x holds the initial guess.  Synchronises ``stream``.
+ * C128; x holds the initial guess.  Synchronises ``stream``.  Solves on one
+ * coarse handle must not overlap (they share its cached workspace).
  * Errors: BAD_ARG, NOT_CONVERGED (max_outer reached), NONFINITE, CUDA, NO_MEMORY.
  */
+#define HDCR_SMOOTHER_CR 0
+#define HDCR_SMOOTHER_CHEBYSHEV 1
+#define HDCR_COARSE_CR 0
+#define HDCR_COARSE_DENSE 1
+
 typedef struct {
   double tol;         /* true relative residual target, e.g. 1e-10           */
   int max_outer;      /* cap on outer iterations                             */
   int restart;        /* FGCR restart length (1..64)                         */
-  int smoother_steps; /* CR steps of the smoother (>= 0)                     */
-  double coarse_tol;  /* relative residual of the coarse solve, e.g. 1e-4    */
+  int smoother_kind;  /* HDCR_SMOOTHER_CR or HDCR_SMOOTHER_CHEBYSHEV         */
+  int smoother_order; /* CR steps or Chebyshev order (>= 0)                  */
+  double cheb_lo;     /* Chebyshev smoother interval on H^2                  */
+  double cheb_hi;
+  int coarse_solver;  /* HDCR_COARSE_CR or HDCR_COARSE_DENSE                 */
+  double coarse_tol;  /* relative residual of the coarse CR, e.g. 1e-4       */
   int coarse_max;     /* cap on coarse CR iterations                         */
   int inner_dtype;    /* HDCR_C128 or HDCR_C64                               */
 } hdcr_solve_params;
 
-int hdcr_solve(const hdcr_coarse* co, const void* U, const void* b, void* x,
+int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x,
                const hdcr_solve_params* params, hdcr_solve_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------- gauge force
+ * hdcr_gauge_force: the gauge-link gradient of a solve (not in the paper;
+ * derived from the operator above).  For H x = b and H y = eta, with
+ * w = Gamma5 y, the loss Re(eta^dag x) changes by Re sum tr(dU_mu(x) F_mu(x)) with
+ *   F_mu(x) = 1/2 sum_s [ B + C^dag ],
+ *   B_ba = sum_alpha [(1 - gamma_mu) x(x+mu,s)]_{alpha b} conj(w(x,s)_{alpha a}),
+ *   C_ba = sum_alpha [(1 + gamma_mu) x(x,s)]_{alpha b} conj(w(x+mu,s)_{alpha a})
+ * (the t-boundary phase enters through x(x+mu), w(x+mu)).  x, w: one field each;
+ * F: 4*V4*9 complex in the gauge layout, F[mu][x4][b][a] = (F_mu(x))_ba.  The
+ * gradient of the loss with respect to Re U_ab + i Im U_ab is conj(F_ba).
+ */
+int hdcr_gauge_force(const hdcr_geom* g, const void* x, const void* w, void* F, int dtype,
+                     void* stream);
 
 #ifdef __cplusplus
 }

@@ -315,3 +315,60 @@ def hdcr_solve(U, sub: Subspace, A, b, p: HDCRParams, x0=None):
     H = lambda v: dwf.apply_H(U, v, p.M5, p.mf, p.bc_t)
     B = lambda r: vcycle(U, sub, A, r, p)
     return fgcr(H, B, b, x0=x0, tol=p.tol, restart=p.restart, maxiter=p.max_outer)
+
+
+# ------------------------------------------------- Chebyshev variants (Section 4, Fig. 1)
+def chebyshev_inverse_coeffs(lo: float, hi: float, order: int) -> np.ndarray:
+    """Coefficients c_0..c_order of the truncated Chebyshev series of f(y) = 1/y on
+    [lo, hi] (Section 4: "an order 10 Chebyshev polynomial approximation to 1/x in
+    the range [1.0, 64.0]"), from Chebyshev-Gauss quadrature with 4*(order+1) nodes:
+    p(y) = c_0/2 + sum_{k>=1} c_k T_k(t), t = (2y - hi - lo)/(hi - lo)."""
+    m = 4 * (order + 1)
+    theta = np.pi * (np.arange(m) + 0.5) / m
+    y = 0.5 * (hi + lo) + 0.5 * (hi - lo) * np.cos(theta)
+    f = 1.0 / y
+    return np.array([2.0 / m * np.sum(f * np.cos(k * theta)) for k in range(order + 1)])
+
+
+def chebyshev_smoother(U, r, p: HDCRParams, lo: float = 1.0, hi: float = 64.0, order: int = 10):
+    """S r = H p(H^2) r with p the Chebyshev approximation of 1/y on [lo, hi] (Section 4).
+
+    Reading: the interval of the paper's smoother refers to y = H^2 (the
+    spectrum of H reaches |lambda| ~ 8, so [1, 64] covers 1 <= |lambda| <= 8), and
+    S = H p(H^2) approximates H^{-1} there.  Linear in r.  The three-term
+    recurrence T_{k+1} = 2 t T_k - T_{k-1} runs on vectors with t = (2 H^2 - hi - lo)/(hi - lo)."""
+    H = lambda v: dwf.apply_H(U, v, p.M5, p.mf, p.bc_t)
+    c = chebyshev_inverse_coeffs(lo, hi, order)
+    a, b = 2.0 / (hi - lo), -(hi + lo) / (hi - lo)
+    tmap = lambda v: a * H(H(v)) + b * v
+    v = H(r)
+    t_prev = v
+    acc = 0.5 * c[0] * t_prev
+    if order >= 1:
+        t_cur = tmap(v)
+        acc = acc + c[1] * t_cur
+        for k in range(2, order + 1):
+            t_next = 2.0 * tmap(t_cur) - t_prev
+            acc = acc + c[k] * t_next
+            t_prev, t_cur = t_cur, t_next
+    return acc
+
+
+def chebyshev_filter(U, x0, M5, mf, bc_t=1, lam_cut: float = 0.5, lam_max: float = 8.0,
+                     order: int = 500):
+    """T_order(t(H^2)) x0, normalised: the Chebyshev low-pass filter of Fig. 1 (right)
+    applied to Gaussian noise (Section 4, option iii).  t maps [lam_cut^2, lam_max^2] onto
+    [-1, 1], where |T| <= 1, while modes with |lambda| < lam_cut are enhanced.  The
+    recurrence is rescaled every 8 steps (a common factor keeps it exact)."""
+    H = lambda v: dwf.apply_H(U, v, M5, mf, bc_t)
+    lo, hi = lam_cut * lam_cut, lam_max * lam_max
+    a, b = 2.0 / (hi - lo), -(hi + lo) / (hi - lo)
+    tmap = lambda v: a * H(H(v)) + b * v
+    t_prev = x0
+    t_cur = tmap(x0)
+    for k in range(2, order + 1):
+        t_prev, t_cur = t_cur, 2.0 * tmap(t_cur) - t_prev
+        if k % 8 == 0:
+            s = 1.0 / np.sqrt(dwf.norm2(t_cur))
+            t_prev, t_cur = t_prev * s, t_cur * s
+    return t_cur / np.sqrt(dwf.norm2(t_cur))

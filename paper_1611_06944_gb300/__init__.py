@@ -37,6 +37,26 @@ class _LazyLib:
 _L = _LazyLib()
 
 
+def launch_count() -> int:
+    """Kernels launched by libhdcr so far in this process."""
+    return int(_L.hdcr_launch_count())
+
+
+def stencil_timer(enable: bool) -> None:
+    """Start (reset) or stop event timing of every application of H."""
+    _check(_L.hdcr_stencil_timer(1 if enable else 0), "stencil_timer")
+
+
+def stencil_timer_read(dtype: torch.dtype) -> dict:
+    """Recorded stencil launches of one precision: device ms, launches, 5d sites."""
+    ms = ctypes.c_double()
+    nl = ctypes.c_longlong()
+    ns = ctypes.c_longlong()
+    _check(_L.hdcr_stencil_timer_read(_dt(dtype), ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ns)),
+           "stencil_timer_read")
+    return {"ms": ms.value, "launches": nl.value, "sites": ns.value}
+
+
 def load_library():
     """Load libhdcr.so now (raises ImportError if it has not been built)."""
     return _L.hdcr_version()
@@ -45,7 +65,8 @@ __all__ = [
     "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "norm2", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
-    "CoarseOperator", "build_coarse_op", "apply_coarse", "hdcr_solve",
+    "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
+    "hdcr_solve", "hdcr_solve_into", "gauge_force", "HDCRSolve", "solve_autograd",
 ]
 
 library_path = _lib.LIB_PATH
@@ -275,21 +296,36 @@ def _block_arr(block):
     return arr
 
 
+def _dt(d: torch.dtype) -> int:
+    return _lib.HDCR_C128 if d == torch.complex128 else _lib.HDCR_C64
+
+
 def build_subspace(lat: Lattice, U: torch.Tensor, noise: torch.Tensor, M5: float, mf: float, block,
-                   smooth_iters: int = 10, store_dtype: torch.dtype = torch.complex128,
-                   stream=None) -> Subspace:
-    """Subspace from nvec/2 noise fields (complex128, packed): smoothing by CR on H x = 0,
-    Gamma5 chiral split, block orthonormalisation (Section 4)."""
+                   kind: str = "chebyshev", order: int = 300, lam_cut: float = 0.3, lam_max: float = 8.0,
+                   filter_dtype: torch.dtype = torch.complex128,
+                   store_dtype: torch.dtype = torch.complex128, stream=None) -> Subspace:
+    """Subspace from nvec/2 noise fields (complex128, packed) (Section 4): each is filtered
+    towards the low modes of H -- kind "cr" (``order`` CR steps on H x = 0) or
+    "chebyshev" (the order-``order`` low-pass filter T(t(H^2)) of Fig. 1) -- then split
+    by Gamma5 chirality and block-orthonormalised in FP64."""
     if U.dtype != torch.complex128 or noise.dtype != torch.complex128:
         raise TypeError("build_subspace takes complex128 links and noise")
     half = _nfields(lat, noise, "noise")
+    sp = _lib.hdcr_subspace_params()
+    sp.nvec = 2 * half
+    for i in range(4):
+        sp.block[i] = int(block[i])
+    sp.kind = {"cr": _lib.HDCR_SUBSPACE_CR_SMOOTH, "chebyshev": _lib.HDCR_SUBSPACE_CHEBYSHEV}[kind]
+    sp.order = int(order)
+    sp.lam_cut = float(lam_cut)
+    sp.lam_max = float(lam_max)
+    sp.filter_dtype = _dt(filter_dtype)
+    sp.store_dtype = _dt(store_dtype)
     h = ctypes.c_void_p()
     g = lat.c_geom()
     p = _params(M5, mf)
-    code = _lib.HDCR_C128 if store_dtype == torch.complex128 else _lib.HDCR_C64
-    _check(_L.hdcr_build_subspace(C_ref(g), C_ref(p), _dev(U, "U"), _dev(noise, "noise"), 2 * half,
-                                  _block_arr(block), int(smooth_iters), code, _stream(stream),
-                                  ctypes.byref(h)), "build_subspace")
+    _check(_L.hdcr_build_subspace(C_ref(g), C_ref(p), _dev(U, "U"), _dev(noise, "noise"), C_ref(sp),
+                                  _stream(stream), ctypes.byref(h)), "build_subspace")
     return Subspace(h, lat, block, 2 * half, store_dtype, U.device)
 
 
@@ -385,21 +421,122 @@ def apply_coarse(co: CoarseOperator, c: torch.Tensor, stream=None) -> torch.Tens
     return out
 
 
+def coarse_invert(co: CoarseOperator, stream=None) -> None:
+    """Dense FP32 inverse of the coarse operator (Gauss-Jordan with partial pivoting)."""
+    _check(_L.hdcr_coarse_invert(co.handle, _stream(stream)), "coarse_invert")
+
+
+def coarse_solve_dense(co: CoarseOperator, c: torch.Tensor, stream=None) -> torch.Tensor:
+    """A^{-1} c with the dense inverse (complex64 coarse vectors)."""
+    per = co.sub.Vc * co.sub.nvec
+    out = torch.empty_like(c)
+    _check(_L.hdcr_coarse_solve_dense(co.handle, _dev(c, "c"), _dev(out, "out"), c.numel() // per,
+                                      _stream(stream)), "coarse_solve_dense")
+    return out
+
+
+def _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi, coarse_solver,
+                  coarse_tol, coarse_max, inner_dtype):
+    prm = _lib.hdcr_solve_params()
+    prm.tol = float(tol)
+    prm.max_outer = int(max_outer)
+    prm.restart = int(restart)
+    prm.smoother_kind = {"cr": _lib.HDCR_SMOOTHER_CR, "chebyshev": _lib.HDCR_SMOOTHER_CHEBYSHEV}[smoother]
+    prm.smoother_order = int(smoother_order)
+    prm.cheb_lo = float(cheb_lo)
+    prm.cheb_hi = float(cheb_hi)
+    prm.coarse_solver = {"cr": _lib.HDCR_COARSE_CR, "dense": _lib.HDCR_COARSE_DENSE}[coarse_solver]
+    prm.coarse_tol = float(coarse_tol)
+    prm.coarse_max = int(coarse_max)
+    prm.inner_dtype = _dt(inner_dtype)
+    return prm
+
+
+def hdcr_solve_into(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x: torch.Tensor,
+                    tol: float = 1e-10, max_outer: int = 500, restart: int = 8,
+                    smoother: str = "chebyshev", smoother_order: int = 10, cheb_lo: float = 1.0,
+                    cheb_hi: float = 64.0, coarse_solver: str = "dense", coarse_tol: float = 1e-4,
+                    coarse_max: int = 1000, inner_dtype: torch.dtype = torch.complex128,
+                    stream=None) -> dict:
+    """hdcr_solve with a caller-owned x (initial guess in, iterate out).  Returns the
+    stats dict, including a failed solve's status, without raising."""
+    if U.dtype != torch.complex128 or b.dtype != torch.complex128 or x.dtype != torch.complex128:
+        raise TypeError("hdcr_solve takes complex128 links, source and solution")
+    prm = _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi,
+                        coarse_solver, coarse_tol, coarse_max, inner_dtype)
+    st = _lib.hdcr_solve_stats()
+    status = _L.hdcr_solve(co.handle, _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), C_ref(prm), C_ref(st),
+                           _stream(stream))
+    d = st.as_dict()
+    d["status"] = status
+    return d
+
+
 def hdcr_solve(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x0: torch.Tensor | None = None,
-               tol: float = 1e-10, max_outer: int = 500, restart: int = 8, smoother_steps: int = 8,
-               coarse_tol: float = 1e-4, coarse_max: int = 1000,
-               inner_dtype: torch.dtype = torch.complex128, stream=None):
+               tol: float = 1e-10, max_outer: int = 500, restart: int = 8,
+               smoother: str = "chebyshev", smoother_order: int = 10, cheb_lo: float = 1.0,
+               cheb_hi: float = 64.0, coarse_solver: str = "dense", coarse_tol: float = 1e-4,
+               coarse_max: int = 1000, inner_dtype: torch.dtype = torch.complex128, stream=None):
     """H x = b by flexible GCR preconditioned with the two-level V-cycle (Section 4).
+    smoother "chebyshev" (S = H p(H^2), p ~ 1/y on [cheb_lo, cheb_hi]) or "cr"
+    (smoother_order CR steps); coarse_solver "dense" (exact, FP32 inverse) or "cr".
     Returns (x, stats dict); raises HDCRError when the solve fails."""
     if U.dtype != torch.complex128 or b.dtype != torch.complex128:
         raise TypeError("hdcr_solve takes complex128 links and source")
     if _nfields(co.sub.lat, b, "b") != 1:
         raise ValueError("hdcr_solve takes one right-hand side")
     x = torch.zeros_like(b) if x0 is None else x0.clone()
-    prm = _lib.hdcr_solve_params(float(tol), int(max_outer), int(restart), int(smoother_steps),
-                                 float(coarse_tol), int(coarse_max),
-                                 _lib.HDCR_C128 if inner_dtype == torch.complex128 else _lib.HDCR_C64)
+    prm = _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi,
+                        coarse_solver, coarse_tol, coarse_max, inner_dtype)
     st = _lib.hdcr_solve_stats()
     _check(_L.hdcr_solve(co.handle, _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), C_ref(prm), C_ref(st),
                          _stream(stream)), "hdcr_solve")
     return x, st.as_dict()
+
+
+# ------------------------------------------------------------------ gradient
+def gauge_force(lat: Lattice, x: torch.Tensor, w: torch.Tensor, stream=None) -> torch.Tensor:
+    """F_mu(x) with dL = Re sum tr(dU F) for L = Re(eta^dag x), H x = b, w = Gamma5 H^{-1} eta.
+    Returns a (4, V4, 3, 3) tensor, F[mu, x4, b, a] = (F_mu(x))_ba."""
+    if x.dtype != w.dtype or _nfields(lat, x, "x") != 1 or _nfields(lat, w, "w") != 1:
+        raise ValueError("x and w must be single fields of one dtype")
+    F = torch.empty((4, lat.V4, 3, 3), dtype=x.dtype, device=x.device)
+    g = lat.c_geom()
+    _check(_L.hdcr_gauge_force(C_ref(g), _dev(x, "x"), _dev(w, "w"), F.data_ptr(), _code(x),
+                               _stream(stream)), "gauge_force")
+    return F
+
+
+class HDCRSolve(torch.autograd.Function):
+    """x = H(U)^{-1} b by HDCR, differentiable in U and b.
+
+    Forward: build the subspace and coarse operator from ``noise`` (not
+    differentiated: the converged solution does not depend on it) and solve.
+    Backward, given g = dL/dx (torch convention): the adjoint solve H y = g with
+    the same Hermitian operator and coarse space, then dL/db = y and
+    dL/dU = F^dag per link with F the gauge force of (x, Gamma5 y).
+    """
+
+    @staticmethod
+    def forward(ctx, U, b, lat, noise, M5, mf, block, filter_kw, solve_kw):
+        sub = build_subspace(lat, U, noise, M5, mf, block, **filter_kw)
+        co = build_coarse_op(sub, U, M5, mf, op_dtype=sub.dtype)
+        x, st = hdcr_solve(co, U, b, inner_dtype=sub.dtype, **solve_kw)
+        ctx.lat, ctx.co, ctx.solve_kw, ctx.dtype = lat, co, solve_kw, sub.dtype
+        ctx.save_for_backward(U, x)
+        ctx.stats = st
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        U, x = ctx.saved_tensors
+        y, _ = hdcr_solve(ctx.co, U, gx.contiguous(), inner_dtype=ctx.dtype, **ctx.solve_kw)
+        F = gauge_force(ctx.lat, x, apply_gamma5_r5(ctx.lat, y))
+        gU = F.conj().transpose(-1, -2).contiguous()
+        return gU, y, None, None, None, None, None, None, None
+
+
+def solve_autograd(lat: Lattice, U: torch.Tensor, b: torch.Tensor, noise: torch.Tensor, M5: float, mf: float,
+                   block, filter_kw: dict | None = None, solve_kw: dict | None = None) -> torch.Tensor:
+    """Differentiable HDCR solve: see HDCRSolve."""
+    return HDCRSolve.apply(U, b, lat, noise, M5, mf, tuple(block), filter_kw or {}, solve_kw or {})

@@ -43,11 +43,28 @@ class hdcr_solve_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+HDCR_SUBSPACE_CR_SMOOTH = 0
+HDCR_SUBSPACE_CHEBYSHEV = 1
+HDCR_SMOOTHER_CR = 0
+HDCR_SMOOTHER_CHEBYSHEV = 1
+HDCR_COARSE_CR = 0
+HDCR_COARSE_DENSE = 1
+
+
+class hdcr_subspace_params(C.Structure):
+    _fields_ = [
+        ("nvec", C.c_int), ("block", C.c_int * 4), ("kind", C.c_int), ("order", C.c_int),
+        ("lam_cut", C.c_double), ("lam_max", C.c_double), ("filter_dtype", C.c_int),
+        ("store_dtype", C.c_int),
+    ]
+
+
 class hdcr_solve_params(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("max_outer", C.c_int), ("restart", C.c_int),
-        ("smoother_steps", C.c_int), ("coarse_tol", C.c_double), ("coarse_max", C.c_int),
-        ("inner_dtype", C.c_int),
+        ("smoother_kind", C.c_int), ("smoother_order", C.c_int), ("cheb_lo", C.c_double),
+        ("cheb_hi", C.c_double), ("coarse_solver", C.c_int), ("coarse_tol", C.c_double),
+        ("coarse_max", C.c_int), ("inner_dtype", C.c_int),
     ]
 
 
@@ -64,6 +81,9 @@ SIGNATURES = {
     "hdcr_strerror": (C.c_char_p, [_I]),
     "hdcr_last_error": (C.c_char_p, []),
     "hdcr_version": (_I, []),
+    "hdcr_launch_count": (C.c_ulonglong, []),
+    "hdcr_stencil_timer": (_I, [_I]),
+    "hdcr_stencil_timer_read": (_I, [_I, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "hdcr_apply_g5dwf": (_I, [_G, _DP, _P, _P, _P, _I, _I, _P]),
     "hdcr_apply_gamma5_r5": (_I, [_G, _P, _P, _I, _I, _P]),
     "hdcr_fermion_pack": (_I, [_G, _P, _P, _I, _I, _P]),
@@ -72,7 +92,7 @@ SIGNATURES = {
     "hdcr_cdot": (_I, [_P, _P, _SZ, _I, _P, _P]),
     "hdcr_norm2": (_I, [_P, _SZ, _I, _P, _P]),
     "hdcr_cr_solve": (_I, [_G, _DP, _P, _P, _P, _I, _D, _I, _ST, _P]),
-    "hdcr_build_subspace": (_I, [_G, _DP, _P, _P, _I, C.POINTER(C.c_int), _I, _I, _P, C.POINTER(_P)]),
+    "hdcr_build_subspace": (_I, [_G, _DP, _P, _P, C.POINTER(hdcr_subspace_params), _P, C.POINTER(_P)]),
     "hdcr_subspace_from_vectors": (_I, [_G, C.POINTER(C.c_int), _I, _P, _I, _P, C.POINTER(_P)]),
     "hdcr_subspace_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "hdcr_subspace_get_vectors": (_I, [_P, _P, _P]),
@@ -82,8 +102,11 @@ SIGNATURES = {
     "hdcr_build_coarse_op": (_I, [_P, _DP, _P, _I, _P, C.POINTER(_P)]),
     "hdcr_coarse_get_op": (_I, [_P, _P, _P]),
     "hdcr_apply_coarse": (_I, [_P, _P, _P, _I, _I, _P]),
+    "hdcr_coarse_invert": (_I, [_P, _P]),
+    "hdcr_coarse_solve_dense": (_I, [_P, _P, _P, _I, _P]),
     "hdcr_coarse_destroy": (None, [_P]),
     "hdcr_solve": (_I, [_P, _P, _P, _P, C.POINTER(hdcr_solve_params), _ST, _P]),
+    "hdcr_gauge_force": (_I, [_G, _P, _P, _P, _I, _P]),
 }
 
 

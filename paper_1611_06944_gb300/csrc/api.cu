@@ -3,11 +3,16 @@
 #include <stdarg.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "hdcr_internal.cuh"
 
 namespace hdcr {
 
 static thread_local char g_last_error[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -80,3 +85,5 @@ extern "C" const char* hdcr_strerror(int status) {
 extern "C" const char* hdcr_last_error(void) { return hdcr::g_last_error; }
 
 extern "C" int hdcr_version(void) { return 100; }
+
+extern "C" unsigned long long hdcr_launch_count(void) { return hdcr::g_launches.load(std::memory_order_relaxed); }

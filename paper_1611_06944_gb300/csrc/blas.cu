@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const cpx<R>* __rest
 
 template <typename R>
 int launch_cdot(const void* u, const void* v, long long n, RedScratch rs, double* result, cudaStream_t st) {
-  cdot_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>((const cpx<R>*)u, (const cpx<R>*)v, n, rs, result);
+  cdot_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>((const cpx<R>*)u, (const cpx<R>*)v, n, rs, result); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -76,7 +76,7 @@ template int launch_cdot<float>(const void*, const void*, long long, RedScratch,
 
 template <typename R>
 int launch_norm2(const void* u, long long n, RedScratch rs, double* result, cudaStream_t st) {
-  norm2_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>((const cpx<R>*)u, n, rs, result);
+  norm2_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>((const cpx<R>*)u, n, rs, result); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }

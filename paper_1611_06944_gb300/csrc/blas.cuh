@@ -19,4 +19,8 @@ int launch_norm2(const void* u, long long n, RedScratch rs, double* result, cuda
 
 int device_red_scratch(RedScratch* out);
 
+// stencil timer (dwf.cu): bracket one stencil launch with events when enabled
+void stencil_timer_begin(int kind, long long sites, cudaStream_t st, int* slot);
+void stencil_timer_end(int slot, cudaStream_t st);
+
 }  // namespace hdcr

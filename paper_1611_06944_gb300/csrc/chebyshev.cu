@@ -1,0 +1,209 @@
+// Chebyshev polynomials of H^2 (Section 4 and Fig. 1):
+//
+//  * smoother  S r = H p(H^2) r, p the truncated Chebyshev series of 1/y on
+//    [lo, hi] ("an order 10 Chebyshev polynomial approximation to 1/x in the
+//    range [1.0, 64.0]"; the interval is read as one for y = H^2, whose top
+//    edge lambda_max(H)^2 is about 64);
+//  * filter    T_n(t(H^2)) x, t mapping [lam_cut^2, lam_max^2] onto [-1, 1]:
+//    the low-pass filter applied to Gaussian noise to build the subspace.
+//
+// Both run the three-term recurrence T_{k+1} = 2 t T_k - T_{k-1} on vectors;
+// one fused kernel per step forms T_{k+1} from H^2 T_k and accumulates the
+// series, so a step costs two stencil launches and one BLAS pass.
+#include <math.h>
+
+#include <vector>
+
+#include "chebyshev.cuh"
+
+namespace hdcr {
+
+std::vector<double> cheb_inverse_coeffs(double lo, double hi, int order) {
+  // c_k = (2/m) sum_j f(y_j) cos(k theta_j), theta_j = pi (j + 1/2) / m, m = 4 (order + 1)
+  const int m = 4 * (order + 1);
+  std::vector<double> c(order + 1, 0.0);
+  for (int j = 0; j < m; ++j) {
+    const double th = M_PI * (j + 0.5) / m;
+    const double y = 0.5 * (hi + lo) + 0.5 * (hi - lo) * cos(th);
+    const double f = 1.0 / y;
+    for (int k = 0; k <= order; ++k) c[k] += f * cos(k * th);
+  }
+  for (int k = 0; k <= order; ++k) c[k] *= 2.0 / m;
+  return c;
+}
+
+// next = 2 (a w + b cur) - prev (written over prev);  acc = acc0 * acc + ck * next
+template <typename R>
+__global__ void cheb_step_kernel(const cpx<R>* __restrict__ w, const cpx<R>* __restrict__ cur,
+                                 cpx<R>* __restrict__ prev, cpx<R>* __restrict__ acc, long long n, R a, R b,
+                                 R ck, int with_acc) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> wv = ld(w + i), cv = ld(cur + i), pv = ld(prev + i);
+    cpx<R> nx;
+    nx.re = (R)2 * fma(a, wv.re, b * cv.re) - pv.re;
+    nx.im = (R)2 * fma(a, wv.im, b * cv.im) - pv.im;
+    st(prev + i, nx);
+    if (with_acc) {
+      cpx<R> av = ld(acc + i);
+      av.re = fma(ck, nx.re, av.re);
+      av.im = fma(ck, nx.im, av.im);
+      st(acc + i, av);
+    }
+  }
+}
+
+// cur = a w + b v (first step, T_1);  acc = c0/2 v + c1 cur
+template <typename R>
+__global__ void cheb_first_kernel(const cpx<R>* __restrict__ w, const cpx<R>* __restrict__ v,
+                                  cpx<R>* __restrict__ cur, cpx<R>* __restrict__ acc, long long n, R a, R b,
+                                  R c0h, R c1, int with_acc) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> wv = ld(w + i), vv = ld(v + i);
+    cpx<R> t;
+    t.re = fma(a, wv.re, b * vv.re);
+    t.im = fma(a, wv.im, b * vv.im);
+    st(cur + i, t);
+    if (with_acc) {
+      cpx<R> av;
+      av.re = fma(c1, t.re, c0h * vv.re);
+      av.im = fma(c1, t.im, c0h * vv.im);
+      st(acc + i, av);
+    }
+  }
+}
+
+// u *= 1/sqrt(*n2), v *= 1/sqrt(*n2)
+template <typename R>
+__global__ void rescale2_kernel(cpx<R>* __restrict__ u, cpx<R>* __restrict__ v, long long n, const double* n2) {
+  const R s = (R)(*n2 > 0.0 ? 1.0 / sqrt(*n2) : 1.0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> a = ld(u + i);
+    st(u + i, cpx<R>(s * a.re, s * a.im));
+    if (v) {
+      const cpx<R> c = ld(v + i);
+      st(v + i, cpx<R>(s * c.re, s * c.im));
+    }
+  }
+}
+
+template <typename R>
+int cheb_work_alloc(ChebWork<R>* w, long long n) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(cpx<R>) * n * 4 + 256);
+  if (e != cudaSuccess) return cuda_status(e, "Chebyshev workspace");
+  w->t0 = (cpx<R>*)p;
+  w->t1 = w->t0 + n;
+  w->h1 = w->t1 + n;
+  w->h2 = w->h1 + n;
+  w->n2 = (double*)(w->h2 + n);
+  return HDCR_OK;
+}
+
+template <typename R>
+void cheb_work_free(ChebWork<R>* w) {
+  if (w->t0) cudaFree(w->t0);
+  w->t0 = nullptr;
+}
+
+template <typename R>
+int cheb_smoother(const FineOp<R>& H, const cpx<R>* r, cpx<R>* out, const std::vector<double>& c, double lo,
+                  double hi, ChebWork<R>& w, cudaStream_t st, int* matvecs) {
+  const long long n = H.n();
+  const int nb = num_blocks(n, 256, 4096);
+  const int order = (int)c.size() - 1;
+  const R a = (R)(2.0 / (hi - lo)), b = (R)(-(hi + lo) / (hi - lo));
+  // v = H r (held in t0 = T_0 v)
+  HDCR_TRY(H.apply(r, w.t0, st));
+  int mv = 1;
+  if (order == 0) {
+    rescale_copy(w.t0, out, n, (R)(0.5 * c[0]), st);
+    *matvecs += mv;
+    return HDCR_OK;
+  }
+  // T_1 v = t(H^2) v
+  HDCR_TRY(H.apply(w.t0, w.h1, st));
+  HDCR_TRY(H.apply(w.h1, w.h2, st));
+  mv += 2;
+  cheb_first_kernel<R><<<nb, 256, 0, st>>>(w.h2, w.t0, w.t1, out, n, a, b, (R)(0.5 * c[0]), (R)c[1], 1); count_launch();
+  HDCR_LAUNCH_CHECK();
+  cpx<R>* prev = w.t0;
+  cpx<R>* cur = w.t1;
+  for (int k = 2; k <= order; ++k) {
+    HDCR_TRY(H.apply(cur, w.h1, st));
+    HDCR_TRY(H.apply(w.h1, w.h2, st));
+    mv += 2;
+    cheb_step_kernel<R><<<nb, 256, 0, st>>>(w.h2, cur, prev, out, n, a, b, (R)c[k], 1); count_launch();
+    HDCR_LAUNCH_CHECK();
+    cpx<R>* t = prev;
+    prev = cur;
+    cur = t;
+  }
+  *matvecs += mv;
+  return HDCR_OK;
+}
+
+template <typename R>
+__global__ void scale_copy_kernel(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, long long n, R s) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<R> v = ld(in + i);
+    st(out + i, cpx<R>(s * v.re, s * v.im));
+  }
+}
+
+template <typename R>
+void rescale_copy(const cpx<R>* in, cpx<R>* out, long long n, R s, cudaStream_t st) {
+  scale_copy_kernel<R><<<num_blocks(n, 256, 4096), 256, 0, st>>>(in, out, n, s); count_launch();
+}
+
+template <typename R>
+int cheb_filter(const FineOp<R>& H, cpx<R>* x, int order, double lam_cut, double lam_max, ChebWork<R>& w,
+                RedScratch rs, cudaStream_t st) {
+  const long long n = H.n();
+  const int nb = num_blocks(n, 256, 4096);
+  const double lo = lam_cut * lam_cut, hi = lam_max * lam_max;
+  const R a = (R)(2.0 / (hi - lo)), b = (R)(-(hi + lo) / (hi - lo));
+  // T_0 = x (copy into t0), T_1 = t(H^2) x
+  rescale_copy(x, w.t0, n, (R)1, st);
+  HDCR_TRY(H.apply(w.t0, w.h1, st));
+  HDCR_TRY(H.apply(w.h1, w.h2, st));
+  cheb_first_kernel<R><<<nb, 256, 0, st>>>(w.h2, w.t0, w.t1, nullptr, n, a, b, (R)0, (R)0, 0); count_launch();
+  HDCR_LAUNCH_CHECK();
+  cpx<R>* prev = w.t0;
+  cpx<R>* cur = w.t1;
+  for (int k = 2; k <= order; ++k) {
+    HDCR_TRY(H.apply(cur, w.h1, st));
+    HDCR_TRY(H.apply(w.h1, w.h2, st));
+    cheb_step_kernel<R><<<nb, 256, 0, st>>>(w.h2, cur, prev, nullptr, n, a, b, (R)0, 0); count_launch();
+    HDCR_LAUNCH_CHECK();
+    cpx<R>* t = prev;
+    prev = cur;
+    cur = t;
+    if (k % 8 == 0) {  // keep the growing recurrence in range: common rescale of both terms
+      HDCR_TRY(launch_norm2<R>(cur, n, rs, w.n2, st));
+      rescale2_kernel<R><<<nb, 256, 0, st>>>(cur, prev, n, w.n2); count_launch();
+      HDCR_LAUNCH_CHECK();
+    }
+  }
+  HDCR_TRY(launch_norm2<R>(cur, n, rs, w.n2, st));
+  rescale2_kernel<R><<<nb, 256, 0, st>>>(cur, (cpx<R>*)nullptr, n, w.n2); count_launch();
+  HDCR_LAUNCH_CHECK();
+  rescale_copy(cur, x, n, (R)1, st);
+  return HDCR_OK;
+}
+
+#define HDCR_INST_CHEB(R)                                                                            \
+  template int cheb_work_alloc<R>(ChebWork<R>*, long long);                                         \
+  template void cheb_work_free<R>(ChebWork<R>*);                                                    \
+  template int cheb_smoother<R>(const FineOp<R>&, const cpx<R>*, cpx<R>*, const std::vector<double>&, \
+                                double, double, ChebWork<R>&, cudaStream_t, int*);                  \
+  template int cheb_filter<R>(const FineOp<R>&, cpx<R>*, int, double, double, ChebWork<R>&,         \
+                              RedScratch, cudaStream_t);                                            \
+  template void rescale_copy<R>(const cpx<R>*, cpx<R>*, long long, R, cudaStream_t);
+HDCR_INST_CHEB(double)
+HDCR_INST_CHEB(float)
+
+}  // namespace hdcr

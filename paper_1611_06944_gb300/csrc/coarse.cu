@@ -287,7 +287,7 @@ template <typename R>
 int launch_restrict(const hdcr_subspace* sub, const cpx<R>* fine, cpx<R>* coarse, int nrhs, cudaStream_t st) {
   dim3 grid(sub->bg.Vc, (sub->nvec + RP_KC - 1) / RP_KC, nrhs);
   restrict_kernel<R><<<grid, RED_THREADS, 0, st>>>(sub->g, sub->bg, (const cpx<R>*)sub->vecs, fine, coarse,
-                                                   sub->nvec);
+                                                   sub->nvec); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -297,7 +297,7 @@ int launch_prolong(const hdcr_subspace* sub, const cpx<R>* coarse, const cpx<R>*
                    int nrhs, cudaStream_t st) {
   const long long n = sub->g.V5 * 12 * nrhs;
   prolong_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(sub->g, sub->bg, (const cpx<R>*)sub->vecs, coarse,
-                                                        fine_in, fine, sub->nvec, nrhs);
+                                                        fine_in, fine, sub->nvec, nrhs); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -306,7 +306,7 @@ template <typename R>
 int launch_coarse_apply(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st) {
   const long long n = (long long)co->bg.Vc * co->nvec * nrhs;
   coarse_apply_kernel<R><<<num_blocks(n, 128), 128, 0, st>>>((const cpx<R>*)co->A, co->nbr, in, out,
-                                                             co->bg.Vc, co->nvec, nrhs);
+                                                             co->bg.Vc, co->nvec, nrhs); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -315,7 +315,7 @@ template <typename R>
 int CoarseOp<R>::apply_dot(const cpx<R>* in, cpx<R>* out, RedScratch rs, double* res, cudaStream_t st) const {
   HDCR_TRY(launch_coarse_apply<R>(co, in, out, 1, st));
   const long long n = this->n();
-  cdot_re_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(in, out, n, rs, res);
+  cdot_re_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(in, out, n, rs, res); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -333,7 +333,7 @@ template <typename R, int MU, int SIGN>
 static void launch_leg_face(const Geom& g, const BlockGeom& bg, const cpx<R>* U, const cpx<R>* vecs, cpx<R>* Y,
                             int nvec, cudaStream_t st) {
   const long long n = g.V5 / bg.b[MU] * nvec;
-  leg_face_kernel<R, MU, SIGN><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, vecs, Y, nvec);
+  leg_face_kernel<R, MU, SIGN><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, vecs, Y, nvec); count_launch();
 }
 
 template <typename R>
@@ -349,7 +349,7 @@ static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>
   for (int leg = 0; leg < NLEGS; ++leg) {
     if (leg == 0) {
       const long long n = g.V5 * nvec;
-      leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec);
+      leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec); count_launch();
     } else {
       switch (leg) {
         case 1: launch_leg_face<R, 0, +1>(g, bg, U, phi, Y, nvec, st); break;
@@ -363,7 +363,7 @@ static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>
       }
     }
     HDCR_LAUNCH_CHECK();
-    project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, leg, T);
+    project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, leg, T); count_launch();
     HDCR_LAUNCH_CHECK();
   }
   return HDCR_OK;
@@ -534,5 +534,6 @@ extern "C" void hdcr_coarse_destroy(hdcr_coarse* co) {
   solve_cache_release(co);
   if (co->A) cudaFree(co->A);
   if (co->nbr) cudaFree(co->nbr);
+  if (co->Ainv) cudaFree(co->Ainv);
   delete co;
 }

@@ -70,6 +70,7 @@ struct hdcr_coarse {
   int dtype;    // of A
   void* A;      // [Vc][9][nvec][nvec]
   int* nbr;     // [Vc][9] coarse site reached by each leg
+  void* Ainv;   // dense inverse (FP32 complex, (Vc*nvec)^2), built on demand
   double M5, mf;
   int device;
 };
@@ -97,6 +98,9 @@ struct CoarseOp {
 };
 
 int coarse_check(const hdcr_coarse* co);
+int coarse_invert(hdcr_coarse* co, cudaStream_t st);
+template <typename R>
+int launch_dense_solve(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st);
 void solve_cache_release(const hdcr_coarse* co);  // frees the cached solve workspace
 int subspace_check(const hdcr_subspace* sub);
 

@@ -195,8 +195,11 @@ void crwork_free(CRWork<R>* w) {
 template <typename R>
 int launch_g5dwf_dot(const Geom& g, double M5, double mf, const cpx<R>* U, const cpx<R>* in,
                      cpx<R>* out, RedScratch rs, double* result, cudaStream_t st) {
+  int slot;
+  stencil_timer_begin(sizeof(R) == 8 ? 0 : 1, g.V5, st, &slot);
   HDCR_DISPATCH_LS(g.Ls, (g5dwf_dot_kernel<R, LSC><<<red_blocks(g.V5 * 4), RED_THREADS, 0, st>>>(
                              g, (R)(5.0 - M5), (R)mf, U, in, out, rs, result)));
+  stencil_timer_end(slot, st);
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -204,34 +207,34 @@ int launch_g5dwf_dot(const Geom& g, double M5, double mf, const cpx<R>* U, const
 template <typename R>
 int launch_cr_setup_r(const cpx<R>* b, const cpx<R>* Hx, cpx<R>* r, cpx<R>* p, long long n,
                       RedScratch rs, CRDev* s, cudaStream_t st) {
-  cr_setup_r_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, Hx, r, p, n, rs, s);
+  cr_setup_r_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, Hx, r, p, n, rs, s); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
 template <typename R>
 int launch_cr_setup_ap(const cpx<R>* Ar, cpx<R>* Ap, long long n, RedScratch rs, CRDev* s, cudaStream_t st) {
-  cr_setup_ap_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(Ar, Ap, n, rs, s);
+  cr_setup_ap_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(Ar, Ap, n, rs, s); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
 template <typename R>
 int launch_cr_update_xr(cpx<R>* x, cpx<R>* r, const cpx<R>* p, const cpx<R>* Ap, long long n,
                         RedScratch rs, CRDev* s, cudaStream_t st) {
-  cr_update_xr_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(x, r, p, Ap, n, rs, s);
+  cr_update_xr_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(x, r, p, Ap, n, rs, s); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
 template <typename R>
 int launch_cr_update_p(const cpx<R>* r, cpx<R>* p, const cpx<R>* Ar, cpx<R>* Ap, long long n,
                        RedScratch rs, CRDev* s, cudaStream_t st) {
-  cr_update_p_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(r, p, Ar, Ap, n, rs, s);
+  cr_update_p_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(r, p, Ar, Ap, n, rs, s); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
 template <typename R>
 int launch_diff_norm(const cpx<R>* b, const cpx<R>* y, long long n, RedScratch rs, double* result,
                      cudaStream_t st) {
-  diff_norm_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, y, n, rs, result);
+  diff_norm_kernel<R><<<red_blocks(n), RED_THREADS, 0, st>>>(b, y, n, rs, result); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }

@@ -10,6 +10,9 @@
 // chiral-basis spin projection (two spin components go through the SU(3)
 // multiply instead of four) and the s-hops read only the projected half of
 // the neighbour spinor (P_+ = upper, P_- = lower spins in the chiral basis).
+#include <mutex>
+#include <vector>
+
 #include "dwf_stencil.cuh"
 
 namespace hdcr {
@@ -81,14 +84,62 @@ __global__ void convert_kernel(const cpx<Ri>* __restrict__ in, cpx<Ro>* __restri
   st(out + i, cpx<Ro>((Ro)v.re, (Ro)v.im));
 }
 
+// ------------------------------------------------------------ stencil timer
+// While enabled, every stencil launch is bracketed by CUDA events recorded on
+// its own stream; hdcr_stencil_timer_read() adds up the elapsed times per
+// precision.  Up to TIMER_PAIRS launches are recorded between resets.
+namespace {
+constexpr int TIMER_PAIRS = 16384;
+struct StencilTimer {
+  std::mutex mu;
+  bool enabled = false;
+  std::vector<cudaEvent_t> ev;  // 2 per launch
+  std::vector<int> kind;        // 0 = FP64, 1 = FP32
+  std::vector<long long> sites;
+  int used = 0;
+};
+StencilTimer g_timer;
+}  // namespace
+
+void stencil_timer_begin(int kind, long long sites, cudaStream_t st, int* slot) {
+  *slot = -1;
+  std::lock_guard<std::mutex> lock(g_timer.mu);
+  if (!g_timer.enabled || g_timer.used >= TIMER_PAIRS) return;
+  const int i = g_timer.used++;
+  if ((int)g_timer.kind.size() <= i) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      g_timer.used--;
+      return;
+    }
+    g_timer.ev.push_back(a);
+    g_timer.ev.push_back(b);
+    g_timer.kind.push_back(kind);
+    g_timer.sites.push_back(sites);
+  }
+  g_timer.kind[i] = kind;
+  g_timer.sites[i] = sites;
+  cudaEventRecord(g_timer.ev[2 * i], st);
+  *slot = i;
+}
+
+void stencil_timer_end(int slot, cudaStream_t st) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lock(g_timer.mu);
+  cudaEventRecord(g_timer.ev[2 * slot + 1], st);
+}
+
 // ------------------------------------------------------------ host launchers
 template <typename R>
 int launch_g5dwf(const Geom& g, double M5, double mf, const void* U, const void* in, void* out,
                  int nrhs, cudaStream_t st) {
   const int threads = 256;
   const long long n = g.V5 * nrhs;
+  int slot;
+  stencil_timer_begin(sizeof(R) == 8 ? 0 : 1, n, st, &slot);
   HDCR_DISPATCH_LS(g.Ls, (g5dwf_kernel<R, LSC><<<num_blocks(n, threads), threads, 0, st>>>(
                              g, (R)(5.0 - M5), (R)mf, (const cpx<R>*)U, (const cpx<R>*)in, (cpx<R>*)out, nrhs)));
+  stencil_timer_end(slot, st);
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -100,7 +151,7 @@ template int launch_g5dwf<float>(const Geom&, double, double, const void*, const
 template <typename R>
 int launch_gamma5_r5(const Geom& g, const void* in, void* out, int nfields, cudaStream_t st) {
   const long long n = g.V5 * 12 * nfields;
-  gamma5_r5_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<R>*)in, (cpx<R>*)out, nfields);
+  gamma5_r5_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<R>*)in, (cpx<R>*)out, nfields); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -121,6 +172,7 @@ int launch_convert(const void* in, int idt, void* out, int odt, long long n, cud
     set_error("hdcr_convert: unknown dtype pair %d -> %d", idt, odt);
     return HDCR_ERR_BAD_ARG;
   }
+  count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -187,7 +239,7 @@ extern "C" int hdcr_fermion_pack(const hdcr_geom* gp, const void* natural, void*
                                                                  (cpx<double>*)packed, nfields);
   else
     pack_kernel<float><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<float>*)natural,
-                                                                (cpx<float>*)packed, nfields);
+                                                                (cpx<float>*)packed, nfields); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -203,7 +255,7 @@ extern "C" int hdcr_fermion_unpack(const hdcr_geom* gp, const void* packed, void
                                                                    (cpx<double>*)natural, nfields);
   else
     unpack_kernel<float><<<num_blocks(n, 256), 256, 0, st>>>(g, (const cpx<float>*)packed,
-                                                                  (cpx<float>*)natural, nfields);
+                                                                  (cpx<float>*)natural, nfields); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -215,4 +267,35 @@ extern "C" int hdcr_convert(const void* in, int in_dtype, void* out, int out_dty
     return HDCR_ERR_BAD_ARG;
   }
   return launch_convert(in, in_dtype, out, out_dtype, (long long)n, as_stream(stream));
+}
+
+extern "C" int hdcr_stencil_timer(int enable) {
+  std::lock_guard<std::mutex> lock(g_timer.mu);
+  g_timer.enabled = enable != 0;
+  g_timer.used = 0;
+  return HDCR_OK;
+}
+
+extern "C" int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* launches, long long* sites) {
+  if (!total_ms || !launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64)) {
+    set_error("hdcr_stencil_timer_read: bad arguments");
+    return HDCR_ERR_BAD_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_timer.mu);
+  const int want = dtype == HDCR_C128 ? 0 : 1;
+  double ms = 0.0;
+  long long nl = 0, ns = 0;
+  for (int i = 0; i < g_timer.used; ++i) {
+    if (g_timer.kind[i] != want) continue;
+    HDCR_CUDA_TRY(cudaEventSynchronize(g_timer.ev[2 * i + 1]));
+    float t = 0.f;
+    HDCR_CUDA_TRY(cudaEventElapsedTime(&t, g_timer.ev[2 * i], g_timer.ev[2 * i + 1]));
+    ms += t;
+    nl++;
+    ns += g_timer.sites[i];
+  }
+  *total_ms = ms;
+  *launches = nl;
+  *sites = ns;
+  return HDCR_OK;
 }

@@ -232,12 +232,15 @@ __device__ __forceinline__ void store_g5r5(const Geom& g, cpx<R>* __restrict__ o
     if ((ls) == 16) {                     \
       constexpr int LSC = 16;             \
       KERNEL_CALL;                        \
+      count_launch();                     \
     } else if ((ls) == 8) {               \
       constexpr int LSC = 8;              \
       KERNEL_CALL;                        \
+      count_launch();                     \
     } else {                              \
       constexpr int LSC = 0;              \
       KERNEL_CALL;                        \
+      count_launch();                     \
     }                                     \
   } while (0)
 

@@ -7,10 +7,14 @@
 // preconditioner is nonlinear (CR), which is why the outer iteration is the
 // flexible variant.  The preconditioner runs in FP64 or FP32 (inner_dtype);
 // the outer orthogonalisation, updates and the true residual are FP64.
+// Smoother: CR steps from zero (nonlinear) or the Chebyshev polynomial
+// S = H p(H^2) of Section 4 (linear).  Coarse solve: CR on the coarse operator
+// or its dense inverse.
 #include <chrono>
 #include <mutex>
 #include <vector>
 
+#include "chebyshev.cuh"
 #include "coarse.cuh"
 
 namespace hdcr {
@@ -106,6 +110,8 @@ struct SolveCache {
   void* U_in = nullptr;  // links in the inner precision (FP32 mode)
   void* sw = nullptr;    // CRWork<R> of the smoother
   void* cw = nullptr;    // CRWork<R> of the coarse solve
+  void* chw = nullptr;   // ChebWork<R> of the Chebyshev smoother
+  std::vector<double> cheb_c;
   RedBuffers rb{};       // outer reductions; scal: [0..127] MGS coefficients, 128.. scalars
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
@@ -120,7 +126,11 @@ static void free_inner(SolveCache* c) {
     crwork_free<R>((CRWork<R>*)c->cw);
     delete (CRWork<R>*)c->cw;
   }
-  c->sw = c->cw = nullptr;
+  if (c->chw) {
+    cheb_work_free<R>((ChebWork<R>*)c->chw);
+    delete (ChebWork<R>*)c->chw;
+  }
+  c->sw = c->cw = c->chw = nullptr;
 }
 
 void solve_cache_free(SolveCache* c) {
@@ -170,10 +180,13 @@ static int alloc_cache(const hdcr_coarse* co, int restart, SolveCache** out) {
   int s = red_buffers_alloc(&c->rb, 192);
   CRWork<R>* sw = new CRWork<R>();
   CRWork<R>* cw = new CRWork<R>();
+  ChebWork<R>* chw = new ChebWork<R>();
   c->sw = sw;
   c->cw = cw;
+  c->chw = chw;
   if (s == HDCR_OK) s = crwork_alloc<R>(sw, c->fs);
   if (s == HDCR_OK) s = crwork_alloc<R>(cw, c->cs);
+  if (s == HDCR_OK) s = cheb_work_alloc<R>(chw, c->fs);
   for (int i = 0; i < 6 && s == HDCR_OK; ++i) {
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) s = HDCR_ERR_CUDA;
   }
@@ -186,61 +199,83 @@ static int alloc_cache(const hdcr_coarse* co, int restart, SolveCache** out) {
 }
 
 struct VStats {
-  int fine = 0;     // inner-precision fine applies
-  int coarse = 0;   // coarse applies
+  int fine = 0;          // inner-precision fine applies
+  int coarse = 0;        // coarse stencil applies
+  int coarse_dense = 0;  // dense coarse solves
   int coarse_fail = 0;
 };
 
-// z = B r in precision R (r, z in R)
+// out = S r (out must not alias r or the workspaces)
 template <typename R>
-static int vcycle(const hdcr_coarse* co, const FineOp<R>& H, SolveCache* c, const hdcr_solve_params* prm,
-                  const cpx<R>* r, cpx<R>* z, VStats* vs, cudaStream_t st) {
-  const long long fs = c->fs, cs = c->cs;
+static int smooth(const FineOp<R>& H, SolveCache* c, const hdcr_solve_params* prm, const cpx<R>* r, cpx<R>* out,
+                  VStats* vs, cudaStream_t st) {
+  if (prm->smoother_kind == HDCR_SMOOTHER_CHEBYSHEV)
+    return cheb_smoother<R>(H, r, out, c->cheb_c, prm->cheb_lo, prm->cheb_hi, *(ChebWork<R>*)c->chw, st, &vs->fine);
   CRWork<R>& sw = *(CRWork<R>*)c->sw;
-  CRWork<R>& cw = *(CRWork<R>*)c->cw;
-  cpx<R>* t1 = (cpx<R>*)c->t1;
-  cpx<R>* t2 = (cpx<R>*)c->t2;
-  cpx<R>* e = (cpx<R>*)c->e;
-  const int nb = num_blocks(fs, 256, 4096);
-  CRConfig smooth;
-  smooth.fixed_iters = prm->smoother_steps;
-  smooth.x_zero = true;
+  CRConfig cfg;
+  cfg.fixed_iters = prm->smoother_order;
+  cfg.x_zero = true;
   CRResult res;
-  // z1 = S r
-  HDCR_CUDA_TRY(cudaEventRecord(c->ev[0], st));
-  HDCR_CUDA_TRY(cudaMemsetAsync(z, 0, sizeof(cpx<R>) * fs, st));
-  HDCR_TRY(cr_run<R>(H, r, z, sw, smooth, &res, st));
+  HDCR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(cpx<R>) * c->fs, st));
+  HDCR_TRY(cr_run<R>(H, r, out, sw, cfg, &res, st));
   vs->fine += res.matvecs;
-  HDCR_CUDA_TRY(cudaEventRecord(c->ev[1], st));
-  // r1 = r - H z1;  z2 = z1 + P A^{-1} P^dag r1
-  HDCR_TRY(H.apply(z, t1, st));
-  vs->fine++;
-  sub_kernel<R><<<nb, 256, 0, st>>>(r, t1, t2, fs);
-  HDCR_LAUNCH_CHECK();
-  HDCR_CUDA_TRY(cudaEventRecord(c->ev[2], st));
-  HDCR_TRY(launch_restrict<R>(co->sub, t2, (cpx<R>*)c->c_rhs, 1, st));
-  HDCR_CUDA_TRY(cudaMemsetAsync(c->c_sol, 0, sizeof(cpx<R>) * cs, st));
+  return HDCR_OK;
+}
+
+// c_sol = A^{-1} c_rhs (coarse vectors in R)
+template <typename R>
+static int coarse_solve(const hdcr_coarse* co, SolveCache* c, const hdcr_solve_params* prm, VStats* vs,
+                        cudaStream_t st) {
+  if (prm->coarse_solver == HDCR_COARSE_DENSE) {
+    vs->coarse_dense++;
+    return launch_dense_solve<R>(co, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, 1, st);
+  }
+  CRWork<R>& cw = *(CRWork<R>*)c->cw;
+  HDCR_CUDA_TRY(cudaMemsetAsync(c->c_sol, 0, sizeof(cpx<R>) * c->cs, st));
   CRConfig ccfg;
   ccfg.tol = prm->coarse_tol;
   ccfg.max_iter = prm->coarse_max;
   ccfg.x_zero = true;
   ccfg.check_every = 8;
   CoarseOp<R> A{co};
+  CRResult res;
   HDCR_TRY(cr_run<R>(A, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, cw, ccfg, &res, st));
   vs->coarse += res.matvecs;
   if (!res.converged) vs->coarse_fail++;
+  return HDCR_OK;
+}
+
+// z = B r in precision R (r, z in R)
+template <typename R>
+static int vcycle(const hdcr_coarse* co, const FineOp<R>& H, SolveCache* c, const hdcr_solve_params* prm,
+                  const cpx<R>* r, cpx<R>* z, VStats* vs, cudaStream_t st) {
+  const long long fs = c->fs;
+  cpx<R>* t1 = (cpx<R>*)c->t1;
+  cpx<R>* t2 = (cpx<R>*)c->t2;
+  cpx<R>* e = (cpx<R>*)c->e;
+  const int nb = num_blocks(fs, 256, 4096);
+  // z1 = S r
+  HDCR_CUDA_TRY(cudaEventRecord(c->ev[0], st));
+  HDCR_TRY(smooth<R>(H, c, prm, r, z, vs, st));
+  HDCR_CUDA_TRY(cudaEventRecord(c->ev[1], st));
+  // r1 = r - H z1;  z2 = z1 + P A^{-1} P^dag r1
+  HDCR_TRY(H.apply(z, t1, st));
+  vs->fine++;
+  sub_kernel<R><<<nb, 256, 0, st>>>(r, t1, t2, fs); count_launch();
+  HDCR_LAUNCH_CHECK();
+  HDCR_CUDA_TRY(cudaEventRecord(c->ev[2], st));
+  HDCR_TRY(launch_restrict<R>(co->sub, t2, (cpx<R>*)c->c_rhs, 1, st));
+  HDCR_TRY(coarse_solve<R>(co, c, prm, vs, st));
   HDCR_TRY(launch_prolong<R>(co->sub, (const cpx<R>*)c->c_sol, z, z, 1, st));
   HDCR_CUDA_TRY(cudaEventRecord(c->ev[3], st));
   // r2 = r - H z2;  z = z2 + S r2
   HDCR_TRY(H.apply(z, t1, st));
   vs->fine++;
-  sub_kernel<R><<<nb, 256, 0, st>>>(r, t1, t2, fs);
+  sub_kernel<R><<<nb, 256, 0, st>>>(r, t1, t2, fs); count_launch();
   HDCR_LAUNCH_CHECK();
   HDCR_CUDA_TRY(cudaEventRecord(c->ev[4], st));
-  HDCR_CUDA_TRY(cudaMemsetAsync(e, 0, sizeof(cpx<R>) * fs, st));
-  HDCR_TRY(cr_run<R>(H, t2, e, sw, smooth, &res, st));
-  vs->fine += res.matvecs;
-  add_kernel<R><<<nb, 256, 0, st>>>(z, e, fs);
+  HDCR_TRY(smooth<R>(H, c, prm, t2, e, vs, st));
+  add_kernel<R><<<nb, 256, 0, st>>>(z, e, fs); count_launch();
   HDCR_LAUNCH_CHECK();
   HDCR_CUDA_TRY(cudaEventRecord(c->ev[5], st));
   return HDCR_OK;
@@ -259,6 +294,8 @@ static int solve_impl(const hdcr_coarse* co, SolveCache* c, const void* U, const
     Uin = (const cpx<R>*)c->U_in;
   }
   FineOp<R> Hin{co->g, co->M5, co->mf, Uin};
+  if (prm->smoother_kind == HDCR_SMOOTHER_CHEBYSHEV)
+    c->cheb_c = cheb_inverse_coeffs(prm->cheb_lo, prm->cheb_hi, prm->smoother_order);
   double* scal = c->rb.scal;    // [0, 2*restart): MGS coefficients; 128: |w|^2; 130: a; 132: |r|^2; 133: |b|^2
   RedScratch rs = c->rb.rs;
   double* ring = pinned_ring();
@@ -268,7 +305,7 @@ static int solve_impl(const hdcr_coarse* co, SolveCache* c, const void* U, const
   }
   // r = b - H x, |b|^2
   HDCR_TRY(H64.apply(x, c->tmp, st));
-  sub_kernel<double><<<nb, 256, 0, st>>>(b, c->tmp, c->r, fs);
+  sub_kernel<double><<<nb, 256, 0, st>>>(b, c->tmp, c->r, fs); count_launch();
   HDCR_LAUNCH_CHECK();
   HDCR_TRY(launch_norm2<double>(b, fs, rs, scal + 133, st));
   HDCR_TRY(launch_norm2<double>(c->r, fs, rs, scal + 132, st));
@@ -304,14 +341,14 @@ static int solve_impl(const hdcr_coarse* co, SolveCache* c, const void* U, const
       for (int j = 0; j < i; ++j) {
         HDCR_TRY(launch_cdot<double>(c->W + (long long)j * fs, w, fs, rs, scal + 2 * j, st));
         axpy2_neg_kernel<<<nb, 256, 0, st>>>(w, c->W + (long long)j * fs, z, c->Z + (long long)j * fs, fs,
-                                             scal + 2 * j);
+                                             scal + 2 * j); count_launch();
         HDCR_LAUNCH_CHECK();
       }
       HDCR_TRY(launch_norm2<double>(w, fs, rs, scal + 128, st));
-      scale2_kernel<<<nb, 256, 0, st>>>(w, z, fs, scal + 128);
+      scale2_kernel<<<nb, 256, 0, st>>>(w, z, fs, scal + 128); count_launch();
       HDCR_LAUNCH_CHECK();
       HDCR_TRY(launch_cdot<double>(w, c->r, fs, rs, scal + 130, st));
-      fgcr_update_kernel<<<red_blocks(fs), RED_THREADS, 0, st>>>(x, z, c->r, w, fs, scal + 130, rs, scal + 132);
+      fgcr_update_kernel<<<red_blocks(fs), RED_THREADS, 0, st>>>(x, z, c->r, w, fs, scal + 130, rs, scal + 132); count_launch();
       HDCR_LAUNCH_CHECK();
       HDCR_CUDA_TRY(cudaMemcpyAsync(ring, scal + 132, sizeof(double), cudaMemcpyDeviceToHost, st));
       HDCR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -332,7 +369,7 @@ static int solve_impl(const hdcr_coarse* co, SolveCache* c, const void* U, const
     // true residual (restart or convergence check)
     HDCR_TRY(H64.apply(x, c->tmp, st));
     fine64++;
-    sub_kernel<double><<<nb, 256, 0, st>>>(b, c->tmp, c->r, fs);
+    sub_kernel<double><<<nb, 256, 0, st>>>(b, c->tmp, c->r, fs); count_launch();
     HDCR_LAUNCH_CHECK();
     HDCR_TRY(launch_norm2<double>(c->r, fs, rs, scal + 132, st));
     HDCR_CUDA_TRY(cudaMemcpyAsync(ring, scal + 132, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -356,7 +393,7 @@ static int solve_impl(const hdcr_coarse* co, SolveCache* c, const void* U, const
     stats->iters = iters;
     stats->fine_matvecs = fine64 + (sizeof(R) == 8 ? vs.fine : 0);
     stats->fine_matvecs_lo = sizeof(R) == 8 ? 0 : vs.fine;
-    stats->coarse_matvecs = vs.coarse;
+    stats->coarse_matvecs = vs.coarse + vs.coarse_dense;
     stats->restarts = restarts;
     stats->true_resid = bb > 0 ? sqrt(rr / bb) : 0.0;
     stats->t_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -394,7 +431,7 @@ void solve_cache_release(const hdcr_coarse* co) {
 }
 }  // namespace hdcr
 
-extern "C" int hdcr_solve(const hdcr_coarse* co, const void* U, const void* b, void* x,
+extern "C" int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x,
                           const hdcr_solve_params* prm, hdcr_solve_stats* stats, void* stream) {
   HDCR_TRY(coarse_check(co));
   if (!U || !b || !x || !prm || b == x) {
@@ -402,8 +439,15 @@ extern "C" int hdcr_solve(const hdcr_coarse* co, const void* U, const void* b, v
     return HDCR_ERR_BAD_ARG;
   }
   if (!(prm->tol > 0.0) || prm->max_outer < 1 || prm->restart < 1 || prm->restart > 64 ||
-      prm->smoother_steps < 0 || !(prm->coarse_tol > 0.0) || prm->coarse_max < 1) {
+      prm->smoother_order < 0 || !(prm->coarse_tol > 0.0) || prm->coarse_max < 1 ||
+      (prm->smoother_kind != HDCR_SMOOTHER_CR && prm->smoother_kind != HDCR_SMOOTHER_CHEBYSHEV) ||
+      (prm->coarse_solver != HDCR_COARSE_CR && prm->coarse_solver != HDCR_COARSE_DENSE)) {
     set_error("hdcr_solve: bad parameters");
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (prm->smoother_kind == HDCR_SMOOTHER_CHEBYSHEV &&
+      (prm->smoother_order < 1 || !(prm->cheb_lo > 0.0) || !(prm->cheb_hi > prm->cheb_lo))) {
+    set_error("hdcr_solve: Chebyshev smoother needs order >= 1 and 0 < cheb_lo < cheb_hi");
     return HDCR_ERR_BAD_ARG;
   }
   if (prm->inner_dtype != HDCR_C128 && prm->inner_dtype != HDCR_C64) {
@@ -415,6 +459,7 @@ extern "C" int hdcr_solve(const hdcr_coarse* co, const void* U, const void* b, v
               co->sub->dtype, co->dtype, prm->inner_dtype);
     return HDCR_ERR_BAD_ARG;
   }
+  if (prm->coarse_solver == HDCR_COARSE_DENSE && !co->Ainv) HDCR_TRY(coarse_invert(co, as_stream(stream)));
   cudaStream_t st = as_stream(stream);
   SolveCache* cache = nullptr;
   {

@@ -38,6 +38,9 @@ int cuda_status(cudaError_t e, const char* what);
 
 #define HDCR_LAUNCH_CHECK() HDCR_CUDA_TRY(cudaGetLastError())
 
+// number of kernels this library has launched in the process (a diagnostic)
+void count_launch();
+
 // --------------------------------------------------------------- geometry
 struct Geom {
   int L[4];      // x, y, z, t

@@ -4,6 +4,7 @@
 //   -> restriction to blocks (Eq. 4.1) -> block orthonormalisation, so that
 //   P_S = sum |phi_k^b><phi_k^b| (Eq. 4.3) is a projector.
 // All of it runs in FP64; the basis is then stored in the requested dtype.
+#include "chebyshev.cuh"
 #include "coarse.cuh"
 
 namespace hdcr {
@@ -156,7 +157,7 @@ static int orthonormalise_and_store(const Geom& g, const BlockGeom& bg, cpx<doub
     return cuda_status(e0, "subspace status flag");
   }
   cudaMemsetAsync(dstatus, 0, sizeof(int), st);
-  block_gs_kernel<<<bg.Vc, GS_THREADS, 0, st>>>(g, bg, vecs, nvec, 1e-12, dstatus);
+  block_gs_kernel<<<bg.Vc, GS_THREADS, 0, st>>>(g, bg, vecs, nvec, 1e-12, dstatus); count_launch();
   cudaError_t e = cudaGetLastError();
   int hstatus = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, dstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -205,53 +206,76 @@ static int orthonormalise_and_store(const Geom& g, const BlockGeom& bg, cpx<doub
   return HDCR_OK;
 }
 
-static int build_subspace_impl(const Geom& g, const BlockGeom& bg, const hdcr_dwf_params* p, const void* U,
-                               const void* noise, int nvec, int smooth_iters, int store_dtype,
-                               cudaStream_t st, hdcr_subspace** out) {
+// step 1 for one vector: filter x (precision R, in place) towards the low modes of H
+template <typename R>
+static int filter_one(const FineOp<R>& H, cpx<R>* x, const cpx<R>* zero, const hdcr_subspace_params* sp,
+                      CRWork<R>& w, ChebWork<R>& cw, cudaStream_t st) {
+  if (sp->kind == HDCR_SUBSPACE_CR_SMOOTH) {
+    CRConfig cfg;
+    cfg.fixed_iters = sp->order;
+    return cr_run<R>(H, zero, x, w, cfg, nullptr, st);
+  }
+  return cheb_filter<R>(H, x, sp->order, sp->lam_cut, sp->lam_max, cw, w.rb.rs, st);
+}
+
+template <typename R>
+static int filter_all(const Geom& g, const hdcr_dwf_params* p, const void* U, const void* noise,
+                      const hdcr_subspace_params* sp, cpx<double>* vecs, cudaStream_t st) {
   const long long fs = g.V5 * 12;
-  const int half = nvec / 2;
-  cpx<double>* vecs = nullptr;
-  cpx<double>* x = nullptr;
-  cpx<double>* zero = nullptr;
-  HDCR_CUDA_TRY(cudaMalloc(&vecs, sizeof(cpx<double>) * fs * nvec));
-  cudaError_t e = cudaMalloc(&x, sizeof(cpx<double>) * fs * 2);
-  if (e != cudaSuccess) {
-    cudaFree(vecs);
-    return cuda_status(e, "subspace workspace");
+  const int half = sp->nvec / 2;
+  const bool f64 = sizeof(R) == 8;
+  // x (R), zero (R), x64 scratch, U in R
+  const size_t bytes = sizeof(cpx<R>) * fs * 2 + sizeof(cpx<double>) * fs + (f64 ? 0 : sizeof(cpx<R>) * g.V4 * 36) + 512;
+  void* mem = nullptr;
+  HDCR_CUDA_TRY(cudaMalloc(&mem, bytes));
+  cpx<R>* x = (cpx<R>*)mem;
+  cpx<R>* zero = x + fs;
+  cpx<double>* x64 = (cpx<double>*)(zero + fs);
+  const cpx<R>* Ur = (const cpx<R>*)U;
+  if (!f64) {
+    cpx<R>* u32 = (cpx<R>*)(x64 + fs);
+    launch_convert(U, HDCR_C128, u32, HDCR_C64, (long long)g.V4 * 36, st);
+    Ur = u32;
   }
-  zero = x + fs;
-  CRWork<double> w;
-  int s = crwork_alloc<double>(&w, fs);
-  if (s != HDCR_OK) {
-    cudaFree(vecs);
-    cudaFree(x);
-    return s;
-  }
-  FineOp<double> H{g, p->M5, p->mf, (const cpx<double>*)U};
-  CRConfig cfg;
-  cfg.fixed_iters = smooth_iters;
-  cudaMemsetAsync(zero, 0, sizeof(cpx<double>) * fs, st);
+  CRWork<R> w;
+  ChebWork<R> cw;
+  int s = crwork_alloc<R>(&w, fs);
+  if (s == HDCR_OK && sp->kind == HDCR_SUBSPACE_CHEBYSHEV) s = cheb_work_alloc<R>(&cw, fs);
+  FineOp<R> H{g, p->M5, p->mf, Ur};
+  cudaMemsetAsync(zero, 0, sizeof(cpx<R>) * fs, st);
   for (int i = 0; i < half && s == HDCR_OK; ++i) {
-    cudaMemcpyAsync(x, (const cpx<double>*)noise + (long long)i * fs, sizeof(cpx<double>) * fs,
-                    cudaMemcpyDeviceToDevice, st);
-    s = cr_run<double>(H, zero, x, w, cfg, nullptr, st);
+    const cpx<double>* src = (const cpx<double>*)noise + (long long)i * fs;
+    s = launch_convert(src, HDCR_C128, x, f64 ? HDCR_C128 : HDCR_C64, fs, st);
+    if (s == HDCR_OK) s = filter_one<R>(H, x, zero, sp, w, cw, st);
+    if (s == HDCR_OK) s = launch_convert(x, f64 ? HDCR_C128 : HDCR_C64, x64, HDCR_C128, fs, st);
+    if (s == HDCR_OK) s = launch_norm2<double>(x64, fs, w.rb.rs, &w.dev()->tr, st);
     if (s != HDCR_OK) break;
-    s = launch_norm2<double>(x, fs, w.rb.rs, &w.dev()->tr, st);
-    if (s != HDCR_OK) break;
-    scale_rsqrt_kernel<<<num_blocks(fs, 256, 4096), 256, 0, st>>>(x, fs, &w.dev()->tr);
-    gamma5_split_kernel<<<num_blocks(fs, 256, 4096), 256, 0, st>>>(g, x, vecs + (long long)i * fs,
-                                                                   vecs + (long long)(i + half) * fs);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) s = cuda_status(e, "subspace smoothing");
+    scale_rsqrt_kernel<<<num_blocks(fs, 256, 4096), 256, 0, st>>>(x64, fs, &w.dev()->tr); count_launch();
+    gamma5_split_kernel<<<num_blocks(fs, 256, 4096), 256, 0, st>>>(g, x64, vecs + (long long)i * fs,
+                                                                   vecs + (long long)(i + half) * fs); count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, "subspace filtering");
   }
   cudaStreamSynchronize(st);
-  crwork_free<double>(&w);
-  cudaFree(x);
+  crwork_free<R>(&w);
+  cheb_work_free<R>(&cw);
+  cudaFree(mem);
+  return s;
+}
+
+static int build_subspace_impl(const Geom& g, const BlockGeom& bg, const hdcr_dwf_params* p, const void* U,
+                               const void* noise, const hdcr_subspace_params* sp, cudaStream_t st,
+                               hdcr_subspace** out) {
+  const long long fs = g.V5 * 12;
+  cpx<double>* vecs = nullptr;
+  HDCR_CUDA_TRY(cudaMalloc(&vecs, sizeof(cpx<double>) * fs * sp->nvec));
+  int s = sp->filter_dtype == HDCR_C128 ? filter_all<double>(g, p, U, noise, sp, vecs, st)
+                                        : filter_all<float>(g, p, U, noise, sp, vecs, st);
   if (s != HDCR_OK) {
     cudaFree(vecs);
     return s;
   }
-  return orthonormalise_and_store(g, bg, vecs, nvec, store_dtype, st, out);
+  return orthonormalise_and_store(g, bg, vecs, sp->nvec, sp->store_dtype, st, out);
 }
 
 }  // namespace hdcr
@@ -274,17 +298,27 @@ static int subspace_args(const hdcr_geom* gp, const int block[4], int nvec, int 
 }
 
 extern "C" int hdcr_build_subspace(const hdcr_geom* gp, const hdcr_dwf_params* p, const void* U,
-                                   const void* noise, int nvec, const int block[4], int smooth_iters,
-                                   int store_dtype, void* stream, hdcr_subspace** out) {
+                                   const void* noise, const hdcr_subspace_params* sp, void* stream,
+                                   hdcr_subspace** out) {
+  if (!sp) {
+    set_error("hdcr_build_subspace: null parameters");
+    return HDCR_ERR_BAD_ARG;
+  }
   Geom g;
   BlockGeom bg;
-  HDCR_TRY(subspace_args(gp, block, nvec, store_dtype, &g, &bg));
-  if (!p || !U || !noise || !out || smooth_iters < 0) {
-    set_error("hdcr_build_subspace: null pointer or negative smooth_iters");
+  HDCR_TRY(subspace_args(gp, sp->block, sp->nvec, sp->store_dtype, &g, &bg));
+  if (!p || !U || !noise || !out || sp->order < 0 ||
+      (sp->kind != HDCR_SUBSPACE_CR_SMOOTH && sp->kind != HDCR_SUBSPACE_CHEBYSHEV) ||
+      (sp->filter_dtype != HDCR_C128 && sp->filter_dtype != HDCR_C64)) {
+    set_error("hdcr_build_subspace: null pointer or bad parameters");
+    return HDCR_ERR_BAD_ARG;
+  }
+  if (sp->kind == HDCR_SUBSPACE_CHEBYSHEV && (sp->order < 1 || !(sp->lam_cut > 0.0) || !(sp->lam_max > sp->lam_cut))) {
+    set_error("hdcr_build_subspace: Chebyshev filter needs order >= 1 and 0 < lam_cut < lam_max");
     return HDCR_ERR_BAD_ARG;
   }
   *out = nullptr;
-  return build_subspace_impl(g, bg, p, U, noise, nvec, smooth_iters, store_dtype, as_stream(stream), out);
+  return build_subspace_impl(g, bg, p, U, noise, sp, as_stream(stream), out);
 }
 
 extern "C" int hdcr_subspace_from_vectors(const hdcr_geom* gp, const int block[4], int nvec,

@@ -14,10 +14,14 @@ Conventions (shared vocabulary, not method arithmetic):
 * 5d fermion field ``psi``: complex128 array of shape
   ``(Lt, Lz, Ly, Lx, Ls, 4, 3)`` (site, fifth coordinate s, spin, colour).
 
-The synthetic links follow the recipe U = exp(i*eps*H) with H a traceless
-Hermitian matrix whose complex entries start as Gaussian (Re, Im ~ N(0,1)),
-which stands in for the dynamical ensemble of the paper's Section 5 (the
-ensemble itself is not available here).
+The synthetic links follow the recipe U = exp(i*eps*H) with H a Gaussian
+traceless Hermitian matrix, which stands in for the dynamical ensemble of the
+paper's Section 5 (the ensemble itself is not available here).  "Gaussian
+traceless Hermitian" is read in the convention used for HMC momenta:
+H = sum_a omega_a lambda_a / 2 over the eight Gell-Mann matrices with
+omega_a ~ N(0, 1).  With it eps = 0.5 gives a mean plaquette of about 0.50
+and eps = 0.3 about 0.79 (a physical DWF ensemble at a^-1 = 1.73 GeV sits
+near 0.59).
 """
 from __future__ import annotations
 
@@ -25,6 +29,7 @@ import numpy as np
 
 __all__ = [
     "rng",
+    "plaquette",
     "gauge_field",
     "random_su3_field",
     "gaussian_fermion",
@@ -45,12 +50,27 @@ def lattice_shape(L) -> tuple:
     return (Lt, Lz, Ly, Lx)
 
 
+def _gell_mann_generators() -> np.ndarray:
+    """T_a = lambda_a / 2, a = 1..8 (tr T_a T_b = delta_ab / 2)."""
+    l = np.zeros((8, 3, 3), dtype=np.complex128)
+    l[0][0, 1] = l[0][1, 0] = 1
+    l[1][0, 1], l[1][1, 0] = -1j, 1j
+    l[2][0, 0], l[2][1, 1] = 1, -1
+    l[3][0, 2] = l[3][2, 0] = 1
+    l[4][0, 2], l[4][2, 0] = -1j, 1j
+    l[5][1, 2] = l[5][2, 1] = 1
+    l[6][1, 2], l[6][2, 1] = -1j, 1j
+    l[7] = np.diag([1.0, 1.0, -2.0]) / np.sqrt(3.0)
+    return l / 2
+
+
+_T = _gell_mann_generators()
+
+
 def _traceless_hermitian(g: np.random.Generator, n: int) -> np.ndarray:
-    G = g.standard_normal((n, 3, 3)) + 1j * g.standard_normal((n, 3, 3))
-    H = 0.5 * (G + np.conj(np.swapaxes(G, -1, -2)))
-    tr = np.trace(H, axis1=-2, axis2=-1).real / 3.0
-    H = H - tr[:, None, None] * np.eye(3)[None]
-    return H
+    """n matrices H = sum_a omega_a T_a with omega_a ~ N(0, 1)."""
+    w = g.standard_normal((n, 8))
+    return np.einsum("na,aij->nij", w, _T)
 
 
 def _expm_i_hermitian(H: np.ndarray, eps: float) -> np.ndarray:
@@ -118,3 +138,17 @@ def point_sources(L, Ls: int, site=(0, 0, 0, 0), s: int = 0) -> np.ndarray:
         for c in range(3):
             out[3 * sp + c, t, z, y, x, s, sp, c] = 1.0
     return out
+
+
+def plaquette(U: np.ndarray) -> float:
+    """Mean plaquette Re tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag) / 3 of a
+    gauge field (a roughness diagnostic of the synthetic inputs)."""
+    ax = {0: 3, 1: 2, 2: 1, 3: 0}
+    tot = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            P = (U[mu] @ np.roll(U[nu], -1, axis=ax[mu])
+                 @ np.conj(np.swapaxes(np.roll(U[mu], -1, axis=ax[nu]), -1, -2))
+                 @ np.conj(np.swapaxes(U[nu], -1, -2)))
+            tot += np.trace(P, axis1=-2, axis2=-1).real.mean() / 3.0
+    return tot / 6.0

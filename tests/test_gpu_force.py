@@ -1,0 +1,104 @@
+"""GPU gauge force and the differentiable HDCR solve against the FP64 oracle and
+against central finite differences."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dwf, force
+from oracle.krylov import cr
+from gpu_util import dev, host, links, natural, planes, relerr
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+M5 = 1.8
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_1611_06944_gb300 as hd
+    return hd
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-13), ("c64", 1e-5)])
+@pytest.mark.parametrize("L,Ls,bc", [((4, 4, 2, 6), 4, -1), ((3, 2, 4, 4), 5, 1)])
+def test_force_kernel_matches_oracle(hd, dtype, tol, L, Ls, bc):
+    x = synth.gaussian_fermion(L, Ls, 4000)
+    w = synth.gaussian_fermion(L, Ls, 4001)
+    npdt = np.complex128 if dtype == "c128" else np.complex64
+    xd, wd = planes(x).astype(npdt), planes(w).astype(npdt)
+    F = host(hd.gauge_force(hd.Lattice(L, Ls, bc), dev(xd), dev(wd))).astype(np.complex128)
+    want = force.gauge_force(np.zeros((4,) + synth.lattice_shape(L) + (3, 3), complex),
+                             natural(xd.astype(np.complex128), L, Ls), natural(wd.astype(np.complex128), L, Ls), bc)
+    assert relerr(F, want.reshape(F.shape)) < tol
+
+
+def _loss_and_grad(hd, lat, U, b, eta, noise, block, nvec_kw):
+    Ut = dev(links(U)).requires_grad_(True)
+    bt = dev(planes(b)).requires_grad_(True)
+    x = hd.solve_autograd(lat, Ut, bt, dev(planes(noise)), M5, 0.05, block,
+                          filter_kw=nvec_kw, solve_kw=dict(tol=1e-12, max_outer=500))
+    loss = torch.vdot(dev(planes(eta)).reshape(-1), x.reshape(-1)).real
+    loss.backward()
+    return float(loss), host(Ut.grad), host(bt.grad)
+
+
+def test_autograd_matches_oracle_gradient(hd):
+    """4^4 x 8: d Re(eta^dag x) / dU and / db from the GPU backward (adjoint HDCR solve +
+    force kernel) against the oracle's gradient from tightly converged CR solves."""
+    L, Ls, block = (4, 4, 4, 4), 8, (2, 2, 2, 2)
+    U = synth.gauge_field(L, 0.3, 5000)
+    b = synth.gaussian_fermion(L, Ls, 5001)
+    eta = synth.gaussian_fermion(L, Ls, 5002)
+    noise = synth.gaussian_fermion(L, Ls, 5003, count=4)
+    lat = hd.Lattice(L, Ls)
+    loss, gU, gb = _loss_and_grad(hd, lat, U, b, eta, noise, block, dict(kind="chebyshev", order=60))
+    H = lambda v: dwf.apply_H(U, v, M5, 0.05)
+    x, _ = cr(H, b, tol=1e-13, maxiter=100000)
+    y, _ = cr(H, eta, tol=1e-13, maxiter=100000)
+    gU_o, gb_o = force.solve_gradient(U, x, y)
+    assert abs(loss - np.vdot(eta, x).real) < 1e-9 * abs(loss)
+    assert relerr(gU, gU_o.reshape(gU.shape)) < 1e-6
+    assert relerr(natural(gb, L, Ls), gb_o) < 1e-6
+
+
+def test_autograd_vs_finite_differences(hd):
+    """8^3 x 16, Ls = 8 (the differentiation workload), complex128: central
+    differences with h = 1e-6 along U -> exp(i h T) U on 20 random links agree with
+    the backward's gradient to 1e-6 relative."""
+    L, Ls, block, mf = (8, 8, 8, 16), 8, (4, 4, 4, 4), 0.05
+    U = synth.gauge_field(L, 0.5, 6000)
+    b = synth.gaussian_fermion(L, Ls, 6001)
+    eta = synth.gaussian_fermion(L, Ls, 6002)
+    noise = synth.gaussian_fermion(L, Ls, 6003, count=8)
+    lat = hd.Lattice(L, Ls)
+    Ut = dev(links(U)).requires_grad_(True)
+    x = hd.solve_autograd(lat, Ut, dev(planes(b)), dev(planes(noise)), M5, mf, block,
+                          filter_kw=dict(kind="chebyshev", order=100),
+                          solve_kw=dict(tol=1e-12, max_outer=500))
+    etad = dev(planes(eta)).reshape(-1)
+    torch.vdot(etad, x.reshape(-1)).real.backward()
+    F = np.conj(np.swapaxes(host(Ut.grad), -1, -2))          # grad_U = F^dag
+    bd = dev(planes(b))
+
+    def loss(Ua):
+        xs, _ = hd.cr_solve(lat, dev(Ua), bd, M5, mf, tol=1e-13, max_iter=200000)
+        return float(torch.vdot(etad, xs.reshape(-1)).real)
+
+    rng = synth.rng(6004)
+    Ul = links(U)
+    h = 1e-6
+    for _ in range(20):
+        mu = int(rng.integers(4))
+        x4 = int(rng.integers(Ul.shape[1]))
+        G = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        T = 0.5 * (G + G.conj().T)
+        T -= np.trace(T) / 3 * np.eye(3)
+        w_, V = np.linalg.eigh(T)
+        E = lambda s: (V * np.exp(1j * s * h * w_)) @ V.conj().T
+        Up, Um = Ul.copy(), Ul.copy()
+        Up[mu, x4] = E(1) @ Ul[mu, x4]
+        Um[mu, x4] = E(-1) @ Ul[mu, x4]
+        fd = (loss(Up) - loss(Um)) / (2 * h)
+        an = np.trace(1j * T @ Ul[mu, x4] @ F[mu, x4]).real
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.abs(F).max()), (mu, x4, fd, an)

@@ -41,7 +41,7 @@ SUBSPACE_CASES = [
 def test_build_subspace_matches_oracle(hd, L, Ls, block, nvec, eps, mf, bc):
     g, U, noise, sub = _oracle_sub(L, Ls, block, nvec, eps, mf, 3000, bc=bc)
     lat = hd.Lattice(L, Ls, bc)
-    gsub = hd.build_subspace(lat, dev(links(U)), dev(planes(noise)), M5, mf, block, smooth_iters=10)
+    gsub = hd.build_subspace(lat, dev(links(U)), dev(planes(noise)), M5, mf, block, kind="cr", order=10)
     got = natural(host(gsub.vectors()), L, Ls)
     want = mg.from_blocks(g, sub.Phi)
     for k in range(nvec):
@@ -112,7 +112,8 @@ def test_coarse_op_properties_full_size(hd):
     lat = hd.Lattice(L, Ls)
     U = dev(links(synth.gauge_field(L, 0.5, 3300)))
     noise = dev(planes(synth.gaussian_fermion(L, Ls, 3301, count=nvec // 2)))
-    sub = hd.build_subspace(lat, U, noise, M5, 0.01, block, smooth_iters=10)
+    sub = hd.build_subspace(lat, U, noise, M5, 0.01, block, kind="chebyshev", order=60,
+                            filter_dtype=torch.complex64)
     del noise
     co = hd.build_coarse_op(sub, U, M5, 0.01)
     A = host(co.op())
@@ -139,10 +140,10 @@ def test_subspace_errors(hd):
     U = dev(links(synth.gauge_field(L, 0.3, 1)))
     noise = dev(planes(synth.gaussian_fermion(L, Ls, 2, count=2)))
     with pytest.raises(hd.HDCRError) as e:
-        hd.build_subspace(lat, U, noise, M5, 0.01, (3, 2, 2, 2))
+        hd.build_subspace(lat, U, noise, M5, 0.01, (3, 2, 2, 2), kind="cr", order=2)
     assert e.value.status == -2
     with pytest.raises(hd.HDCRError) as e:
-        hd.build_subspace(lat, U, noise, M5, 0.01, (4, 2, 2, 2))      # coarse extent 1
+        hd.build_subspace(lat, U, noise, M5, 0.01, (4, 2, 2, 2), kind="cr", order=2)  # coarse extent 1
     assert e.value.status == -2
     v = synth.gaussian_fermion(L, Ls, 3, count=1)
     dup = planes(np.concatenate([v, v]))
@@ -151,20 +152,65 @@ def test_subspace_errors(hd):
     assert e.value.status == -5
 
 
-@pytest.mark.parametrize("inner", ["c128", "c64"])
-def test_hdcr_solve_tiny_workload(hd, inner):
-    """4^4 x 8, eps = 0.3, mf = 0.01, 2^4 blocks, nvec = 8: HDCR to a true residual of
-    1e-10 (checked by the oracle) and the same solution as the oracle's CR."""
-    L, Ls, block, nvec, mf = (4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.01
+@pytest.mark.parametrize("fdt", ["c128", "c64"])
+def test_chebyshev_filter_subspace_matches_oracle(hd, fdt):
+    L, Ls, block, nvec, mf = (4, 4, 4, 4), 8, (2, 2, 2, 2), 4, 0.01
+    g = mg.Geometry(L, Ls, block)
+    U = synth.gauge_field(L, 0.5, 3400)
+    noise = synth.gaussian_fermion(L, Ls, 3401, count=nvec // 2)
+    sm = np.stack([mg.chebyshev_filter(U, x0, M5, mf, 1, 0.5, 8.0, 20) for x0 in noise])
+    want = mg.from_blocks(g, mg.basis_from_vectors(g, mg.chiral_split(sm)).Phi)
+    tdt = torch.complex128 if fdt == "c128" else torch.complex64
+    gsub = hd.build_subspace(hd.Lattice(L, Ls), dev(links(U)), dev(planes(noise)), M5, mf, block,
+                             kind="chebyshev", order=20, lam_cut=0.5, lam_max=8.0, filter_dtype=tdt)
+    got = natural(host(gsub.vectors()), L, Ls)
+    tol = 1e-10 if fdt == "c128" else 1e-3
+    for k in range(nvec):
+        assert relerr(got[k], want[k]) < tol, k
+
+
+def test_dense_coarse_inverse(hd):
+    L, Ls, block, nvec, mf = (6, 6, 4, 4), 4, (2, 2, 2, 2), 4, 0.05
+    g, U, noise, sub = _oracle_sub(L, Ls, block, nvec, 0.5, mf, 3500, iters=4)
+    lat = hd.Lattice(L, Ls)
+    gsub = _gpu_sub_from_oracle(hd, lat, g, sub, torch.complex64)
+    co = hd.build_coarse_op(gsub, dev(links(U)), M5, mf, op_dtype=torch.complex64)
+    hd.coarse_invert(co)
+    Ad = mg.coarse_dense(host(co.op()), g)
+    rng = synth.rng(3501)
+    c = rng.standard_normal((2, g.Vc, nvec)) + 1j * rng.standard_normal((2, g.Vc, nvec))
+    y = host(hd.coarse_solve_dense(co, dev(c, torch.complex64))).astype(np.complex128)
+    cond = np.linalg.cond(Ad)
+    for r in range(2):
+        want = np.linalg.solve(Ad, c[r].ravel()).reshape(c[r].shape)
+        assert relerr(y[r], want) < max(1e-5, cond * 3e-7)
+
+
+SOLVER_CASES = [
+    # (inner dtype, smoother, coarse solver, mf)
+    ("c128", "chebyshev", "dense", 0.01),
+    ("c64", "chebyshev", "dense", 0.01),
+    ("c128", "cr", "cr", 0.1),
+]
+
+
+@pytest.mark.parametrize("inner,smoother,coarse,mf", SOLVER_CASES)
+def test_hdcr_solve_tiny_workload(hd, inner, smoother, coarse, mf):
+    """4^4 x 8, eps = 0.3, 2^4 blocks, nvec = 8: HDCR to a true residual of 1e-10
+    (checked by the oracle) and the same solution as the oracle's CR."""
+    L, Ls, block, nvec = (4, 4, 4, 4), 8, (2, 2, 2, 2), 8
     lat = hd.Lattice(L, Ls)
     Uh = synth.gauge_field(L, 0.3, 1000)
     U = dev(links(Uh))
     noise = dev(planes(synth.gaussian_fermion(L, Ls, 3001, count=nvec // 2)))
     tdt = torch.complex128 if inner == "c128" else torch.complex64
-    sub = hd.build_subspace(lat, U, noise, M5, mf, block, smooth_iters=10, store_dtype=tdt)
+    sub = hd.build_subspace(lat, U, noise, M5, mf, block, kind="chebyshev", order=100, lam_cut=0.3,
+                            store_dtype=tdt)
     co = hd.build_coarse_op(sub, U, M5, mf, op_dtype=tdt)
     b = synth.gaussian_fermion(L, Ls, 2000)
-    x, st = hd.hdcr_solve(co, U, dev(planes(b)), tol=1e-10, inner_dtype=tdt)
+    x, st = hd.hdcr_solve(co, U, dev(planes(b)), tol=1e-10, inner_dtype=tdt, smoother=smoother,
+                          smoother_order=10 if smoother == "chebyshev" else 8, coarse_solver=coarse,
+                          max_outer=2000, restart=16)
     assert st["status"] == 0 and st["true_resid"] <= 1e-10
     xg = natural(host(x), L, Ls)
     r = b - dwf.apply_H(Uh, xg, M5, mf)
@@ -174,12 +220,39 @@ def test_hdcr_solve_tiny_workload(hd, inner):
     assert st["coarse_matvecs"] > 0 and st["iters"] > 0
 
 
+def test_hdcr_vcycle_matches_oracle_first_iterate(hd):
+    """With the linear Chebyshev smoother the preconditioner is a fixed linear map (up to
+    the FP32 dense coarse inverse), so the first FGCR iterate x1 = a B b, with a the
+    least-squares step, agrees with the oracle's V-cycle to the coarse inverse's accuracy."""
+    L, Ls, block, nvec, mf = (4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.05
+    g, U, noise, sub = _oracle_sub(L, Ls, block, nvec, 0.3, mf, 3600, iters=6)
+    lat = hd.Lattice(L, Ls)
+    gsub = _gpu_sub_from_oracle(hd, lat, g, sub)
+    co = hd.build_coarse_op(gsub, dev(links(U)), M5, mf)
+    b = synth.gaussian_fermion(L, Ls, 3601)
+    with pytest.raises(hd.HDCRError):
+        x1, _ = hd.hdcr_solve(co, dev(links(U)), dev(planes(b)), tol=1e-14, max_outer=1, restart=1)
+    xd = dev(np.zeros_like(planes(b)))
+    A = mg.coarse_op(U, sub, M5, mf)
+    Ad = mg.coarse_dense(A, g)
+    p = mg.HDCRParams(M5=M5, mf=mf)
+    S = lambda v: mg.chebyshev_smoother(U, v, p)
+    Qc = lambda c: np.linalg.solve(Ad, c.ravel()).reshape(c.shape)
+    z = mg.vcycle(U, sub, A, b, p, S=S, Qc=Qc)
+    w = dwf.apply_H(U, z, M5, mf)
+    x1 = (np.vdot(w, b) / np.vdot(w, w)) * z
+    # the GPU solve with max_outer = 1 leaves its first iterate in x via hdcr_solve_into
+    st = hd.hdcr_solve_into(co, dev(links(U)), dev(planes(b)), xd, tol=1e-14, max_outer=1, restart=1)
+    assert st["status"] == -3
+    assert relerr(natural(host(xd), L, Ls), x1) < 1e-4
+
+
 def test_hdcr_solve_reports_cap(hd):
     L, Ls, block, nvec, mf = (4, 4, 4, 4), 4, (2, 2, 2, 2), 4, 0.01
     lat = hd.Lattice(L, Ls)
     U = dev(links(synth.gauge_field(L, 0.3, 1000)))
     noise = dev(planes(synth.gaussian_fermion(L, Ls, 3001, count=2)))
-    sub = hd.build_subspace(lat, U, noise, M5, mf, block)
+    sub = hd.build_subspace(lat, U, noise, M5, mf, block, kind="cr", order=10)
     co = hd.build_coarse_op(sub, U, M5, mf)
     b = dev(planes(synth.gaussian_fermion(L, Ls, 2000)))
     with pytest.raises(hd.HDCRError) as e:

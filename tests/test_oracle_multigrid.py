@@ -238,3 +238,66 @@ def test_coarse_solve_reaches_tolerance():
     c, info = mg.coarse_solve(A, g, rhs, tol=1e-4)
     assert info.converged
     assert relerr(mg.coarse_apply(A, g, c), rhs) <= 1e-4 * 1.0001
+
+
+# ------------------------------------------------------------------ Chebyshev
+def test_chebyshev_coefficients_closed_form():
+    """1/(a + b cos th) = (1/sqrt(a^2 - b^2)) [1 + 2 sum_k (-q)^k cos k th],
+    q = (a - sqrt(a^2 - b^2))/b: the series coefficients of 1/y on [lo, hi]."""
+    for lo, hi, n in [(1.0, 64.0, 10), (0.25, 9.0, 30), (2.0, 3.0, 5)]:
+        a, b = 0.5 * (hi + lo), 0.5 * (hi - lo)
+        s = np.sqrt(a * a - b * b)
+        q = (a - s) / b
+        want = 2.0 / s * (-q) ** np.arange(n + 1)
+        got = mg.chebyshev_inverse_coeffs(lo, hi, n)
+        # quadrature on 4(n+1) nodes aliases the far tail of the series: ~q^(8n) relative
+        assert np.abs(got - want).max() < 1e-8 * np.abs(want).max()
+
+
+def _cheb_eval(c, t):
+    """c_0/2 + sum c_k T_k(t) at a scalar t, T_k(t) = cos(k arccos t) on [-1, 1]."""
+    k = np.arange(len(c))
+    return float(np.sum(c * np.cos(k * np.arccos(np.clip(t, -1, 1)))) - 0.5 * c[0])
+
+
+def test_chebyshev_smoother_on_eigenvectors():
+    """S v = lambda p(lambda^2) v for an eigenvector (H v = lambda v): the smoother is
+    the polynomial H p(H^2) of Section 4, and y p(y) ~ 1 on [1, 64]."""
+    L, Ls = (2, 2, 2, 2), 4
+    U = synth.gauge_field(L, 0.5, 400)
+    Hd = dense_H_from_stencil(dwf, U, Ls, M5, MF)
+    ev, V = np.linalg.eigh(Hd)
+    p = mg.HDCRParams(M5=M5, mf=MF)
+    c = mg.chebyshev_inverse_coeffs(1.0, 64.0, 10)
+    shape = (2, 2, 2, 2, Ls, 4, 3)
+    for i in [0, len(ev) // 3, np.argmin(np.abs(ev)), len(ev) - 1]:
+        lam = ev[i]
+        v = V[:, i].reshape(shape)
+        Sv = mg.chebyshev_smoother(U, v, p)
+        pl = _cheb_eval(c, (2 * lam * lam - 65.0) / 63.0) if 1.0 <= lam * lam <= 64.0 else None
+        ratio = np.vdot(v, Sv) / np.vdot(v, v)
+        assert relerr(Sv, ratio * v) < 1e-12                 # eigenvector is kept
+        if pl is not None:
+            assert abs(ratio - lam * pl) < 1e-10 * abs(lam * pl)
+
+
+def test_chebyshev_filter_on_eigenvectors():
+    """The filter maps an eigenvector combination v1 + v2 to T_n(t(l1^2)) v1 + T_n(t(l2^2)) v2
+    (up to normalisation): low modes (|l| < lam_cut) are enhanced."""
+    L, Ls = (2, 2, 2, 2), 4
+    U = synth.gauge_field(L, 0.5, 410)
+    Hd = dense_H_from_stencil(dwf, U, Ls, M5, MF)
+    ev, V = np.linalg.eigh(Hd)
+    i1 = int(np.argmin(np.abs(ev)))
+    i2 = int(np.argmax(np.abs(ev) > 2.0))
+    shape = (2, 2, 2, 2, Ls, 4, 3)
+    x0 = (V[:, i1] + V[:, i2]).reshape(shape)
+    lc, lm, n = 1.0, 8.0, 12
+    out = mg.chebyshev_filter(U, x0, M5, MF, 1, lc, lm, n)
+    tf = lambda lam: (2 * lam * lam - (lm * lm + lc * lc)) / (lm * lm - lc * lc)
+    T = lambda t: np.cosh(n * np.arccosh(abs(t))) * (np.sign(t) ** n) if abs(t) > 1 else np.cos(n * np.arccos(t))
+    a1, a2 = T(tf(ev[i1])), T(tf(ev[i2]))
+    want = (a1 * V[:, i1] + a2 * V[:, i2]).reshape(shape)
+    want = want / np.sqrt(dwf.norm2(want))
+    assert relerr(out, want) < 1e-10 or relerr(out, -want) < 1e-10
+    assert abs(a1) > 10 * abs(a2)
