@@ -141,6 +141,24 @@ int hdcr_cdot(const void* u, const void* v, size_t n, int dtype, double* result,
               void* stream);
 int hdcr_norm2(const void* u, size_t n, int dtype, double* result, void* stream);
 
+/* hdcr_cdot_noalloc: the same inner product as hdcr_cdot, for callers that may
+ * not let the library allocate device memory -- for example code that runs
+ * while a CUDA graph is being captured (an allocation breaks the capture), or
+ * a caller that keeps the whole device memory budget in its own pool.  The
+ * paper has no counterpart: this is an interface of the library, not a step of
+ * the method.  Its scratch (one FP64 partial sum per 4096 entries and a
+ * completion counter, 1 MiB) is a fixed array compiled into the library, held
+ * on every GPU that loads the library until the process exits; the call
+ * allocates nothing and only launches kernels and clears the counter on
+ * ``stream``.  n may not exceed HDCR_NOALLOC_MAX_N (BAD_ARG otherwise).  The
+ * first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (different streams) race and
+ * give wrong results.  result: DEVICE pointer to 2 doubles. */
+#define HDCR_NOALLOC_MAX_N 268435456
+int hdcr_cdot_noalloc(const void* u, const void* v, size_t n, int dtype, double* result,
+                      void* stream);
+
 /* ---------------------------------------------------------------- CR solve
  * Conjugate residual (Section 3) on H x = b, unpreconditioned, all in ``dtype``
  * (inner products in FP64).  x holds the initial guess on entry.  Stops when the

@@ -63,7 +63,7 @@ def load_library():
 
 __all__ = [
     "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
-    "convert", "cdot", "norm2", "cr_solve", "cr_solve_into", "library_path",
+    "convert", "cdot", "cdot_noalloc", "norm2", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
     "hdcr_solve", "hdcr_solve_into", "gauge_force", "HDCRSolve", "solve_autograd",
@@ -208,6 +208,18 @@ def cdot(u: torch.Tensor, v: torch.Tensor, stream=None) -> complex:
     res = torch.empty(2, dtype=torch.float64, device=u.device)
     _check(_L.hdcr_cdot(_dev(u, "u"), _dev(v, "v"), u.numel(), _code(u), res.data_ptr(),
                         _stream(stream)), "cdot")
+    r = res.cpu()
+    return complex(float(r[0]), float(r[1]))
+
+
+def cdot_noalloc(u: torch.Tensor, v: torch.Tensor, stream=None) -> complex:
+    """<u, v> like cdot, through the entry point that allocates no device memory
+    (its scratch is a fixed array in the library; see hdcr_cdot_noalloc)."""
+    if u.dtype != v.dtype or u.numel() != v.numel():
+        raise ValueError("u and v must match in dtype and size")
+    res = torch.empty(2, dtype=torch.float64, device=u.device)
+    _check(_L.hdcr_cdot_noalloc(_dev(u, "u"), _dev(v, "v"), u.numel(), _code(u), res.data_ptr(),
+                                _stream(stream)), "cdot_noalloc")
     r = res.cpu()
     return complex(float(r[0]), float(r[1]))
 
