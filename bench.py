@@ -59,7 +59,7 @@ def bytes_per_site(real_bytes: int, Ls: int) -> float:
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal, profiling recipe)
 # DRAM traffic of one FP64 / FP32 stencil launch at 16^4 x 16 from ncu, with the hash of
 # the stencil sources it was measured on (reported as null once the sources change)
-NCU_TRAFFIC = {"f64": 450.68e6, "f32": 205.54e6, "src_hash": "cd9d5589615212bb"}
+NCU_TRAFFIC = {"f64": 453.58e6, "f32": 204.74e6, "src_hash": "cd9d5589615212bb"}
 
 
 def stencil_src_hash() -> str:
@@ -206,6 +206,34 @@ def hdcr_step(hd, lat, U, b, noise, inner="f64"):
     return x, F, st
 
 
+def step_breakdown(hd, lat, U, b, noise) -> dict:
+    """Wall time of each phase of one step, synchronising between phases (outside the timed region)."""
+    import torch
+    out = {}
+
+    def tick(name, t0):
+        torch.cuda.synchronize()
+        out[name] = round(time.perf_counter() - t0, 4)
+        return time.perf_counter()
+
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    sub = hd.build_subspace(lat, U, noise, M5, MF, BLOCK, filter_dtype=torch.complex64,
+                            store_dtype=torch.complex128, **FILTER)
+    t = tick("subspace_s", t)
+    co = hd.build_coarse_op(sub, U, M5, MF, op_dtype=torch.complex128)
+    t = tick("coarse_op_s", t)
+    hd.coarse_invert(co)
+    t = tick("coarse_invert_s", t)
+    x, st = hd.hdcr_solve(co, U, b, inner_dtype=torch.complex128, **SOLVE)
+    t = tick("solve_s", t)
+    hd.gauge_force(lat, x, hd.apply_gamma5_r5(lat, x))
+    tick("force_s", t)
+    co.close()
+    sub.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -257,6 +285,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     t_mixed = time.perf_counter() - t0
     sol_diff = float(torch.linalg.vector_norm(x - x_cr) / torch.linalg.vector_norm(x_cr))
+    phases = step_breakdown(hd, lat, U, b, noise)
     # FP32 stencil bandwidth (the second half of the metric)
     U32, b32 = U.to(torch.complex64), b.to(torch.complex64)
     y32 = torch.empty_like(b32)
@@ -314,6 +343,7 @@ def run_ours(args, world, rank, local):
                  "coarse_solves": stats[-1]["coarse_matvecs"], "true_resid": stats[-1]["true_resid"],
                  "solve_s": round(stats[-1]["t_total"], 4), "smoother_s": round(stats[-1]["t_smoother"], 4),
                  "coarse_s": round(stats[-1]["t_coarse"], 4)},
+        "step_phases": phases,
         "plain_fp64_cr": {"seconds": round(t_cr, 4), "iters": st_cr["iters"], "true_resid": st_cr["true_resid"],
                           "speedup_of_hdcr_step": round(t_cr / agg["seconds_per_unit"], 3),
                           "solution_rel_diff": sol_diff},

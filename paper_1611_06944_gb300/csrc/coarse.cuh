@@ -70,7 +70,7 @@ struct hdcr_coarse {
   int dtype;    // of A
   void* A;      // [Vc][9][nvec][nvec]
   int* nbr;     // [Vc][9] coarse site reached by each leg
-  void* Ainv;   // dense inverse (FP32 complex, (Vc*nvec)^2), built on demand
+  void* Ainv;   // dense inverse (FP32 complex, n = Vc*nvec, n x n) then its column gather index (n ints)
   double M5, mf;
   int device;
 };

@@ -8,18 +8,24 @@
 // stencil, inverted in place by Gauss-Jordan elimination with partial (row)
 // pivoting, and applied as a matrix-vector product.
 //
-// Elimination step k: one CTA finds the pivot row (largest |a_ik|, lowest
-// index on ties), swaps it into row k, saves column k and scales row k by the
-// inverse pivot; then the grid applies the rank-1 update to every other row.
-// The row interchanges are undone at the end by swapping columns in reverse
-// order.
+// Blocked elimination.  Step k of Gauss-Jordan multiplies the matrix from the
+// left by S_k (the row interchange) and E_k = I + u_k e_k^T, and overwrites
+// column k with E_k e_k.  For a panel of P consecutive steps the interchanges can
+// be moved to the front, so the panel acts on every other column j as
+// col_j <- (I + U K^T) col_j, K^T selecting the panel's rows and U (n x P)
+// accumulating the u_k (with later interchanges applied to its rows).  The P
+// steps on the panel's own columns run as one grid-wide launch each (a thread
+// per row; the last CTA to finish also picks the next pivot), then a tiled
+// complex GEMM applies the rank-P update to all other columns.  The row
+// interchanges amount to a permutation of the inverse's columns, which the
+// matrix-vector product applies as a gather of the input vector.
+#include <climits>
+#include <utility>
 #include <vector>
 
 #include "coarse.cuh"
 
 namespace hdcr {
-
-constexpr int GJ_THREADS = 1024;
 
 // assemble the dense matrix D[(a, j)][(b, k)] from the 9 legs (legs reaching the same b add up)
 __global__ void assemble_dense_kernel(const cpx<float>* __restrict__ A, const int* __restrict__ nbr, int Vc,
@@ -42,119 +48,266 @@ __global__ void assemble_dense_kernel(const cpx<float>* __restrict__ A, const in
   }
 }
 
-__global__ void __launch_bounds__(GJ_THREADS) gj_pivot_kernel(cpx<float>* __restrict__ M, int n, int k,
-                                                              cpx<float>* __restrict__ ck,
-                                                              cpx<float>* __restrict__ rk, int* __restrict__ perm,
-                                                              int* __restrict__ status) {
-  __shared__ float sv[GJ_THREADS / 32];
-  __shared__ int si[GJ_THREADS / 32];
-  __shared__ int piv;
-  __shared__ float ipr, ipi;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // argmax |M[i][k]|^2 over i >= k, lowest index on ties
-  float best = -1.f;
-  int bi = n;
-  for (int i = k + tid; i < n; i += GJ_THREADS) {
-    const cpx<float> v = M[(long long)i * n + k];
-    const float m = v.re * v.re + v.im * v.im;
-    if (m > best || (m == best && i < bi)) {
-      best = m;
-      bi = i;
-    }
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float ob = __shfl_down_sync(0xffffffffu, best, off);
-    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-    if (ob > best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
-    }
-  }
-  if (lane == 0) {
-    sv[warp] = best;
-    si[warp] = bi;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    float b = -1.f;
-    int ii = n;
-    for (int w = 0; w < GJ_THREADS / 32; ++w)
-      if (sv[w] > b || (sv[w] == b && si[w] < ii)) {
-        b = sv[w];
-        ii = si[w];
-      }
-    piv = ii;
-    perm[k] = ii;
-    if (!(b > 0.f) || !(b < 3.0e38f)) atomicExch(status, 1 + k);
-  }
-  __syncthreads();
-  const int p = piv;
-  if (p != k && p < n) {
-    for (int j = tid; j < n; j += GJ_THREADS) {
-      const cpx<float> a = M[(long long)k * n + j], b = M[(long long)p * n + j];
-      M[(long long)k * n + j] = b;
-      M[(long long)p * n + j] = a;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const cpx<float> d = M[(long long)k * n + k];
-    const float m = d.re * d.re + d.im * d.im;
-    const float inv = m > 0.f ? 1.f / m : 0.f;
-    ipr = d.re * inv;
-    ipi = -d.im * inv;
-  }
-  __syncthreads();
-  const float pr = ipr, pi = ipi;
-  for (int i = tid; i < n; i += GJ_THREADS) ck[i] = M[(long long)i * n + k];
-  __syncthreads();
-  for (int j = tid; j < n; j += GJ_THREADS) {
-    cpx<float> v;
-    if (j == k) {
-      v = cpx<float>(pr, pi);
-    } else {
-      const cpx<float> a = M[(long long)k * n + j];
-      v = cpx<float>(a.re * pr - a.im * pi, a.re * pi + a.im * pr);
-    }
-    rk[j] = v;
-    M[(long long)k * n + j] = v;
+constexpr int GJ_P = 32;      // panel width
+constexpr int GJ_TILE = 64;   // tile of the rank-P update (rows and columns)
+constexpr int GJ_ROWS = 64;   // rows (threads) per CTA of the panel kernels
+constexpr int GJ_MAX_N = 32768;
+constexpr int GJ_MAX_CTAS = GJ_MAX_N / GJ_ROWS;
+
+// Workspace of the elimination.  The panel is held column-major (element (i, c)
+// at c*n + i) so that a thread per row reads and writes coalesced, in two
+// buffers: step l reads buffer l&1 and writes buffer (l+1)&1, so no CTA
+// overwrites a row another CTA still has to read.
+struct GJWork {
+  cpx<float>* W[2];    // panel columns
+  cpx<float>* U[2];    // accumulated multipliers (column c < l filled after step l)
+  cpx<float>* T;       // panel rows of M after the interchanges, [GJ_P][n]
+  float* cand_m;       // per-CTA pivot candidates
+  int* cand_i;
+  unsigned int* counter;  // zero between launches
+  int* perm;           // perm[k]: row interchanged with row k at step k
+  int* status;         // 1 + k of the first zero or non-finite pivot
+};
+
+__device__ __forceinline__ float pivot_metric(cpx<float> v) {
+  const float m = v.re * v.re + v.im * v.im;
+  return m == m ? m : INFINITY;  // a NaN wins the search and is then reported
+}
+
+__device__ __forceinline__ void better(float& m, int& i, float om, int oi) {
+  if (om > m || (om == m && oi < i)) {
+    m = om;
+    i = oi;
   }
 }
 
-// M[i][j] -= ck[i] rk[j] (j != k), M[i][k] = -ck[i] rk[k], for every i != k
-__global__ void gj_update_kernel(cpx<float>* __restrict__ M, int n, int k, const cpx<float>* __restrict__ ck,
-                                 const cpx<float>* __restrict__ rk) {
-  const long long total = (long long)n * n;
+// argmax over the CTA (largest metric, lowest row on ties), then over the grid:
+// the last CTA to finish picks the pivot of step k and records it in perm[k]
+__device__ void pivot_select(float m, int i, int k, const GJWork& w) {
+  __shared__ float sm[GJ_ROWS / 32];
+  __shared__ int si[GJ_ROWS / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    better(m, i, __shfl_down_sync(0xffffffffu, m, off), __shfl_down_sync(0xffffffffu, i, off));
+  if (lane == 0) {
+    sm[warp] = m;
+    si[warp] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < GJ_ROWS / 32; ++q) better(m, i, sm[q], si[q]);
+    w.cand_m[blockIdx.x] = m;
+    w.cand_i[blockIdx.x] = i;
+    __threadfence();
+    last = atomicAdd(w.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  m = -1.f;
+  i = INT_MAX;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += GJ_ROWS) better(m, i, __ldcg(w.cand_m + b), __ldcg(w.cand_i + b));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    better(m, i, __shfl_down_sync(0xffffffffu, m, off), __shfl_down_sync(0xffffffffu, i, off));
+  __syncthreads();
+  if (lane == 0) {
+    sm[warp] = m;
+    si[warp] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < GJ_ROWS / 32; ++q) better(m, i, sm[q], si[q]);
+    if (!(m > 0.f) || !(m < 3.0e38f)) {
+      atomicCAS(w.status, 0, 1 + k);
+      i = k;  // carry on without an interchange; the result is discarded
+    }
+    w.perm[k] = i;
+    *w.counter = 0u;
+  }
+}
+
+// Start of a panel: W = M[:, k0:k0+pw] (zero beyond pw), U = 0, pivot of step k0.
+__global__ void __launch_bounds__(GJ_ROWS) gj_panel_init_kernel(const cpx<float>* __restrict__ M, int n, int k0,
+                                                                int pw, GJWork w) {
+  const int i = blockIdx.x * GJ_ROWS + threadIdx.x;
+  float m = -1.f;
+  int bi = INT_MAX;
+  if (i < n) {
+    const cpx<float>* row = M + (long long)i * n + k0;
+#pragma unroll 8
+    for (int c = 0; c < GJ_P; ++c) {
+      const cpx<float> v = c < pw ? row[c] : cpx<float>(0.f, 0.f);
+      w.W[0][(long long)c * n + i] = v;
+      w.U[0][(long long)c * n + i] = cpx<float>(0.f, 0.f);
+      w.U[1][(long long)c * n + i] = cpx<float>(0.f, 0.f);
+      if (c == 0 && i >= k0) {
+        m = pivot_metric(v);
+        bi = i;
+      }
+    }
+  }
+  pivot_select(m, bi, k0, w);
+}
+
+// Step k = k0 + l of the panel.  Rows k and p = perm[k] are interchanged on the
+// fly (each CTA reads both from the input buffer), then every row i gets
+//   u_i = -W[i][l] / W[k][l]  (u_k = 1 / W[k][l] - 1),
+//   W[i][c] += u_i W[k][c] for c != l,  W[i][l] = [i == k] + u_i,
+//   U[i][c] += u_i U[k][c] for c < l,   U[i][l] = u_i,
+// and the CTAs together pick the pivot of step k + 1 from the new column l + 1.
+__global__ void __launch_bounds__(GJ_ROWS) gj_step_kernel(int n, int k0, int l, int pw, GJWork w) {
+  __shared__ cpx<float> rk[GJ_P], ruk[GJ_P];  // new row k (old row p)
+  __shared__ cpx<float> rp[GJ_P], rup[GJ_P];  // new row p (old row k)
+  const int k = k0 + l;
+  const int p = w.perm[k];
+  const bool odd = l & 1;
+  const cpx<float>* __restrict__ Win = odd ? w.W[1] : w.W[0];
+  const cpx<float>* __restrict__ Uin = odd ? w.U[1] : w.U[0];
+  cpx<float>* __restrict__ Wout = odd ? w.W[0] : w.W[1];
+  cpx<float>* __restrict__ Uout = odd ? w.U[0] : w.U[1];
+  const int t = threadIdx.x;
+  if (t < GJ_P) {
+    rk[t] = Win[(long long)t * n + p];
+    ruk[t] = Uin[(long long)t * n + p];
+    rp[t] = Win[(long long)t * n + k];
+    rup[t] = Uin[(long long)t * n + k];
+  }
+  __syncthreads();
+  const cpx<float> d = rk[l];
+  const float dm = d.re * d.re + d.im * d.im;
+  const float inv = dm > 0.f ? 1.f / dm : 0.f;
+  const cpx<float> pinv(d.re * inv, -d.im * inv);
+  const int i = blockIdx.x * GJ_ROWS + t;
+  float m = -1.f;
+  int bi = INT_MAX;
+  if (i < n) {
+    const bool is_k = i == k, is_p = i == p && p != k;
+    const cpx<float>* src = Win + i;
+    const cpx<float>* srcu = Uin + i;
+    auto wsrc = [&](int c) { return is_k ? rk[c] : (is_p ? rp[c] : src[(long long)c * n]); };
+    auto usrc = [&](int c) { return is_k ? ruk[c] : (is_p ? rup[c] : srcu[(long long)c * n]); };
+    const cpx<float> wl = wsrc(l);
+    const cpx<float> u = is_k ? cpx<float>(pinv.re - 1.f, pinv.im)
+                              : cpx<float>(-(wl.re * pinv.re - wl.im * pinv.im), -(wl.re * pinv.im + wl.im * pinv.re));
+#pragma unroll 8
+    for (int c = 0; c < GJ_P; ++c) {
+      cpx<float> v;
+      if (c == l) {
+        v = cpx<float>(u.re + (is_k ? 1.f : 0.f), u.im);
+      } else {
+        v = wsrc(c);
+        const cpx<float> r = rk[c];
+        v.re += u.re * r.re - u.im * r.im;
+        v.im += u.re * r.im + u.im * r.re;
+      }
+      Wout[(long long)c * n + i] = v;
+      if (c == l + 1 && i > k) {
+        m = pivot_metric(v);
+        bi = i;
+      }
+    }
+    for (int c = 0; c < l; ++c) {
+      cpx<float> v = usrc(c);
+      const cpx<float> r = ruk[c];
+      v.re += u.re * r.re - u.im * r.im;
+      v.im += u.re * r.im + u.im * r.re;
+      Uout[(long long)c * n + i] = v;
+    }
+    Uout[(long long)l * n + i] = u;
+  }
+  if (l + 1 < pw) pivot_select(m, bi, k + 1, w);
+}
+
+// End of a panel: the panel's row interchanges on every column outside it (a
+// thread per column applies them in order), the panel's rows copied to T, and
+// the eliminated panel columns written back into M.
+__global__ void gj_panel_apply_kernel(cpx<float>* __restrict__ M, int n, int k0, int pw,
+                                      const cpx<float>* __restrict__ Wfin, GJWork w) {
+  const long long total = (long long)n + (long long)n * pw;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / n);
-    if (i == k) continue;
-    const int j = (int)(e - (long long)i * n);
-    const cpx<float> c = ck[i], r = rk[j];
-    if (j == k) {
-      M[e] = cpx<float>(-(c.re * r.re - c.im * r.im), -(c.re * r.im + c.im * r.re));
+    if (e < n) {
+      const int j = (int)e;
+      if (j >= k0 && j < k0 + pw) continue;
+      for (int l = 0; l < pw; ++l) {
+        const int k = k0 + l, p = w.perm[k];
+        if (p != k) {
+          const cpx<float> a = M[(long long)k * n + j], b = M[(long long)p * n + j];
+          M[(long long)k * n + j] = b;
+          M[(long long)p * n + j] = a;
+        }
+      }
+      for (int l = 0; l < pw; ++l) w.T[(long long)l * n + j] = M[(long long)(k0 + l) * n + j];
     } else {
-      cpx<float> m = M[e];
-      m.re -= c.re * r.re - c.im * r.im;
-      m.im -= c.re * r.im + c.im * r.re;
-      M[e] = m;
+      const long long f = e - n;
+      const int c = (int)(f / n), i = (int)(f - (long long)c * n);
+      M[(long long)i * n + k0 + c] = Wfin[f];
     }
   }
 }
 
-__global__ void swap_columns_kernel(cpx<float>* __restrict__ M, int n, int a, int b) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const cpx<float> u = M[(long long)i * n + a], v = M[(long long)i * n + b];
-    M[(long long)i * n + a] = v;
-    M[(long long)i * n + b] = u;
+// M[i][j] += sum_c U[i][c] T[c][j] for every j outside the panel (64 x 64 tiles, 4 x 4 per thread)
+__global__ void __launch_bounds__(256) gj_update_tiled_kernel(cpx<float>* __restrict__ M, int n, int k0, int pw,
+                                                              const cpx<float>* __restrict__ Ufin,
+                                                              const cpx<float>* __restrict__ T) {
+  __shared__ cpx<float> sU[GJ_P][GJ_TILE + 1];
+  __shared__ cpx<float> sT[GJ_P][GJ_TILE];
+  const int i0 = blockIdx.y * GJ_TILE, j0 = blockIdx.x * GJ_TILE;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < GJ_P * GJ_TILE; e += 256) {
+    const int c = e / GJ_TILE, r = e % GJ_TILE;
+    const int i = i0 + r;
+    sU[c][r] = (i < n && c < pw) ? Ufin[(long long)c * n + i] : cpx<float>(0.f, 0.f);
+    const int j = j0 + r;
+    sT[c][r] = (j < n && c < pw) ? T[(long long)c * n + j] : cpx<float>(0.f, 0.f);
+  }
+  __syncthreads();
+  const int ty = tid / 16, tx = tid % 16;
+  float ar[4][4], ai[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = 0.f;
+  for (int c = 0; c < GJ_P; ++c) {
+    cpx<float> u[4], t[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) u[a] = sU[c][ty + 16 * a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) t[b] = sT[c][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        ar[a][b] = fmaf(u[a].re, t[b].re, ar[a][b]);
+        ar[a][b] = fmaf(-u[a].im, t[b].im, ar[a][b]);
+        ai[a][b] = fmaf(u[a].re, t[b].im, ai[a][b]);
+        ai[a][b] = fmaf(u[a].im, t[b].re, ai[a][b]);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= n) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j >= n || (j >= k0 && j < k0 + pw)) continue;
+      cpx<float> m = M[(long long)i * n + j];
+      m.re += ar[a][b];
+      m.im += ai[a][b];
+      M[(long long)i * n + j] = m;
+    }
   }
 }
 
-// y[r] = M x[r] (vectors in R, matrix FP32); one warp per row, coalesced row reads
+// y[r] = M x[r][pi] (vectors in R, matrix FP32, pi the column gather index);
+// one warp per row, coalesced row reads
 template <typename R>
-__global__ void dense_gemv_kernel(const cpx<float>* __restrict__ M, int n, const cpx<R>* __restrict__ x,
-                                  cpx<R>* __restrict__ y, int nrhs) {
+__global__ void dense_gemv_kernel(const cpx<float>* __restrict__ M, const int* __restrict__ pi, int n,
+                                  const cpx<R>* __restrict__ x, cpx<R>* __restrict__ y, int nrhs) {
   const int warps = blockDim.x >> 5;
   const int lane = threadIdx.x & 31;
   const long long row0 = (long long)blockIdx.x * warps + (threadIdx.x >> 5);
@@ -166,7 +319,7 @@ __global__ void dense_gemv_kernel(const cpx<float>* __restrict__ M, int n, const
     float sr = 0.f, si = 0.f;
     for (int j = lane; j < n; j += 32) {
       const cpx<float> m = row[j];
-      const cpx<R> v = ld(xv + j);
+      const cpx<R> v = ld(xv + __ldg(pi + j));
       const float vr = (float)v.re, vi = (float)v.im;
       sr = fmaf(m.re, vr, sr);
       sr = fmaf(-m.im, vi, sr);
@@ -186,8 +339,9 @@ template <typename R>
 int launch_dense_solve(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st) {
   const int n = co->bg.Vc * co->nvec;
   const long long rows = (long long)n * nrhs;
-  dense_gemv_kernel<R><<<num_blocks(rows, 8, 152 * 16), 256, 0, st>>>((const cpx<float>*)co->Ainv, n, in, out,
-                                                                       nrhs); count_launch();
+  const cpx<float>* M = (const cpx<float>*)co->Ainv;
+  dense_gemv_kernel<R><<<num_blocks(rows, 8, 152 * 16), 256, 0, st>>>(M, (const int*)(M + (long long)n * n), n, in,
+                                                                       out, nrhs); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -197,38 +351,56 @@ template int launch_dense_solve<float>(const hdcr_coarse*, const cpx<float>*, cp
 int coarse_invert(hdcr_coarse* co, cudaStream_t st) {
   const int Vc = co->bg.Vc, nvec = co->nvec;
   const long long n = (long long)Vc * nvec;
-  if (n > 32768) {
-    set_error("dense coarse inverse: %lld unknowns above the supported 32768", n);
+  if (n > GJ_MAX_N) {
+    set_error("dense coarse inverse: %lld unknowns above the supported %d", n, GJ_MAX_N);
     return HDCR_ERR_BAD_ARG;
   }
   if (co->Ainv) return HDCR_OK;
+  // the inverse (n x n, FP32 complex) followed by its column gather index (n ints)
   const size_t mbytes = sizeof(cpx<float>) * (size_t)n * n;
   void* M = nullptr;
   void* aux = nullptr;
-  HDCR_CUDA_TRY(cudaMalloc(&M, mbytes));
-  const size_t abytes = sizeof(cpx<float>) * (size_t)(2 * n + (long long)Vc * NLEGS * nvec * nvec) +
-                        sizeof(int) * (size_t)(n + 1) + 1024;
+  HDCR_CUDA_TRY(cudaMalloc(&M, mbytes + sizeof(int) * (size_t)n));
+  const long long na = (long long)Vc * NLEGS * nvec * nvec;
+  const size_t abytes = sizeof(cpx<float>) * (size_t)(5 * n * GJ_P + na) +
+                        sizeof(float) * GJ_MAX_CTAS + sizeof(int) * (size_t)(GJ_MAX_CTAS + n + 2) + 256;
   cudaError_t e = cudaMalloc(&aux, abytes);
   if (e != cudaSuccess) {
     cudaFree(M);
     return cuda_status(e, "dense coarse inverse workspace");
   }
-  cpx<float>* ck = (cpx<float>*)aux;
-  cpx<float>* rk = ck + n;
-  cpx<float>* A32 = rk + n;
-  int* perm = (int*)(A32 + (long long)Vc * NLEGS * nvec * nvec);
-  int* status = perm + n;
+  GJWork w;
+  cpx<float>* base = (cpx<float>*)aux;
+  w.W[0] = base;
+  w.W[1] = base + n * GJ_P;
+  w.U[0] = base + 2 * n * GJ_P;
+  w.U[1] = base + 3 * n * GJ_P;
+  w.T = base + 4 * n * GJ_P;
+  cpx<float>* A32 = base + 5 * n * GJ_P;
+  w.cand_m = (float*)(A32 + na);
+  w.cand_i = (int*)(w.cand_m + GJ_MAX_CTAS);
+  w.perm = w.cand_i + GJ_MAX_CTAS;
+  w.status = w.perm + n;
+  w.counter = (unsigned int*)(w.status + 1);
   int s = HDCR_OK;
-  cudaMemsetAsync(M, 0, mbytes, st);
-  cudaMemsetAsync(status, 0, sizeof(int), st);
-  s = launch_convert(co->A, co->dtype, A32, HDCR_C64, (long long)Vc * NLEGS * nvec * nvec, st);
+  e = cudaMemsetAsync(M, 0, mbytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st);  // status and counter
+  if (e != cudaSuccess) s = cuda_status(e, "dense coarse inverse: clear");
+  if (s == HDCR_OK) s = launch_convert(co->A, co->dtype, A32, HDCR_C64, na, st);
   if (s == HDCR_OK) {
-    assemble_dense_kernel<<<num_blocks((long long)Vc * NLEGS * nvec * nvec, 256, 8192), 256, 0, st>>>(
-        A32, co->nbr, Vc, nvec, (cpx<float>*)M); count_launch();
-    const int ub = num_blocks(n * n, 256, 152 * 16);
-    for (int k = 0; k < n; ++k) {
-      gj_pivot_kernel<<<1, GJ_THREADS, 0, st>>>((cpx<float>*)M, (int)n, k, ck, rk, perm, status); count_launch();
-      gj_update_kernel<<<ub, 256, 0, st>>>((cpx<float>*)M, (int)n, k, ck, rk); count_launch();
+    assemble_dense_kernel<<<num_blocks(na, 256, 8192), 256, 0, st>>>(A32, co->nbr, Vc, nvec, (cpx<float>*)M); count_launch();
+    const int tiles = (int)((n + GJ_TILE - 1) / GJ_TILE);
+    const int ctas = (int)((n + GJ_ROWS - 1) / GJ_ROWS);
+    for (long long k0 = 0; k0 < n; k0 += GJ_P) {
+      const int pw = (int)(n - k0 < GJ_P ? n - k0 : GJ_P);
+      gj_panel_init_kernel<<<ctas, GJ_ROWS, 0, st>>>((const cpx<float>*)M, (int)n, (int)k0, pw, w); count_launch();
+      for (int l = 0; l < pw; ++l) {
+        gj_step_kernel<<<ctas, GJ_ROWS, 0, st>>>((int)n, (int)k0, l, pw, w); count_launch();
+      }
+      gj_panel_apply_kernel<<<num_blocks(n + n * pw, 256, 4096), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw,
+                                                                               w.W[pw & 1], w); count_launch();
+      gj_update_tiled_kernel<<<dim3(tiles, tiles), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw, w.U[pw & 1],
+                                                                  w.T); count_launch();
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) s = cuda_status(e, "Gauss-Jordan elimination");
@@ -236,8 +408,8 @@ int coarse_invert(hdcr_coarse* co, cudaStream_t st) {
   std::vector<int> hperm(n);
   int hstatus = 0;
   if (s == HDCR_OK) {
-    e = cudaMemcpyAsync(hperm.data(), perm, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(hperm.data(), w.perm, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, w.status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = cuda_status(e, "Gauss-Jordan pivots");
   }
@@ -246,10 +418,15 @@ int coarse_invert(hdcr_coarse* co, cudaStream_t st) {
     s = HDCR_ERR_NONFINITE;
   }
   if (s == HDCR_OK) {
-    for (long long k = n - 1; k >= 0; --k)
-      if (hperm[k] != k)
-        swap_columns_kernel<<<num_blocks(n, 256, 1024), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k, hperm[k]); count_launch();
-    e = cudaStreamSynchronize(st);
+    // Undoing the interchanges (columns k <-> perm[k], k from n-1 down to 0) makes
+    // column j of the inverse column idx[j] of M; M x[pi] with pi = idx^{-1}
+    // then equals the inverse applied to x.
+    std::vector<int> idx(n), pi(n);
+    for (long long j = 0; j < n; ++j) idx[j] = (int)j;
+    for (long long k = n - 1; k >= 0; --k) std::swap(idx[k], idx[hperm[k]]);
+    for (long long j = 0; j < n; ++j) pi[idx[j]] = (int)j;
+    e = cudaMemcpyAsync((char*)M + mbytes, pi.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = cuda_status(e, "dense coarse inverse");
   }
   cudaFree(aux);
