@@ -100,6 +100,9 @@ unsigned long long hdcr_launch_count(void);
  * for the recorded events. */
 int hdcr_stencil_timer(int enable);
 int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* launches, long long* sites);
+/* Every application of H of one precision since the timer was started,
+ * including those beyond the 16384 that carry events: launches and 5d sites. */
+int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites);
 
 /* ---------------------------------------------------------------- fine operator
  * hdcr_apply_g5dwf: out = H in with H = Gamma5 D_dwf = gamma5 R5 D_dwf

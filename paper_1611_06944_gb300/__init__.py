@@ -48,13 +48,18 @@ def stencil_timer(enable: bool) -> None:
 
 
 def stencil_timer_read(dtype: torch.dtype) -> dict:
-    """Recorded stencil launches of one precision: device ms, launches, 5d sites."""
+    """Stencil launches of one precision since the timer started: device ms, launches and
+    5d sites of those that carry events, and all launches and sites (``all_*``)."""
     ms = ctypes.c_double()
     nl = ctypes.c_longlong()
     ns = ctypes.c_longlong()
     _check(_L.hdcr_stencil_timer_read(_dt(dtype), ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ns)),
            "stencil_timer_read")
-    return {"ms": ms.value, "launches": nl.value, "sites": ns.value}
+    al = ctypes.c_longlong()
+    asites = ctypes.c_longlong()
+    _check(_L.hdcr_stencil_timer_count(_dt(dtype), ctypes.byref(al), ctypes.byref(asites)), "stencil_timer_count")
+    return {"ms": ms.value, "launches": nl.value, "sites": ns.value, "all_launches": al.value,
+            "all_sites": asites.value}
 
 
 def load_library():

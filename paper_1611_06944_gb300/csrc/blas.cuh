@@ -12,6 +12,12 @@ template <typename R>
 int launch_gamma5_r5(const Geom& g, const void* in, void* out, int nfields, cudaStream_t st);
 int launch_convert(const void* in, int idt, void* out, int odt, long long n, cudaStream_t st);
 
+// FP32 operator on the packed two-site kernel (dwf_x2.cu); with rs non-null it
+// also reduces Re <in, H in> into *result.  g5dwf_x2_ok says whether it applies.
+bool g5dwf_x2_ok(const Geom& g, const void* in, const void* out);
+int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in, cpx<float>* out,
+                    int nrhs, RedScratch* rs, double* result, cudaStream_t st);
+
 template <typename R>
 int launch_cdot(const void* u, const void* v, long long n, RedScratch rs, double* result, cudaStream_t st);
 template <typename R>

@@ -197,6 +197,12 @@ int launch_g5dwf_dot(const Geom& g, double M5, double mf, const cpx<R>* U, const
                      cpx<R>* out, RedScratch rs, double* result, cudaStream_t st) {
   int slot;
   stencil_timer_begin(sizeof(R) == 8 ? 0 : 1, g.V5, st, &slot);
+  if (sizeof(R) == 4 && g5dwf_x2_ok(g, in, out)) {
+    const int s = launch_g5dwf_x2(g, M5, mf, (const cpx<float>*)U, (const cpx<float>*)in, (cpx<float>*)out, 1, &rs,
+                                  result, st);
+    stencil_timer_end(slot, st);
+    return s;
+  }
   HDCR_DISPATCH_LS(g.Ls, (g5dwf_dot_kernel<R, LSC><<<red_blocks(g.V5 * 4), RED_THREADS, 0, st>>>(
                              g, (R)(5.0 - M5), (R)mf, U, in, out, rs, result)));
   stencil_timer_end(slot, st);

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <vector>
 
+#include "blas.cuh"
 #include "dwf_stencil.cuh"
 
 namespace hdcr {
@@ -97,6 +98,8 @@ struct StencilTimer {
   std::vector<int> kind;        // 0 = FP64, 1 = FP32
   std::vector<long long> sites;
   int used = 0;
+  long long all_launches[2] = {0, 0};  // every launch while enabled, timed or not
+  long long all_sites[2] = {0, 0};
 };
 StencilTimer g_timer;
 }  // namespace
@@ -104,7 +107,10 @@ StencilTimer g_timer;
 void stencil_timer_begin(int kind, long long sites, cudaStream_t st, int* slot) {
   *slot = -1;
   std::lock_guard<std::mutex> lock(g_timer.mu);
-  if (!g_timer.enabled || g_timer.used >= TIMER_PAIRS) return;
+  if (!g_timer.enabled) return;
+  g_timer.all_launches[kind]++;
+  g_timer.all_sites[kind] += sites;
+  if (g_timer.used >= TIMER_PAIRS) return;
   const int i = g_timer.used++;
   if ((int)g_timer.kind.size() <= i) {
     cudaEvent_t a, b;
@@ -137,6 +143,12 @@ int launch_g5dwf(const Geom& g, double M5, double mf, const void* U, const void*
   const long long n = g.V5 * nrhs;
   int slot;
   stencil_timer_begin(sizeof(R) == 8 ? 0 : 1, n, st, &slot);
+  if (sizeof(R) == 4 && g5dwf_x2_ok(g, in, out)) {
+    const int s = launch_g5dwf_x2(g, M5, mf, (const cpx<float>*)U, (const cpx<float>*)in, (cpx<float>*)out, nrhs,
+                                  nullptr, nullptr, st);
+    stencil_timer_end(slot, st);
+    return s;
+  }
   HDCR_DISPATCH_LS(g.Ls, (g5dwf_kernel<R, LSC><<<num_blocks(n, threads), threads, 0, st>>>(
                              g, (R)(5.0 - M5), (R)mf, (const cpx<R>*)U, (const cpx<R>*)in, (cpx<R>*)out, nrhs)));
   stencil_timer_end(slot, st);
@@ -272,7 +284,23 @@ extern "C" int hdcr_convert(const void* in, int in_dtype, void* out, int out_dty
 extern "C" int hdcr_stencil_timer(int enable) {
   std::lock_guard<std::mutex> lock(g_timer.mu);
   g_timer.enabled = enable != 0;
-  g_timer.used = 0;
+  if (g_timer.enabled) {
+    g_timer.used = 0;
+    g_timer.all_launches[0] = g_timer.all_launches[1] = 0;
+    g_timer.all_sites[0] = g_timer.all_sites[1] = 0;
+  }
+  return HDCR_OK;
+}
+
+extern "C" int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites) {
+  if (!launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64)) {
+    set_error("hdcr_stencil_timer_count: bad arguments");
+    return HDCR_ERR_BAD_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_timer.mu);
+  const int k = dtype == HDCR_C128 ? 0 : 1;
+  *launches = g_timer.all_launches[k];
+  *sites = g_timer.all_sites[k];
   return HDCR_OK;
 }
 

@@ -1,0 +1,323 @@
+// FP32 fine operator H = Gamma5 D_dwf (Section 3) on the packed FP32 pipe.
+//
+// Each thread owns the two fifth-dimension sites (s, s+1), s even, of one 4d
+// site and keeps every complex number of the pair as two float2 lanes
+// (re_s, re_s+1) and (im_s, im_s+1).  The two sites see the same gauge link,
+// so the SU(3) multiply of a hop is one packed FMA per real multiply-add for
+// both sites (fma.rn.f32x2), and each spinor component is one 16-byte load of
+// two consecutive complex numbers of the psi[x4][c][s] layout.
+//
+// A CTA covers 16 4d sites (one x-row of a 16^4 lattice, so the +-x neighbours
+// of its rows are its own) and all their fifth-dimension pairs.  The neighbour
+// indices, boundary factors and link offsets of its sites are worked out once
+// into shared memory; the link elements themselves are read straight from
+// global memory, where the Ls/2 threads of a 4d site read the same address (one
+// broadcast per quarter warp, served by L1).  Staging the links in shared
+// memory instead, or sharing them between the threads with shuffles, measured
+// slower on GB300.
+//
+// The projection onto the two-spinor h of a hop and the fifth-dimension terms
+// are formed lane by lane in scalar FP32 (they write the packed registers
+// directly); the lower spin components are accumulated with the sign of Gamma5
+// already applied, and the store writes the pair at Ls-2-s with its lanes
+// swapped (the R5 reflection).
+#include "dwf_stencil.cuh"
+#include "reduce.cuh"
+
+namespace hdcr {
+
+constexpr int X2_SITES = 16;   // 4d sites per CTA
+constexpr int X2_MAX_LP = 8;   // fifth-dimension pairs per 4d site (Ls <= 16: at most 128 threads)
+
+struct cx2 {
+  float2 re, im;  // lanes: sites s and s+1
+};
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ float4 ld4(const cpx<float>* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+// a + S b and a + S i b for the pair (a, b given as two consecutive complex numbers)
+template <int S>
+__device__ __forceinline__ cx2 comb(float4 a, float4 b) {
+  cx2 h;
+  h.re = make_float2(a.x + S * b.x, a.z + S * b.z);
+  h.im = make_float2(a.y + S * b.y, a.w + S * b.w);
+  return h;
+}
+template <int S>
+__device__ __forceinline__ cx2 comb_i(float4 a, float4 b) {
+  cx2 h;
+  h.re = make_float2(a.x - S * b.y, a.z - S * b.w);
+  h.im = make_float2(a.y + S * b.x, a.w + S * b.z);
+  return h;
+}
+
+// acc_up += coef hp,  acc_lo -= cl lo  (lower accumulated with the Gamma5 sign),
+// for one hop (MU, SIGN): h = (1 -+ gamma_mu) projection of the neighbour pair
+// at nb, hp = U h (SIGN > 0) or U^dag h (SIGN < 0) with the link L (row-major 3x3).
+template <int MU, int SIGN>
+__device__ __forceinline__ void hop_x2(const cpx<float>* __restrict__ L, const cpx<float>* __restrict__ nb, int ls,
+                                       float coef, cx2 (&up)[2][3], cx2 (&lo)[2][3]) {
+  cx2 h[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float4 u0 = ld4(nb + (0 + c) * ls), u1 = ld4(nb + (3 + c) * ls);
+    const float4 d0 = ld4(nb + (6 + c) * ls), d1 = ld4(nb + (9 + c) * ls);
+    constexpr int S = SIGN;
+    if (MU == 3) {
+      h[0][c] = comb<-S>(u0, d0);
+      h[1][c] = comb<-S>(u1, d1);
+    } else if (MU == 0) {
+      h[0][c] = comb_i<S>(u0, d1);
+      h[1][c] = comb_i<S>(u1, d0);
+    } else if (MU == 1) {
+      h[0][c] = comb<S>(u0, d1);
+      h[1][c] = comb<-S>(u1, d0);
+    } else {
+      h[0][c] = comb_i<S>(u0, d0);
+      h[1][c] = comb_i<-S>(u1, d1);
+    }
+  }
+  // hp = U h (forward) or U^dag h (backward); each element broadcast to both lanes
+  cx2 hp[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 pr[2], nr[2], pi[2], ni[2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const cpx<float> lc = ld(L + (SIGN > 0 ? 3 * a + b : 3 * b + a));
+      const float4 l = make_float4(lc.re, lc.re, lc.im, lc.im);
+      const float2 mr = make_float2(l.x, l.y), mi = make_float2(l.z, l.w);
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        const cx2 x = h[sp][b];
+        if (SIGN > 0) {  // re = mr xr - mi xi, im = mr xi + mi xr
+          pr[sp] = b == 0 ? mul2(mr, x.re) : fma2(mr, x.re, pr[sp]);
+          nr[sp] = b == 0 ? mul2(mi, x.im) : fma2(mi, x.im, nr[sp]);
+          pi[sp] = b == 0 ? mul2(mr, x.im) : fma2(mr, x.im, pi[sp]);
+          pi[sp] = fma2(mi, x.re, pi[sp]);
+        } else {  // conj: re = mr xr + mi xi, im = mr xi - mi xr
+          pr[sp] = b == 0 ? mul2(mr, x.re) : fma2(mr, x.re, pr[sp]);
+          pr[sp] = fma2(mi, x.im, pr[sp]);
+          pi[sp] = b == 0 ? mul2(mr, x.im) : fma2(mr, x.im, pi[sp]);
+          ni[sp] = b == 0 ? mul2(mi, x.re) : fma2(mi, x.re, ni[sp]);
+        }
+      }
+    }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      if (SIGN > 0) {
+        hp[sp][a].re = sub2(pr[sp], nr[sp]);
+        hp[sp][a].im = pi[sp];
+      } else {
+        hp[sp][a].re = pr[sp];
+        hp[sp][a].im = sub2(pi[sp], ni[sp]);
+      }
+    }
+  }
+  // upper += coef hp; true lower += cl lo with cl = -coef (SIGN > 0) or +coef,
+  // lo = hp (t) or i sigma_mu hp; the stored lower is minus the true one
+  const float2 cp = f2(coef), cm = f2(-coef);
+  const float2 gl = SIGN > 0 ? cp : cm;  // -cl: factor on lo for the negated lower
+  const float2 gn = SIGN > 0 ? cm : cp;  // +cl
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      up[sp][c].re = fma2(cp, hp[sp][c].re, up[sp][c].re);
+      up[sp][c].im = fma2(cp, hp[sp][c].im, up[sp][c].im);
+    }
+    const cx2 a = hp[0][c], b = hp[1][c];
+    if (MU == 3) {  // lo = (a, b)
+      lo[0][c].re = fma2(gl, a.re, lo[0][c].re);
+      lo[0][c].im = fma2(gl, a.im, lo[0][c].im);
+      lo[1][c].re = fma2(gl, b.re, lo[1][c].re);
+      lo[1][c].im = fma2(gl, b.im, lo[1][c].im);
+    } else if (MU == 0) {  // lo = (i b, i a):  (i z) = (-z.im, z.re)
+      lo[0][c].re = fma2(gn, b.im, lo[0][c].re);
+      lo[0][c].im = fma2(gl, b.re, lo[0][c].im);
+      lo[1][c].re = fma2(gn, a.im, lo[1][c].re);
+      lo[1][c].im = fma2(gl, a.re, lo[1][c].im);
+    } else if (MU == 1) {  // lo = (b, -a)
+      lo[0][c].re = fma2(gl, b.re, lo[0][c].re);
+      lo[0][c].im = fma2(gl, b.im, lo[0][c].im);
+      lo[1][c].re = fma2(gn, a.re, lo[1][c].re);
+      lo[1][c].im = fma2(gn, a.im, lo[1][c].im);
+    } else {  // lo = (i a, -i b):  (-i z) = (z.im, -z.re)
+      lo[0][c].re = fma2(gn, a.im, lo[0][c].re);
+      lo[0][c].im = fma2(gl, a.re, lo[0][c].im);
+      lo[1][c].re = fma2(gl, b.im, lo[1][c].re);
+      lo[1][c].im = fma2(gn, b.re, lo[1][c].im);
+    }
+  }
+}
+
+// Per-CTA data: for each of the X2_SITES 4d sites and each hop
+// d = 2 mu + (0 forward, 1 backward) the neighbour site, the boundary factor
+// and the link (U_mu(x) forward, U_mu(x - mu) backward) as an index into U.
+struct X2Stage {
+  int nb[X2_SITES][8];
+  float coef[X2_SITES][8];
+  int li[X2_SITES][8];
+};
+
+// One pass of H over the pair (x4, s0, s0+1) of every right-hand side; DOT adds
+// Re <in, H in> of the pair's output sites into *dot (products summed in FP32
+// within each spin half, where the terms share the sign of Gamma5, and the two
+// halves combined in FP64, where they cancel).
+template <int LS, bool DOT>
+__device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __restrict__ U, const X2Stage& sm,
+                                          int site, int x4, int p, float diag, float mf, const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
+                                          double* dot) {
+  const int ls = ls_of<LS>(g);
+  const int s0 = 2 * p;
+  const unsigned base = (unsigned)(x4 * 12 * ls);
+  const cpx<float>* self = in + base + s0;
+  cx2 up[2][3], lo[2][3];
+  {
+    // diagonal and fifth-dimension terms, lane by lane:
+    //   upper(s) = diag psi(s) - w psi(s-1),  lower(s) = diag psi(s) - w psi(s+1)
+    const bool wl = s0 == 0, wr = s0 + 2 == ls;
+    const cpx<float>* prv = in + base + (wl ? ls - 1 : s0 - 1);
+    const cpx<float>* nxt = in + base + (wr ? 0 : s0 + 2);
+    const float w0 = wl ? -mf : 1.f, w1 = wr ? -mf : 1.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float4 q = ld4(self + c * ls);
+      const cpx<float> v = ld(prv + c * ls);
+      const int sp = c / 3, cc = c % 3;
+      up[sp][cc].re = make_float2(fmaf(-w0, v.re, diag * q.x), fmaf(-1.f, q.x, diag * q.z));
+      up[sp][cc].im = make_float2(fmaf(-w0, v.im, diag * q.y), fmaf(-1.f, q.y, diag * q.w));
+    }
+#pragma unroll
+    for (int c = 6; c < 12; ++c) {
+      const float4 q = ld4(self + c * ls);
+      const cpx<float> v = ld(nxt + c * ls);
+      const int sp = c / 3 - 2, cc = c % 3;
+      // negated lower: psi(s+1) - diag psi(s)
+      lo[sp][cc].re = make_float2(fmaf(-diag, q.x, q.z), fmaf(-diag, q.z, w1 * v.re));
+      lo[sp][cc].im = make_float2(fmaf(-diag, q.y, q.w), fmaf(-diag, q.w, w1 * v.im));
+    }
+  }
+  const int* nbs = sm.nb[site];
+  const float* cfs = sm.coef[site];
+  hop_x2<0, +1>(U + (unsigned)(sm.li[site][0] * 9), in + (unsigned)(nbs[0] * 12 * ls + s0), ls, cfs[0], up, lo);
+  hop_x2<0, -1>(U + (unsigned)(sm.li[site][1] * 9), in + (unsigned)(nbs[1] * 12 * ls + s0), ls, cfs[1], up, lo);
+  hop_x2<1, +1>(U + (unsigned)(sm.li[site][2] * 9), in + (unsigned)(nbs[2] * 12 * ls + s0), ls, cfs[2], up, lo);
+  hop_x2<1, -1>(U + (unsigned)(sm.li[site][3] * 9), in + (unsigned)(nbs[3] * 12 * ls + s0), ls, cfs[3], up, lo);
+  hop_x2<2, +1>(U + (unsigned)(sm.li[site][4] * 9), in + (unsigned)(nbs[4] * 12 * ls + s0), ls, cfs[4], up, lo);
+  hop_x2<2, -1>(U + (unsigned)(sm.li[site][5] * 9), in + (unsigned)(nbs[5] * 12 * ls + s0), ls, cfs[5], up, lo);
+  hop_x2<3, +1>(U + (unsigned)(sm.li[site][6] * 9), in + (unsigned)(nbs[6] * 12 * ls + s0), ls, cfs[6], up, lo);
+  hop_x2<3, -1>(U + (unsigned)(sm.li[site][7] * 9), in + (unsigned)(nbs[7] * 12 * ls + s0), ls, cfs[7], up, lo);
+  // out(Ls-1-s) = gamma5 acc(s): the pair lands at Ls-2-s0 with its lanes swapped
+  const unsigned ob = base + (unsigned)(ls - 2 - s0);
+  float d[2] = {0.f, 0.f};  // upper and lower spins summed apart: no cancellation within either
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const cx2 v = c < 6 ? up[c / 3][c % 3] : lo[c / 3 - 2][c % 3];
+    const float4 o = make_float4(v.re.y, v.im.y, v.re.x, v.im.x);
+    *reinterpret_cast<float4*>(out + ob + c * ls) = o;
+    if (DOT) {
+      const float4 a = ld4(in + ob + c * ls);
+      float& e = d[c < 6 ? 0 : 1];
+      e = fmaf(a.x, o.x, e);
+      e = fmaf(a.y, o.y, e);
+      e = fmaf(a.z, o.z, e);
+      e = fmaf(a.w, o.w, e);
+    }
+  }
+  if (DOT) *dot += (double)d[0] + (double)d[1];
+}
+
+// Neighbours, boundary factors and link indices of the 4d sites [x0, x0 + X2_SITES).
+__device__ __forceinline__ void stage_sites(const Geom& g, int x0, X2Stage& sm) {
+  for (int t = threadIdx.x; t < X2_SITES * 8; t += blockDim.x) {
+    const int site = t >> 3, d = t & 7, mu = d >> 1;
+    const int x4 = x0 + site;
+    int nb = 0, li = 0;
+    float cf = 0.f;
+    if (x4 < g.V4) {
+      // coordinate mu of x4 and the index stride of direction mu (no dynamic indexing)
+      const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+      const int lm = mu == 0 ? L0 : mu == 1 ? L1 : mu == 2 ? L2 : L3;
+      const int stride = mu == 0 ? 1 : mu == 1 ? L0 : mu == 2 ? L0 * L1 : L0 * L1 * L2;
+      const int cm = (x4 / stride) % lm;
+      int ph = 1;
+      if (d & 1) {
+        nb = cm == 0 ? x4 + (lm - 1) * stride : x4 - stride;
+        if (cm == 0 && mu == 3) ph = g.bc_t;
+      } else {
+        nb = cm == lm - 1 ? x4 - (lm - 1) * stride : x4 + stride;
+        if (cm == lm - 1 && mu == 3) ph = g.bc_t;
+      }
+      li = mu * g.V4 + ((d & 1) ? nb : x4);
+      cf = -0.5f * (float)ph;
+    }
+    sm.nb[site][d] = nb;
+    sm.coef[site][d] = cf;
+    sm.li[site][d] = li;
+  }
+  __syncthreads();
+}
+
+// blockDim = X2_SITES * Ls/2: thread (site, p) = (tid / (Ls/2), tid % (Ls/2)).
+// A CTA loops over groups of X2_SITES 4d sites (grid-stride) and, within a
+// group, over the right-hand sides.
+template <int LS, bool DOT>
+__global__ void __launch_bounds__(128, 4) g5dwf_x2_kernel(Geom g, float diag, float mf,
+                                                          const cpx<float>* __restrict__ U,
+                                                          const cpx<float>* __restrict__ in,
+                                                          cpx<float>* __restrict__ out, int nrhs, RedScratch rs,
+                                                          double* result) {
+  __shared__ X2Stage sm;
+  const int ls = ls_of<LS>(g);
+  const int lp = ls >> 1;
+  const int site = threadIdx.x / lp, p = threadIdx.x - site * lp;
+  const int groups = (g.V4 + X2_SITES - 1) / X2_SITES;
+  const long long fsize = g.V5 * 12;
+  double dot = 0.0;
+  for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    const int x0 = grp * X2_SITES;
+    stage_sites(g, x0, sm);
+    const int x4 = x0 + site;
+    if (x4 < g.V4) {
+      for (int r = 0; r < nrhs; ++r)
+        site_pair<LS, DOT>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot);
+    }
+    __syncthreads();  // the per-site data is refilled for the next group
+  }
+  if (DOT) {
+    double v[1] = {dot};
+    double tot[1];
+    if (grid_reduce<1>(v, rs, tot)) *result = tot[0];
+  }
+}
+
+// Whether the packed kernel applies: even Ls up to 16, 16-byte aligned fields.
+bool g5dwf_x2_ok(const Geom& g, const void* in, const void* out) {
+  return (g.Ls % 2 == 0) && g.Ls <= 2 * X2_MAX_LP && ((((uintptr_t)in) | ((uintptr_t)out)) & 15) == 0;
+}
+
+int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in, cpx<float>* out,
+                    int nrhs, RedScratch* rs, double* result, cudaStream_t st) {
+  const int threads = X2_SITES * (g.Ls / 2);
+  const int groups = (g.V4 + X2_SITES - 1) / X2_SITES;
+  const float diag = (float)(5.0 - M5), fmf = (float)mf;
+  if (rs) {
+    const int blocks = groups < RED_MAX_BLOCKS ? groups : RED_MAX_BLOCKS;
+    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, true><<<blocks, threads, 0, st>>>(g, diag, fmf, U, in, out, nrhs,
+                                                                                    *rs, result)));
+  } else {
+    RedScratch none{nullptr, nullptr};
+    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, false><<<groups, threads, 0, st>>>(g, diag, fmf, U, in, out, nrhs,
+                                                                                     none, nullptr)));
+  }
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+}  // namespace hdcr

@@ -24,7 +24,17 @@ def stencil(n: int, dtype: str, reps: int = 4) -> None:
     for _ in range(reps):
         hd.apply_g5dwf(lat, U, x, 1.8, 0.01, out=y)
     torch.cuda.synchronize()
-    print("ok")
+    # event-timed launches (the inputs exceed L2 at n = 16, so every launch reads from HBM)
+    hd.stencil_timer(True)
+    for _ in range(reps):
+        hd.apply_g5dwf(lat, U, x, 1.8, 0.01, out=y)
+    torch.cuda.synchronize()
+    t = hd.stencil_timer_read(dt)
+    hd.stencil_timer(False)
+    us = t["ms"] / max(t["launches"], 1) * 1e3
+    real = 4 if dtype == "f32" else 8
+    per_site = 2 * 24 * real + 4 * 18 * real / 16   # psi in + out, links shared by the 16 s-sites
+    print(f"ok {dtype} L={n} Ls=16: {us:.2f} us per launch, {lat.V4 * 16 * per_site / (us * 1e-6) / 1e9:.1f} GB/s")
 
 
 def main(argv=None) -> int:

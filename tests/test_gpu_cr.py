@@ -95,3 +95,36 @@ def test_cr_reports_nonfinite_source(hd):
     with pytest.raises(hd.HDCRError) as e:
         hd.cr_solve(hd.Lattice(L, Ls), dev(links(U)), dev(b), 1.8, 0.01, tol=1e-10, max_iter=100)
     assert e.value.status == -4
+
+
+def test_cr_fp32_on_many_site_groups(hd):
+    """FP32 CR (the fused stencil + <r, H r> kernel, which loops over 4d-site groups
+    when they outnumber its reduction grid) on a 16^3 x 12 lattice (1536 groups of
+    32 sites).  The first iterate x1 = alpha b with alpha = <b, Hb> / |Hb|^2 is
+    checked against the FP64 oracle within FP32 rounding amplified by the
+    cancellation in <b, Hb> (H is indefinite), and a converged FP32 solve must
+    report the true residual the oracle measures (which stalls above the
+    recursive residual, the FP32 residual gap)."""
+    L, Ls = (16, 16, 16, 12), 4
+    U = synth.gauge_field(L, 0.5, 1001)
+    b = synth.gaussian_fermion(L, Ls, 2004)
+    U32 = links(U).astype(np.complex64)
+    b32 = planes(b).astype(np.complex64)
+    Ur = U32.astype(np.complex128).reshape(U.shape)
+    br = natural(b32.astype(np.complex128), L, Ls)
+    lat = hd.Lattice(L, Ls)
+    Hb = dwf.apply_H(Ur, br, 1.8, 0.01)
+    amp = np.sqrt(dwf.norm2(br) * dwf.norm2(Hb)) / abs(np.vdot(br, Hb).real)
+    xd = torch.zeros_like(dev(b32))
+    with pytest.raises(hd.HDCRError) as e:
+        hd.cr_solve_into(lat, dev(U32), dev(b32), xd, 1.8, 0.01, tol=1e-14, max_iter=1)
+    assert e.value.status == -3
+    x1 = natural(host(xd).astype(np.complex128), L, Ls)
+    alpha = np.vdot(br, Hb).real / dwf.norm2(Hb)
+    assert relerr(x1, alpha * br) < 20 * 6e-8 * amp
+    x, st = hd.cr_solve(lat, dev(U32), dev(b32), 1.8, 0.01, tol=1e-5, max_iter=20000)
+    assert st["status"] == 0
+    xg = natural(host(x).astype(np.complex128), L, Ls)
+    true = np.sqrt(dwf.norm2(br - dwf.apply_H(Ur, xg, 1.8, 0.01)) / dwf.norm2(br))
+    assert true < 1e-2          # FP32 recursion: the true residual stalls above the recursive one
+    assert abs(st["true_resid"] - true) <= 0.05 * true

@@ -18,6 +18,8 @@ CASES = [
     ((3, 5, 2, 6), 5, -1, 0.5),
     ((8, 6, 4, 8), 8, -1, 0.5),
     ((6, 4, 4, 10), 16, 1, 0.5),
+    ((3, 5, 2, 6), 6, -1, 0.5),   # even Ls on a volume that leaves the last 32-site group ragged
+    ((4, 2, 2, 4), 2, 1, 0.5),    # Ls = 2: both domain walls inside one fifth-dimension pair
 ]
 
 
@@ -132,3 +134,30 @@ def test_reductions_fp64_deterministic(hd):
     assert abs(hd.norm2(ud) - np.vdot(u, u).real) / np.vdot(u, u).real < 1e-14
     u32 = dev(u.astype(np.complex64))
     assert abs(hd.norm2(u32) - np.vdot(u.astype(np.complex64), u.astype(np.complex64)).real) < 1e-6 * n
+
+
+def test_apply_fp32_unaligned_fields_take_the_scalar_kernel(hd):
+    """The packed two-site FP32 kernel needs 16-byte aligned fields; fields that are
+    only 8-byte aligned go to the one-site kernel, and both agree with the oracle."""
+    L, Ls, bc = (4, 4, 2, 6), 8, -1
+    U, psi = _inputs(L, Ls, 0.5, 1700)
+    lat = hd.Lattice(L, Ls, bc)
+    U32 = dev(links(U).astype(np.complex64))
+    p32 = planes(psi).astype(np.complex64)
+    n = p32.size
+    buf_in = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+    buf_out = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+    x_off = buf_in[1:]                       # 8 bytes past a 256-byte boundary
+    x_off.copy_(dev(p32).reshape(-1))
+    y_off = buf_out[1:]
+    hd.apply_g5dwf(lat, U32, x_off, 1.8, 0.01, out=y_off)
+    y_al = hd.apply_g5dwf(lat, U32, dev(p32), 1.8, 0.01)
+    assert x_off.data_ptr() % 16 == 8 and y_al.data_ptr() % 16 == 0
+    pr = natural(p32.astype(np.complex128), L, Ls)
+    want = dwf.apply_H(links(U).astype(np.complex64).astype(np.complex128).reshape(U.shape), pr, 1.8, 0.01,
+                       bc_t=bc)
+    got_off = natural(host(y_off).astype(np.complex128).reshape(p32.shape), L, Ls)
+    got_al = natural(host(y_al).astype(np.complex128), L, Ls)
+    assert relerr(got_off, want) <= 1e-6
+    assert relerr(got_al, want) <= 1e-6
+    assert relerr(got_al, got_off) <= 1e-6
