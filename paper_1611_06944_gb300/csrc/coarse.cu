@@ -1,14 +1,23 @@
 // Little Dirac operator A^{ab}_{jk} = <phi_j^a | H | phi_k^b> (Eq. 4.5), its
 // 9-point application, and the restriction / prolongation P^dag, P (Eq. 4.3).
 //
-// Build: for every leg d the stencil is applied to all nvec basis vectors with
-// only the hops that belong to that leg (leg 0: the local terms and the hops
-// that stay inside the block; leg (mu, +-): the single hop that leaves the
-// block towards a +- mu, evaluated on the block face only), then each block
-// projects: A[a][d][j][k] = sum_{x in block a} phi_j(x)^dag Y_k^{(d)}(x).
-// Blocks span the whole fifth dimension, so the s-hops and Gamma5's R5 stay
-// inside a block.  On a coarse extent of 2 the legs +mu and -mu reach the same
-// coarse site and are both kept.
+// Build.  H splits into the part that stays inside a block (leg 0: the local
+// terms and the hops between sites of one block) and the hops that leave a
+// block towards a +- mu.  Blocks span the whole fifth dimension, so the s-hops
+// and Gamma5's R5 stay inside a block.
+//   leg 0:   Y_k = H_0 phi_k on every site, A[a][0][j][k] = sum_{x in a} phi_j^dag Y_k
+//            for j <= k (A^{aa} is Hermitian; the rest is mirrored).
+//   leg +mu: only the +mu face of block a takes part, and there the hop result
+//            is (hp; lo(hp)) after Gamma5 with hp = -1/2 U_mu(x) h (h the
+//            two-spinor projection of phi_k(x + mu)), lo = i sigma_mu (or 1 for
+//            t).  So A[a][+mu][j][k] = sum_face phit_j^dag hp_k with the
+//            six-component projected basis phit = phi_up + lo^dag phi_lo taken at
+//            the reflected s (R5): half the components of a full projection.
+//   leg -mu: H is Hermitian, so A[a][-mu] = (A[a - mu][+mu])^dag.
+// On a coarse extent of 2 the legs +mu and -mu reach the same coarse site and
+// are both kept.
+#include <algorithm>
+
 #include "coarse.cuh"
 #include "dwf_stencil.cuh"
 
@@ -58,46 +67,6 @@ __global__ void __launch_bounds__(256) leg_self_kernel(Geom g, BlockGeom bg, R d
   store_g5r5<R, 0>(g, Y + (long long)k * 12 * g.V5, x4, s, acc);
 }
 
-// face site f of leg (MU, SIGN): sites whose MU coordinate is the last (SIGN > 0)
-// or first (SIGN < 0) of its block; f runs over (Lc[MU] * other extents) * Ls
-template <int MU, int SIGN>
-__device__ __forceinline__ long long face_site(const Geom& g, const BlockGeom& bg, long long f, int co[4]) {
-  const int s = (int)(f % g.Ls);
-  long long r = f / g.Ls;
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    const int ext = nu == MU ? bg.Lc[nu] : g.L[nu];
-    int c = (int)(r % ext);
-    r /= ext;
-    if (nu == MU) c = c * bg.b[nu] + (SIGN > 0 ? bg.b[nu] - 1 : 0);
-    co[nu] = c;
-  }
-  return (long long)x4_index(g, co) * g.Ls + s;
-}
-
-template <typename R, int MU, int SIGN>
-__global__ void __launch_bounds__(256) leg_face_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ U,
-                                                       const cpx<R>* __restrict__ vecs,
-                                                       cpx<R>* __restrict__ Y, int nvec) {
-  const long long nf = g.V5 / bg.b[MU];
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nf * nvec) return;
-  const int k = (int)(idx / nf);
-  const long long f = idx - (long long)k * nf;
-  int co[4];
-  const long long i5 = face_site<MU, SIGN>(g, bg, f, co);
-  const int x4 = (int)(i5 / g.Ls);
-  const int s = (int)(i5 - (long long)x4 * g.Ls);
-  const cpx<R>* in = vecs + (long long)k * 12 * g.V5;
-  cpx<R> acc[4][3];
-#pragma unroll
-  for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc[sp][c] = cpx<R>((R)0, (R)0);
-  hop_full<R, 0, MU, SIGN>(g, U, in, x4, s, co, acc);
-  store_g5r5<R, 0>(g, Y + (long long)k * 12 * g.V5, x4, s, acc);
-}
-
 // ------------------------------------------------------------ projection
 // local site index l (0 <= l < nsites) of the leg's site set in block a -> fine 5d index
 __device__ __forceinline__ long long leg_local_site(const Geom& g, const BlockGeom& bg, int a, int leg,
@@ -129,7 +98,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(Geom g, BlockGeom
                                                                const cpx<R>* __restrict__ phi,
                                                                const cpx<R>* __restrict__ Y,
                                                                cpx<R>* __restrict__ A, int nvec, int leg,
-                                                               int T) {
+                                                               int T, bool upper) {
   extern __shared__ unsigned char smem_raw[];
   cpx<R>* sphi = reinterpret_cast<cpx<R>*>(smem_raw);   // [nvec][12][T]
   cpx<R>* sy = sphi + (size_t)nvec * 12 * T;            // [nvec][12][T]
@@ -161,7 +130,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(Geom g, BlockGeom
 #pragma unroll
     for (int i = 0; i < PROJ_MAXP; ++i) {
       const int pr = threadIdx.x + i * PROJ_THREADS;
-      if (pr < npairs) {
+      if (pr < npairs && !(upper && pr / nvec > pr % nvec)) {
         const int j = pr / nvec, k = pr % nvec;
         const cpx<R>* pj = sphi + (size_t)j * 12 * T;
         const cpx<R>* yk = sy + (size_t)k * 12 * T;
@@ -176,11 +145,208 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(Geom g, BlockGeom
 #pragma unroll
   for (int i = 0; i < PROJ_MAXP; ++i) {
     const int pr = threadIdx.x + i * PROJ_THREADS;
+    if (pr < npairs && !(upper && pr / nvec > pr % nvec)) {
+      const int j = pr / nvec, k = pr % nvec;
+      A[(((long long)a * NLEGS + leg) * nvec + j) * nvec + k] = cpx<R>((R)acc[i][0], (R)acc[i][1]);
+    }
+  }
+}
+
+// ------------------------------------------------------------ forward legs
+// Face site l of the +MU face of block a: the local sites of the block with
+// the MU coordinate fixed to the block's last, l = ((x4 local) * Ls + s).
+template <int MU>
+__device__ __forceinline__ long long face_site(const Geom& g, const BlockGeom& bg, int a, long long l) {
+  return leg_local_site(g, bg, a, leg_of(MU, +1), l);
+}
+
+// phit_j = phi_up + lo^dag phi_lo at (x, Ls-1-s) for every face site (x, s) of
+// block a:  lo^dag = -i sigma_MU (MU < 3) or 1 (MU = 3).  Layout [j][a][l][6].
+template <typename R, int MU>
+__global__ void __launch_bounds__(256) face_basis_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ phi,
+                                                         cpx<R>* __restrict__ pt, int nvec, long long nf) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)bg.Vc * nf;
+  if (idx >= per * nvec) return;
+  const int j = (int)(idx / per);
+  const long long r = idx - (long long)j * per;
+  const int a = (int)(r / nf);
+  const long long l = r - (long long)a * nf;
+  const long long i5 = face_site<MU>(g, bg, a, l);
+  const int x4 = (int)(i5 / g.Ls);
+  const int s = (int)(i5 - (long long)x4 * g.Ls);
+  const cpx<R>* p = phi + (long long)j * 12 * g.V5 + (unsigned)(x4 * 12 * g.Ls + (g.Ls - 1 - s));
+  cpx<R> u0[3], u1[3], d0[3], d1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u0[c] = ld(p + (0 + c) * g.Ls);
+    u1[c] = ld(p + (3 + c) * g.Ls);
+    d0[c] = ld(p + (6 + c) * g.Ls);
+    d1[c] = ld(p + (9 + c) * g.Ls);
+  }
+  cpx<R> o0[3], o1[3];
+  if (MU == 3) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      o0[c] = u0[c] + d0[c];
+      o1[c] = u1[c] + d1[c];
+    }
+  } else {
+    cpx<R> t0[3], t1[3];
+    i_sigma<R, MU>(d0, d1, t0, t1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      o0[c] = u0[c] - t0[c];
+      o1[c] = u1[c] - t1[c];
+    }
+  }
+  cpx<R>* q = pt + idx * 6;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    st(q + c, o0[c]);
+    st(q + 3 + c, o1[c]);
+  }
+}
+
+// hp_k = -1/2 (phase) U_MU(x) h_k(x + MU) for every face site (x, s) of block a,
+// h the two-spinor of the (1 - gamma_MU) projection.  Layout [k][a][l][6].
+template <typename R, int MU>
+__global__ void __launch_bounds__(256) face_hop_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ U,
+                                                       const cpx<R>* __restrict__ phi, cpx<R>* __restrict__ hf,
+                                                       int nvec, long long nf) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)bg.Vc * nf;
+  if (idx >= per * nvec) return;
+  const int k = (int)(idx / per);
+  const long long r = idx - (long long)k * per;
+  const int a = (int)(r / nf);
+  const long long l = r - (long long)a * nf;
+  const long long i5 = face_site<MU>(g, bg, a, l);
+  const int x4 = (int)(i5 / g.Ls);
+  const int s = (int)(i5 - (long long)x4 * g.Ls);
+  int co[4];
+  x4_coords(g, x4, co);
+  int ph;
+  const int y4 = neighbour<MU, +1>(g, co, &ph);
+  const cpx<R>* nb = phi + (long long)k * 12 * g.V5 + (unsigned)(y4 * 12 * g.Ls + s);
+  const int ls = g.Ls;
+  cpx<R> h[2][3];
+  {
+    cpx<R> u0[3], u1[3], d0[3], d1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      u0[c] = ld(nb + (0 + c) * ls);
+      u1[c] = ld(nb + (3 + c) * ls);
+      d0[c] = ld(nb + (6 + c) * ls);
+      d1[c] = ld(nb + (9 + c) * ls);
+    }
+    if (MU == 3) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        h[0][c] = u0[c] - d0[c];
+        h[1][c] = u1[c] - d1[c];
+      }
+    } else {
+      cpx<R> t0[3], t1[3];
+      i_sigma<R, MU>(d0, d1, t0, t1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        h[0][c] = u0[c] + t0[c];
+        h[1][c] = u1[c] + t1[c];
+      }
+    }
+  }
+  const cpx<R>* Ul = U + (unsigned)((MU * g.V4 + x4) * 9);
+  const R coef = (R)(-0.5 * ph);
+  cpx<R>* q = hf + idx * 6;
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+      cpx<R> t((R)0, (R)0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) t = cmadd(t, ld(Ul + 3 * aa + b), h[sp][b]);
+      st(q + 3 * sp + aa, coef * t);
+    }
+}
+
+// A[a][leg][j][k] = sum_e conj(X[j][a][e]) Y[k][a][e], e < K (contiguous per vector and block)
+template <typename R>
+__global__ void __launch_bounds__(PROJ_THREADS) face_project_kernel(const cpx<R>* __restrict__ X,
+                                                                    const cpx<R>* __restrict__ Y, long long K,
+                                                                    cpx<R>* __restrict__ A, int Vc, int nvec,
+                                                                    int leg, int T) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [nvec][T]
+  cpx<R>* sy = sx + (size_t)nvec * T;                // [nvec][T]
+  const int a = blockIdx.x;
+  const int npairs = nvec * nvec;
+  double acc[PROJ_MAXP][2];
+#pragma unroll
+  for (int i = 0; i < PROJ_MAXP; ++i) acc[i][0] = acc[i][1] = 0.0;
+  for (long long e0 = 0; e0 < K; e0 += T) {
+    const int tn = (int)min((long long)T, K - e0);
+    for (int e = threadIdx.x; e < nvec * T; e += PROJ_THREADS) {
+      const int v = e / T, t = e - v * T;
+      cpx<R> p((R)0, (R)0), q((R)0, (R)0);
+      if (t < tn) {
+        const long long off = ((long long)v * Vc + a) * K + e0 + t;
+        p = ld(X + off);
+        q = ld(Y + off);
+      }
+      sx[e] = p;
+      sy[e] = q;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PROJ_MAXP; ++i) {
+      const int pr = threadIdx.x + i * PROJ_THREADS;
+      if (pr < npairs) {
+        const int j = pr / nvec, k = pr % nvec;
+        const cpx<R>* xj = sx + (size_t)j * T;
+        const cpx<R>* yk = sy + (size_t)k * T;
+        cpx<R> sum((R)0, (R)0);
+        for (int e = 0; e < T; ++e) sum = cjmadd(sum, xj[e], yk[e]);
+        acc[i][0] += (double)sum.re;
+        acc[i][1] += (double)sum.im;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < PROJ_MAXP; ++i) {
+    const int pr = threadIdx.x + i * PROJ_THREADS;
     if (pr < npairs) {
       const int j = pr / nvec, k = pr % nvec;
       A[(((long long)a * NLEGS + leg) * nvec + j) * nvec + k] = cpx<R>((R)acc[i][0], (R)acc[i][1]);
     }
   }
+}
+
+// The legs not computed directly: A[a][0][j][k] = conj(A[a][0][k][j]) for j > k, and
+// A[a][-mu][j][k] = conj(A[a - mu][+mu][k][j]).
+template <typename R>
+__global__ void complete_legs_kernel(cpx<R>* __restrict__ A, const int* __restrict__ nbr, int Vc, int nvec) {
+  const long long n2 = (long long)nvec * nvec;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Vc * 5 * n2) return;
+  const int a = (int)(idx / (5 * n2));
+  const long long r = idx - (long long)a * 5 * n2;
+  const int w = (int)(r / n2);  // 0: leg 0, 1..4: leg (mu = w-1, -)
+  const int j = (int)((r - (long long)w * n2) / nvec), k = (int)(r % nvec);
+  cpx<R> v;
+  int leg;
+  if (w == 0) {
+    if (j <= k) return;
+    leg = 0;
+    v = A[(((long long)a * NLEGS) * nvec + k) * nvec + j];
+  } else {
+    const int mu = w - 1;
+    leg = leg_of(mu, -1);
+    const int b = nbr[a * NLEGS + leg];
+    v = A[(((long long)b * NLEGS + leg_of(mu, +1)) * nvec + k) * nvec + j];
+  }
+  A[(((long long)a * NLEGS + leg) * nvec + j) * nvec + k] = cpx<R>(v.re, -v.im);
 }
 
 // ------------------------------------------------------------ coarse apply
@@ -329,43 +495,51 @@ int CoarseOp<R>::apply_dot(const cpx<R>* in, cpx<R>* out, RedScratch rs, double*
 HDCR_INST_COARSE(double)
 HDCR_INST_COARSE(float)
 
-template <typename R, int MU, int SIGN>
-static void launch_leg_face(const Geom& g, const BlockGeom& bg, const cpx<R>* U, const cpx<R>* vecs, cpx<R>* Y,
-                            int nvec, cudaStream_t st) {
-  const long long n = g.V5 / bg.b[MU] * nvec;
-  leg_face_kernel<R, MU, SIGN><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, vecs, Y, nvec); count_launch();
+template <typename R, int MU>
+static int launch_forward_leg(const Geom& g, const BlockGeom& bg, const cpx<R>* U, const cpx<R>* phi, cpx<R>* pt,
+                              cpx<R>* hf, cpx<R>* A, const int* nbr, int nvec, cudaStream_t st) {
+  (void)nbr;
+  const long long nf = bg.K5 / bg.b[MU];
+  const long long n = (long long)bg.Vc * nf * nvec;
+  face_basis_kernel<R, MU><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, phi, pt, nvec, nf); count_launch();
+  face_hop_kernel<R, MU><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, phi, hf, nvec, nf); count_launch();
+  int T = (int)(48 * 1024 / (2 * (size_t)nvec * sizeof(cpx<R>)));
+  if (T > 256) T = 256;
+  const size_t smem = 2 * (size_t)nvec * T * sizeof(cpx<R>);
+  face_project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(pt, hf, nf * 6, A, bg.Vc, nvec, leg_of(MU, +1), T); count_launch();
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
 }
 
 template <typename R>
 static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>* U, const cpx<R>* phi,
-                    cpx<R>* Y, cpx<R>* A, cudaStream_t st) {
+                    cpx<R>* Y, cpx<R>* face_work, cpx<R>* A, const int* nbr, cudaStream_t st) {
   const Geom& g = sub->g;
   const BlockGeom& bg = sub->bg;
   const int nvec = sub->nvec;
+  // leg 0: in-block part of H on every site, upper triangle of the projection
   int T = (int)(48 * 1024 / (2 * (size_t)nvec * 12 * sizeof(cpx<R>)));
   if (T < 1) T = 1;
   if (T > 16) T = 16;
   const size_t smem = 2 * (size_t)nvec * 12 * T * sizeof(cpx<R>);
-  for (int leg = 0; leg < NLEGS; ++leg) {
-    if (leg == 0) {
-      const long long n = g.V5 * nvec;
-      leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec); count_launch();
-    } else {
-      switch (leg) {
-        case 1: launch_leg_face<R, 0, +1>(g, bg, U, phi, Y, nvec, st); break;
-        case 2: launch_leg_face<R, 0, -1>(g, bg, U, phi, Y, nvec, st); break;
-        case 3: launch_leg_face<R, 1, +1>(g, bg, U, phi, Y, nvec, st); break;
-        case 4: launch_leg_face<R, 1, -1>(g, bg, U, phi, Y, nvec, st); break;
-        case 5: launch_leg_face<R, 2, +1>(g, bg, U, phi, Y, nvec, st); break;
-        case 6: launch_leg_face<R, 2, -1>(g, bg, U, phi, Y, nvec, st); break;
-        case 7: launch_leg_face<R, 3, +1>(g, bg, U, phi, Y, nvec, st); break;
-        default: launch_leg_face<R, 3, -1>(g, bg, U, phi, Y, nvec, st); break;
-      }
-    }
-    HDCR_LAUNCH_CHECK();
-    project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, leg, T); count_launch();
-    HDCR_LAUNCH_CHECK();
-  }
+  const long long n = g.V5 * nvec;
+  leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec); count_launch();
+  HDCR_LAUNCH_CHECK();
+  project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, 0, T, true); count_launch();
+  HDCR_LAUNCH_CHECK();
+  // forward legs on the block faces (six-component projections)
+  long long nfmax = 0;
+  for (int mu = 0; mu < 4; ++mu) nfmax = std::max(nfmax, bg.K5 / bg.b[mu]);
+  cpx<R>* pt = face_work;
+  cpx<R>* hf = face_work + (size_t)nvec * bg.Vc * nfmax * 6;
+  HDCR_TRY((launch_forward_leg<R, 0>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
+  HDCR_TRY((launch_forward_leg<R, 1>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
+  HDCR_TRY((launch_forward_leg<R, 2>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
+  HDCR_TRY((launch_forward_leg<R, 3>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
+  // lower triangle of leg 0 and the backward legs from Hermiticity
+  const long long nc = (long long)bg.Vc * 5 * nvec * nvec;
+  complete_legs_kernel<R><<<num_blocks(nc, 256), 256, 0, st>>>(A, nbr, bg.Vc, nvec); count_launch();
+  HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
 
@@ -398,7 +572,10 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
   // workspace: Y (nvec fields), and basis / links converted to the build precision when needed
   const bool conv_phi = sub->dtype != op_dtype;
   const bool conv_u = op_dtype != HDCR_C128;
-  size_t bytes = cb * (size_t)fs * nvec;
+  long long nfmax = 0;
+  for (int mu = 0; mu < 4; ++mu) nfmax = std::max(nfmax, bg.K5 / bg.b[mu]);
+  const size_t face_bytes = cb * (size_t)2 * nvec * bg.Vc * nfmax * 6;
+  size_t bytes = cb * (size_t)fs * nvec + face_bytes;
   if (conv_phi) bytes += cb * (size_t)fs * nvec;
   if (conv_u) bytes += cb * (size_t)g.V4 * 36;
   void* work = nullptr;
@@ -406,6 +583,8 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
   char* wp = (char*)work;
   void* Y = wp;
   wp += cb * (size_t)fs * nvec;
+  void* face_work = wp;
+  wp += face_bytes;
   const void* phi = sub->vecs;
   if (conv_phi) {
     phi = wp;
@@ -451,10 +630,10 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
   if (s == HDCR_OK) {
     if (op_dtype == HDCR_C128)
       s = build_op<double>(sub, p->M5, p->mf, (const cpx<double>*)Ub, (const cpx<double>*)phi, (cpx<double>*)Y,
-                           (cpx<double>*)co->A, st);
+                           (cpx<double>*)face_work, (cpx<double>*)co->A, co->nbr, st);
     else
       s = build_op<float>(sub, p->M5, p->mf, (const cpx<float>*)Ub, (const cpx<float>*)phi, (cpx<float>*)Y,
-                          (cpx<float>*)co->A, st);
+                          (cpx<float>*)face_work, (cpx<float>*)co->A, co->nbr, st);
   }
   if (s == HDCR_OK) {
     e = cudaStreamSynchronize(st);
