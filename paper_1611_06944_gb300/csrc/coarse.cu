@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "coarse.cuh"
+#include "coarse_tc.cuh"
 #include "dwf_stencil.cuh"
 
 namespace hdcr {
@@ -160,76 +161,65 @@ __device__ __forceinline__ long long face_site(const Geom& g, const BlockGeom& b
   return leg_local_site(g, bg, a, leg_of(MU, +1), l);
 }
 
-// phit_j = phi_up + lo^dag phi_lo at (x, Ls-1-s) for every face site (x, s) of
-// block a:  lo^dag = -i sigma_MU (MU < 3) or 1 (MU = 3).  Layout [j][a][l][6].
+// For vector v and face site (x, s) of the +MU face of block a, both operands of
+// the leg's projection (layout [v][a][l][6]):
+//   pt = phi_up + lo^dag phi_lo at (x, Ls-1-s),  lo^dag = -i sigma_MU (MU < 3) or 1,
+//   hf = -1/2 (phase) U_MU(x) h(x + MU, s), h the two-spinor of the (1 - gamma_MU)
+//        projection of phi_v.
 template <typename R, int MU>
-__global__ void __launch_bounds__(256) face_basis_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ phi,
-                                                         cpx<R>* __restrict__ pt, int nvec, long long nf) {
+__global__ void __launch_bounds__(256) face_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ U,
+                                                   const cpx<R>* __restrict__ phi, cpx<R>* __restrict__ pt,
+                                                   cpx<R>* __restrict__ hf, int nvec, long long nf) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long per = (long long)bg.Vc * nf;
   if (idx >= per * nvec) return;
-  const int j = (int)(idx / per);
-  const long long r = idx - (long long)j * per;
+  const int v = (int)(idx / per);
+  const long long r = idx - (long long)v * per;
   const int a = (int)(r / nf);
   const long long l = r - (long long)a * nf;
   const long long i5 = face_site<MU>(g, bg, a, l);
   const int x4 = (int)(i5 / g.Ls);
   const int s = (int)(i5 - (long long)x4 * g.Ls);
-  const cpx<R>* p = phi + (long long)j * 12 * g.V5 + (unsigned)(x4 * 12 * g.Ls + (g.Ls - 1 - s));
-  cpx<R> u0[3], u1[3], d0[3], d1[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    u0[c] = ld(p + (0 + c) * g.Ls);
-    u1[c] = ld(p + (3 + c) * g.Ls);
-    d0[c] = ld(p + (6 + c) * g.Ls);
-    d1[c] = ld(p + (9 + c) * g.Ls);
-  }
-  cpx<R> o0[3], o1[3];
-  if (MU == 3) {
+  const int ls = g.Ls;
+  const cpx<R>* field = phi + (long long)v * 12 * g.V5;
+  {
+    const cpx<R>* p = field + (unsigned)(x4 * 12 * ls + (ls - 1 - s));
+    cpx<R> u0[3], u1[3], d0[3], d1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      o0[c] = u0[c] + d0[c];
-      o1[c] = u1[c] + d1[c];
+      u0[c] = ld(p + (0 + c) * ls);
+      u1[c] = ld(p + (3 + c) * ls);
+      d0[c] = ld(p + (6 + c) * ls);
+      d1[c] = ld(p + (9 + c) * ls);
     }
-  } else {
-    cpx<R> t0[3], t1[3];
-    i_sigma<R, MU>(d0, d1, t0, t1);
+    cpx<R> o0[3], o1[3];
+    if (MU == 3) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o0[c] = u0[c] + d0[c];
+        o1[c] = u1[c] + d1[c];
+      }
+    } else {
+      cpx<R> t0[3], t1[3];
+      i_sigma<R, MU>(d0, d1, t0, t1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o0[c] = u0[c] - t0[c];
+        o1[c] = u1[c] - t1[c];
+      }
+    }
+    cpx<R>* q = pt + idx * 6;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      o0[c] = u0[c] - t0[c];
-      o1[c] = u1[c] - t1[c];
+      st(q + c, o0[c]);
+      st(q + 3 + c, o1[c]);
     }
   }
-  cpx<R>* q = pt + idx * 6;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    st(q + c, o0[c]);
-    st(q + 3 + c, o1[c]);
-  }
-}
-
-// hp_k = -1/2 (phase) U_MU(x) h_k(x + MU) for every face site (x, s) of block a,
-// h the two-spinor of the (1 - gamma_MU) projection.  Layout [k][a][l][6].
-template <typename R, int MU>
-__global__ void __launch_bounds__(256) face_hop_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ U,
-                                                       const cpx<R>* __restrict__ phi, cpx<R>* __restrict__ hf,
-                                                       int nvec, long long nf) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long per = (long long)bg.Vc * nf;
-  if (idx >= per * nvec) return;
-  const int k = (int)(idx / per);
-  const long long r = idx - (long long)k * per;
-  const int a = (int)(r / nf);
-  const long long l = r - (long long)a * nf;
-  const long long i5 = face_site<MU>(g, bg, a, l);
-  const int x4 = (int)(i5 / g.Ls);
-  const int s = (int)(i5 - (long long)x4 * g.Ls);
   int co[4];
   x4_coords(g, x4, co);
   int ph;
   const int y4 = neighbour<MU, +1>(g, co, &ph);
-  const cpx<R>* nb = phi + (long long)k * 12 * g.V5 + (unsigned)(y4 * 12 * g.Ls + s);
-  const int ls = g.Ls;
+  const cpx<R>* nb = field + (unsigned)(y4 * 12 * ls + s);
   cpx<R> h[2][3];
   {
     cpx<R> u0[3], u1[3], d0[3], d1[3];
@@ -497,23 +487,27 @@ HDCR_INST_COARSE(float)
 
 template <typename R, int MU>
 static int launch_forward_leg(const Geom& g, const BlockGeom& bg, const cpx<R>* U, const cpx<R>* phi, cpx<R>* pt,
-                              cpx<R>* hf, cpx<R>* A, const int* nbr, int nvec, cudaStream_t st) {
-  (void)nbr;
+                              cpx<R>* hf, cpx<R>* A, int nvec, cpx<R>* part, int* err, cudaStream_t st) {
   const long long nf = bg.K5 / bg.b[MU];
   const long long n = (long long)bg.Vc * nf * nvec;
-  face_basis_kernel<R, MU><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, phi, pt, nvec, nf); count_launch();
-  face_hop_kernel<R, MU><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, phi, hf, nvec, nf); count_launch();
-  int T = (int)(48 * 1024 / (2 * (size_t)nvec * sizeof(cpx<R>)));
-  if (T > 256) T = 256;
-  const size_t smem = 2 * (size_t)nvec * T * sizeof(cpx<R>);
-  face_project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(pt, hf, nf * 6, A, bg.Vc, nvec, leg_of(MU, +1), T); count_launch();
-  HDCR_LAUNCH_CHECK();
-  return HDCR_OK;
+  face_kernel<R, MU><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, phi, pt, hf, nvec, nf); count_launch();
+  if constexpr (sizeof(R) == 4) {
+    const TcSrc src{pt, hf, nf * 6, 0, g, bg};
+    return launch_tc_project(src, A, nvec, leg_of(MU, +1), part, err, st);
+  } else {
+    int T = (int)(48 * 1024 / (2 * (size_t)nvec * sizeof(cpx<R>)));
+    if (T > 256) T = 256;
+    const size_t smem = 2 * (size_t)nvec * T * sizeof(cpx<R>);
+    face_project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(pt, hf, nf * 6, A, bg.Vc, nvec, leg_of(MU, +1), T); count_launch();
+    HDCR_LAUNCH_CHECK();
+    return HDCR_OK;
+  }
 }
 
 template <typename R>
 static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>* U, const cpx<R>* phi,
-                    cpx<R>* Y, cpx<R>* face_work, cpx<R>* A, const int* nbr, cudaStream_t st) {
+                    cpx<R>* Y, cpx<R>* face_work, cpx<R>* A, const int* nbr, cpx<R>* part, int* err,
+                    cudaStream_t st) {
   const Geom& g = sub->g;
   const BlockGeom& bg = sub->bg;
   const int nvec = sub->nvec;
@@ -525,17 +519,22 @@ static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>
   const long long n = g.V5 * nvec;
   leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec); count_launch();
   HDCR_LAUNCH_CHECK();
-  project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, 0, T, true); count_launch();
-  HDCR_LAUNCH_CHECK();
+  if constexpr (sizeof(R) == 4) {
+    const TcSrc src{phi, Y, bg.K5 * 12, 1, g, bg};
+    HDCR_TRY(launch_tc_project(src, A, nvec, 0, part, err, st));
+  } else {
+    project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, 0, T, true); count_launch();
+    HDCR_LAUNCH_CHECK();
+  }
   // forward legs on the block faces (six-component projections)
   long long nfmax = 0;
   for (int mu = 0; mu < 4; ++mu) nfmax = std::max(nfmax, bg.K5 / bg.b[mu]);
   cpx<R>* pt = face_work;
   cpx<R>* hf = face_work + (size_t)nvec * bg.Vc * nfmax * 6;
-  HDCR_TRY((launch_forward_leg<R, 0>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
-  HDCR_TRY((launch_forward_leg<R, 1>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
-  HDCR_TRY((launch_forward_leg<R, 2>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
-  HDCR_TRY((launch_forward_leg<R, 3>(g, bg, U, phi, pt, hf, A, nbr, nvec, st)));
+  HDCR_TRY((launch_forward_leg<R, 0>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
+  HDCR_TRY((launch_forward_leg<R, 1>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
+  HDCR_TRY((launch_forward_leg<R, 2>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
+  HDCR_TRY((launch_forward_leg<R, 3>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
   // lower triangle of leg 0 and the backward legs from Hermiticity
   const long long nc = (long long)bg.Vc * 5 * nvec * nvec;
   complete_legs_kernel<R><<<num_blocks(nc, 256), 256, 0, st>>>(A, nbr, bg.Vc, nvec); count_launch();
@@ -575,16 +574,29 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
   long long nfmax = 0;
   for (int mu = 0; mu < 4; ++mu) nfmax = std::max(nfmax, bg.K5 / bg.b[mu]);
   const size_t face_bytes = cb * (size_t)2 * nvec * bg.Vc * nfmax * 6;
-  size_t bytes = cb * (size_t)fs * nvec + face_bytes;
+  // partial projections of the split tensor-core contractions (FP32 builds)
+  const size_t part_bytes = op_dtype == HDCR_C64 ? sizeof(cpx<float>) * TC_MAX_SPLIT * (size_t)bg.Vc * nvec * nvec : 0;
+  size_t bytes = cb * (size_t)fs * nvec + face_bytes + 256 + part_bytes;
   if (conv_phi) bytes += cb * (size_t)fs * nvec;
   if (conv_u) bytes += cb * (size_t)g.V4 * 36;
-  void* work = nullptr;
-  HDCR_CUDA_TRY(cudaMalloc(&work, bytes));
-  char* wp = (char*)work;
+  std::lock_guard<std::mutex> lock(sub->build_mu);
+  if (sub->build_ws_bytes < bytes) {
+    if (sub->build_ws) cudaFree(sub->build_ws);
+    sub->build_ws = nullptr;
+    sub->build_ws_bytes = 0;
+    HDCR_CUDA_TRY(cudaMalloc(&sub->build_ws, bytes));
+    sub->build_ws_bytes = bytes;
+  }
+  char* wp = (char*)sub->build_ws;
   void* Y = wp;
   wp += cb * (size_t)fs * nvec;
   void* face_work = wp;
   wp += face_bytes;
+  int* err = (int*)wp;  // time-out flag of the tensor-core projections
+  wp += 256;
+  void* part = wp;
+  wp += part_bytes;
+  cudaMemsetAsync(err, 0, sizeof(int), st);
   const void* phi = sub->vecs;
   if (conv_phi) {
     phi = wp;
@@ -630,16 +642,22 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
   if (s == HDCR_OK) {
     if (op_dtype == HDCR_C128)
       s = build_op<double>(sub, p->M5, p->mf, (const cpx<double>*)Ub, (const cpx<double>*)phi, (cpx<double>*)Y,
-                           (cpx<double>*)face_work, (cpx<double>*)co->A, co->nbr, st);
+                           (cpx<double>*)face_work, (cpx<double>*)co->A, co->nbr, nullptr, err, st);
     else
       s = build_op<float>(sub, p->M5, p->mf, (const cpx<float>*)Ub, (const cpx<float>*)phi, (cpx<float>*)Y,
-                          (cpx<float>*)face_work, (cpx<float>*)co->A, co->nbr, st);
+                          (cpx<float>*)face_work, (cpx<float>*)co->A, co->nbr, (cpx<float>*)part, err, st);
   }
   if (s == HDCR_OK) {
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) s = cuda_status(e, "coarse operator build");
+    int herr = 0;
+    e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      s = cuda_status(e, "coarse operator build");
+    } else if (herr) {
+      set_error("coarse operator build: a tensor-core projection timed out");
+      s = HDCR_ERR_TIMEOUT;
+    }
   }
-  cudaFree(work);
   if (s != HDCR_OK) {
     hdcr_coarse_destroy(co);
     return s;

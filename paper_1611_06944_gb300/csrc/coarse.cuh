@@ -6,6 +6,8 @@
 // fine sites is contiguous in every plane).
 #pragma once
 
+#include <mutex>
+
 #include "krylov.cuh"
 
 namespace hdcr {
@@ -60,6 +62,12 @@ struct hdcr_subspace {
   int dtype;      // storage of the basis vectors (HDCR_C128 / HDCR_C64)
   void* vecs;     // nvec fields, plane layout, block-orthonormal
   int device;
+  // scratch of hdcr_build_coarse_op, kept for the next build from this basis (a
+  // rebuild after a gauge update needs no allocation); builds from one subspace
+  // are serialised on build_mu
+  mutable std::mutex build_mu;
+  mutable void* build_ws = nullptr;
+  mutable size_t build_ws_bytes = 0;
 };
 
 struct hdcr_coarse {

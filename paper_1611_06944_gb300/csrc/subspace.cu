@@ -362,5 +362,6 @@ extern "C" int hdcr_subspace_get_vectors(const hdcr_subspace* sub, void* out, vo
 extern "C" void hdcr_subspace_destroy(hdcr_subspace* sub) {
   if (!sub) return;
   if (sub->vecs) cudaFree(sub->vecs);
+  if (sub->build_ws) cudaFree(sub->build_ws);
   delete sub;
 }

@@ -1,0 +1,55 @@
+"""The FP32 little Dirac operator (Eq. 4.5), whose projections run on the
+tensor cores, against the FP64 build from the same basis (itself checked
+against the oracle in test_gpu_multigrid).  The cases cover the operand
+shapes the kernel pads differently (2 nvec = 16, 48, 64, 128 rows), chunks of
+the contraction dimension that end ragged, and coarse extents of 2 (legs that
+reach the same coarse site)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import dev, host, links, relerr
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_1611_06944_gb300 as hd
+    return hd
+
+
+# (L, Ls, block, nvec, bc)
+CASES = [
+    ((4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 1),
+    ((6, 4, 4, 6), 5, (3, 2, 2, 3), 24, -1),
+    ((8, 8, 4, 4), 6, (4, 4, 2, 2), 32, 1),
+    ((4, 4, 4, 8), 4, (2, 2, 2, 4), 64, 1),
+]
+
+
+@pytest.mark.parametrize("L,Ls,block,nvec,bc", CASES)
+def test_fp32_coarse_op_matches_fp64_build(hd, L, Ls, block, nvec, bc):
+    U = synth.gauge_field(L, 0.5, 5100)
+    rng = synth.rng(5101)
+    lat = hd.Lattice(L, Ls, bc)
+    shape = (nvec, lat.V4, 12, Ls)
+    v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    sub64 = hd.subspace_from_vectors(lat, block, dev(v), store_dtype=torch.complex128)
+    sub32 = hd.subspace_from_vectors(lat, block, dev(v), store_dtype=torch.complex64)
+    Ud = dev(links(U))
+    A64 = host(hd.build_coarse_op(sub64, Ud, 1.8, 0.01).op())
+    A32 = host(hd.build_coarse_op(sub32, Ud, 1.8, 0.01, op_dtype=torch.complex64).op())
+    # Bound: the FP32 basis differs from the FP64 one by ~1e-7 relative.  Each
+    # product of the projection (three TF32 passes: hi*hi + hi*lo + lo*hi) is good
+    # to ~2^-20 relative and the tensor-core accumulator (not rounded to nearest)
+    # drifts by about as much over a 512-term segment, so an entry is good to
+    # ~1e-6 of sum |phi_j| |Y_k|.  For random bases the entries are smaller than
+    # that sum by the cancellation of ~sqrt(K) random-sign terms (K = 12 Ls |block|
+    # up to 1536 here), i.e. up to ~40x: 1e-5 relative overall, 1e-4 per leg.
+    assert relerr(A32, A64) < 1e-5
+    # leg by leg, so that a wrong leg cannot hide behind the large diagonal one
+    for leg in range(9):
+        assert relerr(A32[:, leg], A64[:, leg]) < 1e-4
