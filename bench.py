@@ -59,7 +59,7 @@ def bytes_per_site(real_bytes: int, Ls: int) -> float:
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal, profiling recipe)
 # DRAM traffic of one FP64 / FP32 stencil launch at 16^4 x 16 from ncu, with the hash of
 # the stencil sources it was measured on (reported as null once the sources change)
-NCU_TRAFFIC = {"f64": 450.38e6, "f32": 205.09e6, "src_hash": "112b32b54d40c6d9"}
+NCU_TRAFFIC = {"f64": 452.55e6, "f32": 205.69e6, "src_hash": "a63f417e2e28ba4e"}
 
 
 def stencil_src_hash() -> str:

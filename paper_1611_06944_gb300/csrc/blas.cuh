@@ -17,6 +17,9 @@ int launch_convert(const void* in, int idt, void* out, int odt, long long n, cud
 bool g5dwf_x2_ok(const Geom& g, const void* in, const void* out);
 int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in, cpx<float>* out,
                     int nrhs, RedScratch* rs, double* result, cudaStream_t st);
+// prev <- 2 (a H in + b cur) - prev for nrhs fields (a Chebyshev step fused into the FP32 stencil)
+int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in,
+                         const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st);
 
 template <typename R>
 int launch_cdot(const void* u, const void* v, long long n, RedScratch rs, double* result, cudaStream_t st);

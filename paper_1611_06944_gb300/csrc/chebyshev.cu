@@ -195,8 +195,66 @@ int cheb_filter(const FineOp<R>& H, cpx<R>* x, int order, double lam_cut, double
   return HDCR_OK;
 }
 
+template <typename R>
+int cheb_filter_multi(const FineOp<R>& H, cpx<R>* x, int nrhs, int order, double lam_cut, double lam_max,
+                      cpx<R>* work, double* n2, RedScratch rs, cudaStream_t st) {
+  const long long n = H.n(), N = n * nrhs;
+  const int nb = num_blocks(N, 256, 8192);
+  const double lo = lam_cut * lam_cut, hi = lam_max * lam_max;
+  const R a = (R)(2.0 / (hi - lo)), b = (R)(-(hi + lo) / (hi - lo));
+  cpx<R>* t0 = work;
+  cpx<R>* t1 = work + N;
+  cpx<R>* h1 = work + 2 * N;
+  cpx<R>* h2 = work + 3 * N;  // the unfused path only
+  bool fused = false;
+  if constexpr (sizeof(R) == 4) fused = g5dwf_x2_ok(H.g, x, work) && g5dwf_x2_ok(H.g, work + N, work + 2 * N);
+  const void* U = H.U;
+  // T_0 = x, T_1 = a H^2 x + b x
+  rescale_copy(x, t0, N, (R)1, st);
+  HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, U, t0, h1, nrhs, st));
+  if (fused) {
+    HDCR_CUDA_TRY(cudaMemsetAsync(t1, 0, sizeof(cpx<R>) * N, st));
+    HDCR_TRY(launch_g5dwf_x2_cheb(H.g, H.M5, H.mf, (const cpx<float>*)U, (const cpx<float>*)h1,
+                                  (const cpx<float>*)t0, (cpx<float>*)t1, (float)(0.5 * a), (float)(0.5 * b), nrhs,
+                                  st));
+  } else {
+    HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, U, h1, h2, nrhs, st));
+    cheb_first_kernel<R><<<nb, 256, 0, st>>>(h2, t0, t1, nullptr, N, a, b, (R)0, (R)0, 0); count_launch();
+    HDCR_LAUNCH_CHECK();
+  }
+  cpx<R>* prev = t0;
+  cpx<R>* cur = t1;
+  for (int k = 2; k <= order; ++k) {
+    // T_k = 2 t(H^2) T_{k-1} - T_{k-2}, written over T_{k-2}
+    HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, U, cur, h1, nrhs, st));
+    if (fused) {
+      HDCR_TRY(launch_g5dwf_x2_cheb(H.g, H.M5, H.mf, (const cpx<float>*)U, (const cpx<float>*)h1,
+                                    (const cpx<float>*)cur, (cpx<float>*)prev, (float)a, (float)b, nrhs, st));
+    } else {
+      HDCR_TRY(launch_g5dwf<R>(H.g, H.M5, H.mf, U, h1, h2, nrhs, st));
+      cheb_step_kernel<R><<<nb, 256, 0, st>>>(h2, cur, prev, nullptr, N, a, b, (R)0, 0); count_launch();
+      HDCR_LAUNCH_CHECK();
+    }
+    cpx<R>* t = prev;
+    prev = cur;
+    cur = t;
+    if (k % 8 == 0) {  // keep the growing recurrence in range: one common rescale of both terms
+      HDCR_TRY(launch_norm2<R>(cur, N, rs, n2, st));
+      rescale2_kernel<R><<<nb, 256, 0, st>>>(cur, prev, N, n2); count_launch();
+      HDCR_LAUNCH_CHECK();
+    }
+  }
+  HDCR_TRY(launch_norm2<R>(cur, N, rs, n2, st));
+  rescale2_kernel<R><<<nb, 256, 0, st>>>(cur, (cpx<R>*)nullptr, N, n2); count_launch();
+  HDCR_LAUNCH_CHECK();
+  rescale_copy(cur, x, N, (R)1, st);
+  return HDCR_OK;
+}
+
 #define HDCR_INST_CHEB(R)                                                                            \
   template int cheb_work_alloc<R>(ChebWork<R>*, long long);                                         \
+  template int cheb_filter_multi<R>(const FineOp<R>&, cpx<R>*, int, int, double, double, cpx<R>*, double*,  \
+                                    RedScratch, cudaStream_t);                                      \
   template void cheb_work_free<R>(ChebWork<R>*);                                                    \
   template int cheb_smoother<R>(const FineOp<R>&, const cpx<R>*, cpx<R>*, const std::vector<double>&, \
                                 double, double, ChebWork<R>&, cudaStream_t, int*);                  \

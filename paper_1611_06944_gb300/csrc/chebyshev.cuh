@@ -34,6 +34,14 @@ template <typename R>
 int cheb_filter(const FineOp<R>& H, cpx<R>* x, int order, double lam_cut, double lam_max, ChebWork<R>& w,
                 RedScratch rs, cudaStream_t st);
 
+// The same filter on nrhs fields x at once (stencil launches over all of them; in
+// FP32 each step's recurrence is fused into the second stencil).  work holds
+// 4 * nrhs fields, n2 one device double.  The fields share one rescaling: the
+// result is x scaled by a common factor, not normalised field by field.
+template <typename R>
+int cheb_filter_multi(const FineOp<R>& H, cpx<R>* x, int nrhs, int order, double lam_cut, double lam_max,
+                      cpx<R>* work, double* n2, RedScratch rs, cudaStream_t st);
+
 template <typename R>
 void rescale_copy(const cpx<R>* in, cpx<R>* out, long long n, R s, cudaStream_t st);
 

@@ -33,6 +33,14 @@ struct cx2 {
   float2 re, im;  // lanes: sites s and s+1
 };
 
+constexpr int X2_STORE = 0, X2_DOT = 1, X2_CHEB = 2;  // epilogues of the kernel
+
+// Chebyshev step of the epilogue X2_CHEB: out <- 2 (a H in + b cur) - out
+struct X2Cheb {
+  const cpx<float>* cur;
+  float a, b;
+};
+
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -165,14 +173,17 @@ struct X2Stage {
   int li[X2_SITES][8];
 };
 
-// One pass of H over the pair (x4, s0, s0+1) of every right-hand side; DOT adds
-// Re <in, H in> of the pair's output sites into *dot (products summed in FP32
-// within each spin half, where the terms share the sign of Gamma5, and the two
-// halves combined in FP64, where they cancel).
-template <int LS, bool DOT>
+// One pass of H over the pair (x4, s0, s0+1) of one right-hand side.  The
+// epilogue EPI: X2_STORE writes H in; X2_DOT also adds Re <in, H in> of the
+// pair's output sites into *dot (products summed in FP32 within each spin half,
+// where the terms share the sign of Gamma5, and the two halves combined in
+// FP64, where they cancel); X2_CHEB writes the next Chebyshev term
+// 2 (a H in + b cur) - prev over prev (cur, prev read at the output sites).
+template <int LS, int EPI>
 __device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __restrict__ U, const X2Stage& sm,
-                                          int site, int x4, int p, float diag, float mf, const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
-                                          double* dot) {
+                                          int site, int x4, int p, float diag, float mf,
+                                          const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
+                                          double* dot, const X2Cheb& ch) {
   const int ls = ls_of<LS>(g);
   const int s0 = 2 * p;
   const unsigned base = (unsigned)(x4 * 12 * ls);
@@ -219,9 +230,14 @@ __device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __res
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
     const cx2 v = c < 6 ? up[c / 3][c % 3] : lo[c / 3 - 2][c % 3];
-    const float4 o = make_float4(v.re.y, v.im.y, v.re.x, v.im.x);
+    float4 o = make_float4(v.re.y, v.im.y, v.re.x, v.im.x);
+    if constexpr (EPI == X2_CHEB) {
+      const float4 cv = ld4(ch.cur + ob + c * ls), pv = ld4(out + ob + c * ls);
+      o = make_float4(2.f * fmaf(ch.a, o.x, ch.b * cv.x) - pv.x, 2.f * fmaf(ch.a, o.y, ch.b * cv.y) - pv.y,
+                      2.f * fmaf(ch.a, o.z, ch.b * cv.z) - pv.z, 2.f * fmaf(ch.a, o.w, ch.b * cv.w) - pv.w);
+    }
     *reinterpret_cast<float4*>(out + ob + c * ls) = o;
-    if (DOT) {
+    if (EPI == X2_DOT) {
       const float4 a = ld4(in + ob + c * ls);
       float& e = d[c < 6 ? 0 : 1];
       e = fmaf(a.x, o.x, e);
@@ -230,7 +246,7 @@ __device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __res
       e = fmaf(a.w, o.w, e);
     }
   }
-  if (DOT) *dot += (double)d[0] + (double)d[1];
+  if (EPI == X2_DOT) *dot += (double)d[0] + (double)d[1];
 }
 
 // Neighbours, boundary factors and link indices of the 4d sites [x0, x0 + X2_SITES).
@@ -267,12 +283,12 @@ __device__ __forceinline__ void stage_sites(const Geom& g, int x0, X2Stage& sm) 
 // blockDim = X2_SITES * Ls/2: thread (site, p) = (tid / (Ls/2), tid % (Ls/2)).
 // A CTA loops over groups of X2_SITES 4d sites (grid-stride) and, within a
 // group, over the right-hand sides.
-template <int LS, bool DOT>
+template <int LS, int EPI>
 __global__ void __launch_bounds__(128, 4) g5dwf_x2_kernel(Geom g, float diag, float mf,
                                                           const cpx<float>* __restrict__ U,
                                                           const cpx<float>* __restrict__ in,
                                                           cpx<float>* __restrict__ out, int nrhs, RedScratch rs,
-                                                          double* result) {
+                                                          double* result, X2Cheb ch) {
   __shared__ X2Stage sm;
   const int ls = ls_of<LS>(g);
   const int lp = ls >> 1;
@@ -286,11 +302,15 @@ __global__ void __launch_bounds__(128, 4) g5dwf_x2_kernel(Geom g, float diag, fl
     const int x4 = x0 + site;
     if (x4 < g.V4) {
       for (int r = 0; r < nrhs; ++r)
-        site_pair<LS, DOT>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot);
+        if constexpr (EPI == X2_CHEB)
+          site_pair<LS, EPI>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot,
+                             X2Cheb{ch.cur + r * fsize, ch.a, ch.b});
+        else
+          site_pair<LS, EPI>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot, ch);
     }
     __syncthreads();  // the per-site data is refilled for the next group
   }
-  if (DOT) {
+  if (EPI == X2_DOT) {
     double v[1] = {dot};
     double tot[1];
     if (grid_reduce<1>(v, rs, tot)) *result = tot[0];
@@ -307,15 +327,27 @@ int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, co
   const int threads = X2_SITES * (g.Ls / 2);
   const int groups = (g.V4 + X2_SITES - 1) / X2_SITES;
   const float diag = (float)(5.0 - M5), fmf = (float)mf;
+  const X2Cheb none_ch{nullptr, 0.f, 0.f};
   if (rs) {
     const int blocks = groups < RED_MAX_BLOCKS ? groups : RED_MAX_BLOCKS;
-    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, true><<<blocks, threads, 0, st>>>(g, diag, fmf, U, in, out, nrhs,
-                                                                                    *rs, result)));
+    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, X2_DOT><<<blocks, threads, 0, st>>>(g, diag, fmf, U, in, out, nrhs,
+                                                                                      *rs, result, none_ch)));
   } else {
     RedScratch none{nullptr, nullptr};
-    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, false><<<groups, threads, 0, st>>>(g, diag, fmf, U, in, out, nrhs,
-                                                                                     none, nullptr)));
+    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, X2_STORE><<<groups, threads, 0, st>>>(
+                               g, diag, fmf, U, in, out, nrhs, none, nullptr, none_ch)));
   }
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in,
+                         const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st) {
+  const int threads = X2_SITES * (g.Ls / 2);
+  const int groups = (g.V4 + X2_SITES - 1) / X2_SITES;
+  RedScratch none{nullptr, nullptr};
+  HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, X2_CHEB><<<groups, threads, 0, st>>>(
+                             g, (float)(5.0 - M5), (float)mf, U, in, prev, nrhs, none, nullptr, X2Cheb{cur, a, b})));
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }

@@ -218,6 +218,49 @@ static int filter_one(const FineOp<R>& H, cpx<R>* x, const cpx<R>* zero, const h
   return cheb_filter<R>(H, x, sp->order, sp->lam_cut, sp->lam_max, cw, w.rb.rs, st);
 }
 
+// step 1 with the Chebyshev filter: all nvec/2 noise fields through one run of
+// the recurrence (multi-field stencil launches), then each is normalised and split
+template <typename R>
+static int filter_all_cheb(const Geom& g, const hdcr_dwf_params* p, const void* U, const void* noise,
+                           const hdcr_subspace_params* sp, cpx<double>* vecs, cudaStream_t st) {
+  const long long fs = g.V5 * 12;
+  const int half = sp->nvec / 2;
+  const bool f64 = sizeof(R) == 8;
+  // x (half fields), recurrence work (4 * half fields), x64 scratch, U in R
+  const size_t bytes = sizeof(cpx<R>) * fs * half * 5 + sizeof(cpx<double>) * fs +
+                       (f64 ? 0 : sizeof(cpx<R>) * g.V4 * 36) + 1024;
+  void* mem = nullptr;
+  HDCR_CUDA_TRY(cudaMalloc(&mem, bytes));
+  cpx<R>* x = (cpx<R>*)mem;
+  cpx<R>* work = x + fs * half;
+  cpx<double>* x64 = (cpx<double>*)(work + 4 * fs * half);
+  const cpx<R>* Ur = (const cpx<R>*)U;
+  if (!f64) {
+    cpx<R>* u32 = (cpx<R>*)(x64 + fs);
+    launch_convert(U, HDCR_C128, u32, HDCR_C64, (long long)g.V4 * 36, st);
+    Ur = u32;
+  }
+  RedBuffers rb{{nullptr, nullptr}, nullptr, 0, nullptr};
+  int s = red_buffers_alloc(&rb, 2);
+  FineOp<R> H{g, p->M5, p->mf, Ur};
+  if (s == HDCR_OK) s = launch_convert(noise, HDCR_C128, x, f64 ? HDCR_C128 : HDCR_C64, fs * half, st);
+  if (s == HDCR_OK) s = cheb_filter_multi<R>(H, x, half, sp->order, sp->lam_cut, sp->lam_max, work, rb.scal, rb.rs, st);
+  for (int i = 0; i < half && s == HDCR_OK; ++i) {
+    s = launch_convert(x + (long long)i * fs, f64 ? HDCR_C128 : HDCR_C64, x64, HDCR_C128, fs, st);
+    if (s == HDCR_OK) s = launch_norm2<double>(x64, fs, rb.rs, rb.scal + 1, st);
+    if (s != HDCR_OK) break;
+    scale_rsqrt_kernel<<<num_blocks(fs, 256, 4096), 256, 0, st>>>(x64, fs, rb.scal + 1); count_launch();
+    gamma5_split_kernel<<<num_blocks(fs, 256, 4096), 256, 0, st>>>(g, x64, vecs + (long long)i * fs,
+                                                                   vecs + (long long)(i + half) * fs); count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, "subspace filtering");
+  }
+  cudaStreamSynchronize(st);
+  red_buffers_free(&rb);
+  cudaFree(mem);
+  return s;
+}
+
 template <typename R>
 static int filter_all(const Geom& g, const hdcr_dwf_params* p, const void* U, const void* noise,
                       const hdcr_subspace_params* sp, cpx<double>* vecs, cudaStream_t st) {
@@ -269,8 +312,13 @@ static int build_subspace_impl(const Geom& g, const BlockGeom& bg, const hdcr_dw
   const long long fs = g.V5 * 12;
   cpx<double>* vecs = nullptr;
   HDCR_CUDA_TRY(cudaMalloc(&vecs, sizeof(cpx<double>) * fs * sp->nvec));
-  int s = sp->filter_dtype == HDCR_C128 ? filter_all<double>(g, p, U, noise, sp, vecs, st)
-                                        : filter_all<float>(g, p, U, noise, sp, vecs, st);
+  int s;
+  if (sp->kind == HDCR_SUBSPACE_CHEBYSHEV)
+    s = sp->filter_dtype == HDCR_C128 ? filter_all_cheb<double>(g, p, U, noise, sp, vecs, st)
+                                      : filter_all_cheb<float>(g, p, U, noise, sp, vecs, st);
+  else
+    s = sp->filter_dtype == HDCR_C128 ? filter_all<double>(g, p, U, noise, sp, vecs, st)
+                                      : filter_all<float>(g, p, U, noise, sp, vecs, st);
   if (s != HDCR_OK) {
     cudaFree(vecs);
     return s;
