@@ -117,6 +117,23 @@ int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites);
 int hdcr_apply_g5dwf(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
                      const void* in, void* out, int dtype, int nrhs, void* stream);
 
+/* Tile-shape autotuner of the FP32 operator (a property of this library, not a
+ * step of the method).  The FP32 kernel runs one CTA per tile of 4d sites;
+ * several tile shapes are compiled in.  With the tuner on (mode 1, the
+ * default) the first plain FP32 application of H (hdcr_apply_g5dwf, or the
+ * solvers' own calls) for a given (device, lattice, Ls, nrhs), outside a
+ * stream capture, runs and event-times every tile shape that divides the
+ * lattice on the call's own fields and stream (synchronising it once), and
+ * keeps the fastest for every later FP32 call with that key.  Results do not
+ * depend on the tile.  mode 0 keeps the default linear tile of 16 consecutive
+ * 4d sites, mode 2 forgets every tuned choice.  force_variant >= 0 runs that
+ * variant wherever it fits (diagnostics), -1 restores tuning.
+ * hdcr_stencil_tune_info: the variant chosen for (g, nrhs) or -1 if none yet,
+ * and the measured microseconds per launch of the first ``nus`` variants
+ * (-1 where a variant does not fit).  Errors: BAD_ARG. */
+int hdcr_stencil_tune(int mode, int force_variant);
+int hdcr_stencil_tune_info(const hdcr_geom* g, int nrhs, int* variant, float* us, int nus);
+
 /* out = Gamma5 in = gamma5 R5 in (Section 3), nfields fields; in == out not allowed. */
 int hdcr_apply_gamma5_r5(const hdcr_geom* g, const void* in, void* out, int dtype,
                          int nfields, void* stream);

@@ -62,13 +62,30 @@ def stencil_timer_read(dtype: torch.dtype) -> dict:
             "all_sites": asites.value}
 
 
+def stencil_tune(mode: int = 1, force_variant: int = -1) -> None:
+    """FP32 stencil tile autotuner: mode 1 tunes on first use (default), 0 keeps the
+    default tile, 2 forgets tuned choices; force_variant >= 0 pins one tile variant."""
+    _check(_L.hdcr_stencil_tune(int(mode), int(force_variant)), "stencil_tune")
+
+
+def stencil_tune_info(lat: "Lattice", nrhs: int = 1, nvariants: int = 16) -> dict:
+    """The tile variant tuned for (lat, nrhs) (-1 if none yet) and the microseconds per
+    launch the tuner measured for each variant (-1 where it does not fit)."""
+    v = ctypes.c_int()
+    us = (ctypes.c_float * nvariants)()
+    g = lat.c_geom()
+    _check(_L.hdcr_stencil_tune_info(ctypes.byref(g), int(nrhs), ctypes.byref(v), us, nvariants),
+           "stencil_tune_info")
+    return {"variant": v.value, "us": [round(float(x), 2) for x in us]}
+
+
 def load_library():
     """Load libhdcr.so now (raises ImportError if it has not been built)."""
     return _L.hdcr_version()
 
 __all__ = [
     "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
-    "convert", "cdot", "cdot_noalloc", "norm2", "cr_solve", "cr_solve_into", "library_path",
+    "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
     "hdcr_solve", "hdcr_solve_into", "gauge_force", "HDCRSolve", "solve_autograd",

@@ -86,6 +86,8 @@ SIGNATURES = {
     "hdcr_stencil_timer_read": (_I, [_I, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "hdcr_stencil_timer_count": (_I, [_I, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "hdcr_apply_g5dwf": (_I, [_G, _DP, _P, _P, _P, _I, _I, _P]),
+    "hdcr_stencil_tune": (_I, [_I, _I]),
+    "hdcr_stencil_tune_info": (_I, [_G, _I, C.POINTER(C.c_int), C.POINTER(C.c_float), _I]),
     "hdcr_apply_gamma5_r5": (_I, [_G, _P, _P, _I, _I, _P]),
     "hdcr_fermion_pack": (_I, [_G, _P, _P, _I, _I, _P]),
     "hdcr_fermion_unpack": (_I, [_G, _P, _P, _I, _I, _P]),

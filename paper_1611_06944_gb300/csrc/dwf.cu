@@ -212,6 +212,24 @@ extern "C" int hdcr_apply_g5dwf(const hdcr_geom* gp, const hdcr_dwf_params* p, c
   return HDCR_ERR_BAD_ARG;
 }
 
+extern "C" int hdcr_stencil_tune(int mode, int force_variant) {
+  if (mode < 0 || mode > 2 || force_variant < -1 || force_variant >= 64) {
+    set_error("hdcr_stencil_tune: mode must be 0, 1 or 2 and force_variant >= -1");
+    return HDCR_ERR_BAD_ARG;
+  }
+  return x2_tune_mode(mode, force_variant);
+}
+
+extern "C" int hdcr_stencil_tune_info(const hdcr_geom* gp, int nrhs, int* variant, float* us, int nus) {
+  Geom g;
+  HDCR_TRY(make_geom(gp, &g));
+  if (!variant || nrhs < 1 || nus < 0 || (nus > 0 && !us)) {
+    set_error("hdcr_stencil_tune_info: bad arguments");
+    return HDCR_ERR_BAD_ARG;
+  }
+  return x2_tune_info(g, nrhs, variant, us, nus);
+}
+
 extern "C" int hdcr_apply_gamma5_r5(const hdcr_geom* gp, const void* in, void* out, int dtype,
                                     int nfields, void* stream) {
   Geom g;

@@ -7,27 +7,31 @@
 // both sites (fma.rn.f32x2), and each spinor component is one 16-byte load of
 // two consecutive complex numbers of the psi[x4][c][s] layout.
 //
-// A CTA covers 16 4d sites (one x-row of a 16^4 lattice, so the +-x neighbours
-// of its rows are its own) and all their fifth-dimension pairs.  The neighbour
-// indices, boundary factors and link offsets of its sites are worked out once
-// into shared memory; the link elements themselves are read straight from
-// global memory, where the Ls/2 threads of a 4d site read the same address (one
-// broadcast per quarter warp, served by L1).  Staging the links in shared
-// memory instead, or sharing them between the threads with shuffles, measured
-// slower on GB300.
+// A CTA covers a tile of 4d sites (16 to 64 of them, x fastest) and all their
+// fifth-dimension pairs.  The neighbour indices, boundary factors and link
+// offsets of its sites are worked out once into shared memory; the spinors and
+// the link elements themselves are read straight from global memory, where the
+// Ls/2 threads of a 4d site read the same link address (one broadcast per
+// quarter warp) and the hops that stay inside the tile hit L1.  The tile shape
+// is picked per lattice by a small autotuner (below).  Staging the links in
+// shared memory instead, or sharing them between the threads with shuffles,
+// measured slower on GB300.
 //
 // The projection onto the two-spinor h of a hop and the fifth-dimension terms
 // are formed lane by lane in scalar FP32 (they write the packed registers
 // directly); the lower spin components are accumulated with the sign of Gamma5
 // already applied, and the store writes the pair at Ls-2-s with its lanes
 // swapped (the R5 reflection).
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "dwf_stencil.cuh"
 #include "reduce.cuh"
 
 namespace hdcr {
 
-constexpr int X2_SITES = 16;   // 4d sites per CTA
-constexpr int X2_MAX_LP = 8;   // fifth-dimension pairs per 4d site (Ls <= 16: at most 128 threads)
+constexpr int X2_MAX_LP = 8;   // fifth-dimension pairs per 4d site (Ls <= 16)
 
 struct cx2 {
   float2 re, im;  // lanes: sites s and s+1
@@ -164,23 +168,14 @@ __device__ __forceinline__ void hop_x2(const cpx<float>* __restrict__ L, const c
   }
 }
 
-// Per-CTA data: for each of the X2_SITES 4d sites and each hop
-// d = 2 mu + (0 forward, 1 backward) the neighbour site, the boundary factor
-// and the link (U_mu(x) forward, U_mu(x - mu) backward) as an index into U.
-struct X2Stage {
-  int nb[X2_SITES][8];
-  float coef[X2_SITES][8];
-  int li[X2_SITES][8];
-};
-
 // One pass of H over the pair (x4, s0, s0+1) of one right-hand side.  The
 // epilogue EPI: X2_STORE writes H in; X2_DOT also adds Re <in, H in> of the
 // pair's output sites into *dot (products summed in FP32 within each spin half,
 // where the terms share the sign of Gamma5, and the two halves combined in
 // FP64, where they cancel); X2_CHEB writes the next Chebyshev term
 // 2 (a H in + b cur) - prev over prev (cur, prev read at the output sites).
-template <int LS, int EPI>
-__device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __restrict__ U, const X2Stage& sm,
+template <int LS, int EPI, typename Stage>
+__device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __restrict__ U, const Stage& sm,
                                           int site, int x4, int p, float diag, float mf,
                                           const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
                                           double* dot, const X2Cheb& ch) {
@@ -249,14 +244,63 @@ __device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __res
   if (EPI == X2_DOT) *dot += (double)d[0] + (double)d[1];
 }
 
-// Neighbours, boundary factors and link indices of the 4d sites [x0, x0 + X2_SITES).
-__device__ __forceinline__ void stage_sites(const Geom& g, int x0, X2Stage& sm) {
-  for (int t = threadIdx.x; t < X2_SITES * 8; t += blockDim.x) {
+// Per-CTA data: for each of the SITES 4d sites of the CTA's tile and each hop
+// d = 2 mu + (0 forward, 1 backward) the neighbour site, the boundary factor
+// and the link (U_mu(x) forward, U_mu(x - mu) backward) as an index into U.
+template <int SITES>
+struct X2Stage {
+  int x4[SITES];
+  int nb[SITES][8];
+  float coef[SITES][8];
+  int li[SITES][8];
+};
+
+// Tile shapes of the CTA: TX x TY x TZ x TT 4d sites (x fastest), the tiles
+// laid out over the lattice in the same order; TY == 0 marks the linear tile of
+// TX consecutive 4d sites, which fits any volume.  A tile shares the hops that
+// stay inside it through L1 (the Ls/2 threads of a site, and the sites of the
+// tile, run on one SM at the same time).
+template <int TX, int TY, int TZ, int TT>
+struct Tile {
+  static constexpr bool linear = TY == 0;
+  static constexpr int sites = linear ? TX : TX * TY * TZ * TT;
+  // 4d index of site `site` of tile `grp`, or -1 past the end of the lattice
+  __device__ static int site_x4(const Geom& g, int grp, int site) {
+    if constexpr (linear) {
+      const int x4 = grp * TX + site;
+      return x4 < g.V4 ? x4 : -1;
+    } else {
+      const int nx = g.L[0] / TX, ny = g.L[1] / TY, nz = g.L[2] / TZ;
+      int r = grp;
+      const int gx = r % nx; r /= nx;
+      const int gy = r % ny; r /= ny;
+      const int gz = r % nz;
+      const int gt = r / nz;
+      int q = site;
+      const int sx = q % TX; q /= TX;
+      const int sy = q % TY; q /= TY;
+      const int sz = q % TZ;
+      const int st = q / TZ;
+      const int c[4] = {gx * TX + sx, gy * TY + sy, gz * TZ + sz, gt * TT + st};
+      return c[3] < g.L[3] ? x4_index(g, c) : -1;
+    }
+  }
+  __host__ static bool fits(const Geom& g) {
+    if (linear) return true;
+    return g.L[0] % TX == 0 && g.L[1] % TY == 0 && g.L[2] % TZ == 0 && g.L[3] % TT == 0;
+  }
+  __host__ __device__ static int tiles(const Geom& g) { return (g.V4 + sites - 1) / sites; }
+};
+
+// Neighbours, boundary factors and link indices of the sites of tile grp.
+template <typename T>
+__device__ __forceinline__ void stage_sites(const Geom& g, int grp, X2Stage<T::sites>& sm) {
+  for (int t = threadIdx.x; t < T::sites * 8; t += blockDim.x) {
     const int site = t >> 3, d = t & 7, mu = d >> 1;
-    const int x4 = x0 + site;
+    const int x4 = T::site_x4(g, grp, site);
     int nb = 0, li = 0;
     float cf = 0.f;
-    if (x4 < g.V4) {
+    if (x4 >= 0) {
       // coordinate mu of x4 and the index stride of direction mu (no dynamic indexing)
       const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
       const int lm = mu == 0 ? L0 : mu == 1 ? L1 : mu == 2 ? L2 : L3;
@@ -273,6 +317,7 @@ __device__ __forceinline__ void stage_sites(const Geom& g, int x0, X2Stage& sm) 
       li = mu * g.V4 + ((d & 1) ? nb : x4);
       cf = -0.5f * (float)ph;
     }
+    if (d == 0) sm.x4[site] = x4;
     sm.nb[site][d] = nb;
     sm.coef[site][d] = cf;
     sm.li[site][d] = li;
@@ -280,27 +325,24 @@ __device__ __forceinline__ void stage_sites(const Geom& g, int x0, X2Stage& sm) 
   __syncthreads();
 }
 
-// blockDim = X2_SITES * Ls/2: thread (site, p) = (tid / (Ls/2), tid % (Ls/2)).
-// A CTA loops over groups of X2_SITES 4d sites (grid-stride) and, within a
-// group, over the right-hand sides.
-template <int LS, int EPI>
-__global__ void __launch_bounds__(128, 4) g5dwf_x2_kernel(Geom g, float diag, float mf,
-                                                          const cpx<float>* __restrict__ U,
-                                                          const cpx<float>* __restrict__ in,
-                                                          cpx<float>* __restrict__ out, int nrhs, RedScratch rs,
-                                                          double* result, X2Cheb ch) {
-  __shared__ X2Stage sm;
+// blockDim = T::sites * Ls/2: thread (site, p) = (tid / (Ls/2), tid % (Ls/2)).
+// A CTA loops over tiles (grid-stride) and, within a tile, over the right-hand
+// sides.  Every tile shape runs 16 warps per SM at 128 registers a thread.
+template <int LS, int EPI, typename T>
+__global__ void __launch_bounds__(T::sites * 8, 64 / T::sites) g5dwf_x2_kernel(
+    Geom g, float diag, float mf, const cpx<float>* __restrict__ U, const cpx<float>* __restrict__ in,
+    cpx<float>* __restrict__ out, int nrhs, RedScratch rs, double* result, X2Cheb ch) {
+  __shared__ X2Stage<T::sites> sm;
   const int ls = ls_of<LS>(g);
   const int lp = ls >> 1;
   const int site = threadIdx.x / lp, p = threadIdx.x - site * lp;
-  const int groups = (g.V4 + X2_SITES - 1) / X2_SITES;
+  const int groups = T::tiles(g);
   const long long fsize = g.V5 * 12;
   double dot = 0.0;
   for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
-    const int x0 = grp * X2_SITES;
-    stage_sites(g, x0, sm);
-    const int x4 = x0 + site;
-    if (x4 < g.V4) {
+    stage_sites<T>(g, grp, sm);
+    const int x4 = sm.x4[site];
+    if (x4 >= 0) {
       for (int r = 0; r < nrhs; ++r)
         if constexpr (EPI == X2_CHEB)
           site_pair<LS, EPI>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot,
@@ -308,13 +350,178 @@ __global__ void __launch_bounds__(128, 4) g5dwf_x2_kernel(Geom g, float diag, fl
         else
           site_pair<LS, EPI>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot, ch);
     }
-    __syncthreads();  // the per-site data is refilled for the next group
+    __syncthreads();  // the per-site data is refilled for the next tile
   }
   if (EPI == X2_DOT) {
     double v[1] = {dot};
     double tot[1];
     if (grid_reduce<1>(v, rs, tot)) *result = tot[0];
   }
+}
+
+// ------------------------------------------------------------------ tile variants
+// Variant k of the kernel: the tile shapes tried by the autotuner.  All keep
+// 16 warps per SM; they differ in which neighbours a CTA finds in L1.
+#define HDCR_X2_TILES(V)   \
+  V(0, 16, 0, 0, 0)        \
+  V(1, 4, 4, 1, 1)         \
+  V(2, 8, 2, 1, 1)         \
+  V(3, 32, 0, 0, 0)        \
+  V(4, 16, 2, 1, 1)        \
+  V(5, 16, 4, 1, 1)
+constexpr int X2_VARIANTS = 6;
+
+template <int EPI, typename T>
+static void x2_launch(const Geom& g, int blocks, float diag, float mf, const cpx<float>* U, const cpx<float>* in,
+                      cpx<float>* out, int nrhs, RedScratch rs, double* result, X2Cheb ch, cudaStream_t st) {
+  const int threads = T::sites * (g.Ls / 2);
+  if (g.Ls == 16) {
+    g5dwf_x2_kernel<16, EPI, T><<<blocks, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
+  } else if (g.Ls == 8) {
+    g5dwf_x2_kernel<8, EPI, T><<<blocks, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
+  } else if constexpr (T::linear && T::sites == 16) {  // other Ls: the default tile only
+    g5dwf_x2_kernel<0, EPI, T><<<blocks, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
+  } else {
+    return;
+  }
+  count_launch();
+}
+
+// Whether variant v applies to the lattice, its tile count, and a launch of it.
+static bool x2_variant_fits(int v, const Geom& g, int* tiles, int* sites) {
+  switch (v) {
+#define HDCR_X2_FITS(K, A, B, C, D)        \
+  case K: {                               \
+    typedef Tile<A, B, C, D> T;           \
+    *tiles = T::tiles(g);                 \
+    *sites = T::sites;                    \
+    return T::fits(g) && T::sites * (g.Ls / 2) <= 512 && (K == 0 || g.Ls == 8 || g.Ls == 16); \
+  }
+    HDCR_X2_TILES(HDCR_X2_FITS)
+#undef HDCR_X2_FITS
+    default:
+      return false;
+  }
+}
+
+template <int EPI>
+static void x2_launch_variant(int v, const Geom& g, int blocks, float diag, float mf, const cpx<float>* U,
+                              const cpx<float>* in, cpx<float>* out, int nrhs, RedScratch rs, double* result,
+                              X2Cheb ch, cudaStream_t st) {
+  switch (v) {
+#define HDCR_X2_CASE(K, A, B, C, D)                                                            \
+  case K:                                                                                      \
+    x2_launch<EPI, Tile<A, B, C, D>>(g, blocks, diag, mf, U, in, out, nrhs, rs, result, ch, st); \
+    break;
+    HDCR_X2_TILES(HDCR_X2_CASE)
+#undef HDCR_X2_CASE
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------------ autotuner
+// The tile shape of the FP32 operator is chosen per (device, lattice, Ls,
+// nrhs) the first time a plain application of H meets that key outside a
+// stream capture: every fitting variant is run on the call's own fields (the
+// result does not depend on the tile, so ``out`` ends as the call leaves it)
+// and timed with CUDA events on the call's stream, and the fastest is kept for
+// every later call with that key (all epilogues).  Until then, and when the
+// tuner is off, the linear 16-site tile runs.
+namespace {
+struct TuneKey {
+  int dev, L[4], Ls, nrhs;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, L[0], L[1], L[2], L[3], Ls, nrhs) <
+           std::tie(o.dev, o.L[0], o.L[1], o.L[2], o.L[3], o.Ls, o.nrhs);
+  }
+};
+struct TuneEntry {
+  int variant;
+  float us[X2_VARIANTS];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+int g_tune_mode = 1;       // 1: tune on first use, 0: default tile only
+int g_force_variant = -1;  // >= 0: run this variant where it fits (diagnostics)
+
+TuneKey tune_key(const Geom& g, int nrhs) {
+  TuneKey k;
+  cudaGetDevice(&k.dev);
+  for (int i = 0; i < 4; ++i) k.L[i] = g.L[i];
+  k.Ls = g.Ls;
+  k.nrhs = nrhs;
+  return k;
+}
+}  // namespace
+
+static int x2_tune(const Geom& g, float diag, float mf, const cpx<float>* U, const cpx<float>* in, cpx<float>* out,
+                   int nrhs, cudaStream_t st, TuneEntry* e) {
+  cudaEvent_t a, b;
+  HDCR_CUDA_TRY(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cuda_status(cudaErrorMemoryAllocation, "cudaEventCreate");
+  }
+  RedScratch none{nullptr, nullptr};
+  const X2Cheb nc{nullptr, 0.f, 0.f};
+  e->variant = 0;
+  float best = 1e30f;
+  int status = HDCR_OK;
+  for (int v = 0; v < X2_VARIANTS && status == HDCR_OK; ++v) {
+    int tiles, sites;
+    e->us[v] = -1.f;
+    if (!x2_variant_fits(v, g, &tiles, &sites)) continue;
+    constexpr int reps = 3;
+    x2_launch_variant<X2_STORE>(v, g, tiles, diag, mf, U, in, out, nrhs, none, nullptr, nc, st);  // warm
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps; ++r)
+      x2_launch_variant<X2_STORE>(v, g, tiles, diag, mf, U, in, out, nrhs, none, nullptr, nc, st);
+    cudaEventRecord(b, st);
+    cudaError_t err = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    if (err != cudaSuccess) {
+      status = cuda_status(err, "stencil autotune");
+      break;
+    }
+    e->us[v] = ms * 1e3f / reps;
+    if (e->us[v] < best) {
+      best = e->us[v];
+      e->variant = v;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return status;
+}
+
+// The variant for this call: forced, tuned (tuning now if allowed), or the default.
+static int x2_pick(const Geom& g, float diag, float mf, const cpx<float>* U, const cpx<float>* in, cpx<float>* out,
+                   int nrhs, bool may_tune, cudaStream_t st, int* variant) {
+  int tiles, sites;
+  *variant = 0;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (g_force_variant >= 0) {
+    if (x2_variant_fits(g_force_variant, g, &tiles, &sites)) *variant = g_force_variant;
+    return HDCR_OK;
+  }
+  if (!g_tune_mode) return HDCR_OK;
+  const TuneKey k = tune_key(g, nrhs);
+  auto it = g_tune.find(k);
+  if (it != g_tune.end()) {
+    *variant = it->second.variant;
+    return HDCR_OK;
+  }
+  if (!may_tune) return HDCR_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return HDCR_OK;
+  TuneEntry e;
+  HDCR_TRY(x2_tune(g, diag, mf, U, in, out, nrhs, st, &e));
+  g_tune[k] = e;
+  *variant = e.variant;
+  return HDCR_OK;
 }
 
 // Whether the packed kernel applies: even Ls up to 16, 16-byte aligned fields.
@@ -324,18 +531,17 @@ bool g5dwf_x2_ok(const Geom& g, const void* in, const void* out) {
 
 int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in, cpx<float>* out,
                     int nrhs, RedScratch* rs, double* result, cudaStream_t st) {
-  const int threads = X2_SITES * (g.Ls / 2);
-  const int groups = (g.V4 + X2_SITES - 1) / X2_SITES;
   const float diag = (float)(5.0 - M5), fmf = (float)mf;
   const X2Cheb none_ch{nullptr, 0.f, 0.f};
+  int v, tiles, sites;
+  HDCR_TRY(x2_pick(g, diag, fmf, U, in, out, nrhs, true, st, &v));
+  x2_variant_fits(v, g, &tiles, &sites);
   if (rs) {
-    const int blocks = groups < RED_MAX_BLOCKS ? groups : RED_MAX_BLOCKS;
-    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, X2_DOT><<<blocks, threads, 0, st>>>(g, diag, fmf, U, in, out, nrhs,
-                                                                                      *rs, result, none_ch)));
+    const int blocks = tiles < RED_MAX_BLOCKS ? tiles : RED_MAX_BLOCKS;
+    x2_launch_variant<X2_DOT>(v, g, blocks, diag, fmf, U, in, out, nrhs, *rs, result, none_ch, st);
   } else {
     RedScratch none{nullptr, nullptr};
-    HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, X2_STORE><<<groups, threads, 0, st>>>(
-                               g, diag, fmf, U, in, out, nrhs, none, nullptr, none_ch)));
+    x2_launch_variant<X2_STORE>(v, g, tiles, diag, fmf, U, in, out, nrhs, none, nullptr, none_ch, st);
   }
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
@@ -343,12 +549,36 @@ int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, co
 
 int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in,
                          const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st) {
-  const int threads = X2_SITES * (g.Ls / 2);
-  const int groups = (g.V4 + X2_SITES - 1) / X2_SITES;
+  const float diag = (float)(5.0 - M5), fmf = (float)mf;
+  int v, tiles, sites;
+  HDCR_TRY(x2_pick(g, diag, fmf, U, in, prev, nrhs, false, st, &v));  // prev is read: no tuning here
+  x2_variant_fits(v, g, &tiles, &sites);
   RedScratch none{nullptr, nullptr};
-  HDCR_DISPATCH_LS(g.Ls, (g5dwf_x2_kernel<LSC, X2_CHEB><<<groups, threads, 0, st>>>(
-                             g, (float)(5.0 - M5), (float)mf, U, in, prev, nrhs, none, nullptr, X2Cheb{cur, a, b})));
+  x2_launch_variant<X2_CHEB>(v, g, tiles, diag, fmf, U, in, prev, nrhs, none, nullptr, X2Cheb{cur, a, b}, st);
   HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
+
+int x2_tune_mode(int mode, int force_variant) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (mode == 2) {
+    g_tune.clear();
+  } else {
+    g_tune_mode = mode != 0;
+  }
+  g_force_variant = force_variant;
+  return HDCR_OK;
+}
+
+int x2_tune_info(const Geom& g, int nrhs, int* variant, float* us, int nus) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(tune_key(g, nrhs));
+  if (it == g_tune.end()) {
+    *variant = -1;
+    return HDCR_OK;
+  }
+  *variant = it->second.variant;
+  for (int i = 0; i < nus; ++i) us[i] = i < X2_VARIANTS ? it->second.us[i] : -1.f;
   return HDCR_OK;
 }
 

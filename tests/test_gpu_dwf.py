@@ -161,3 +161,33 @@ def test_apply_fp32_unaligned_fields_take_the_scalar_kernel(hd):
     assert relerr(got_off, want) <= 1e-6
     assert relerr(got_al, want) <= 1e-6
     assert relerr(got_al, got_off) <= 1e-6
+
+
+@pytest.mark.parametrize("Ls", [8, 16])
+def test_fp32_tile_variants_identical(hd, Ls):
+    """Every tile shape of the FP32 kernel gives the same bits (the tile only changes
+    which CTA computes a site), matches the oracle, and the autotuner picks one of them."""
+    L = (16, 4, 4, 6)
+    U, psi = _inputs(L, Ls, 0.5, 1300)
+    U32 = dev(links(U).astype(np.complex64))
+    p32 = dev(planes(psi).astype(np.complex64))
+    lat = hd.Lattice(L, Ls, -1)
+    Ur = links(U).astype(np.complex64).astype(np.complex128).reshape(U.shape)
+    want = dwf.apply_H(Ur, natural(host(p32).astype(np.complex128), L, Ls), 1.8, 0.01, -1)
+    outs = []
+    try:
+        for v in range(6):
+            hd.stencil_tune(1, v)
+            outs.append(host(hd.apply_g5dwf(lat, U32, p32, 1.8, 0.01)))
+        hd.stencil_tune(2, -1)
+        tuned = host(hd.apply_g5dwf(lat, U32, p32, 1.8, 0.01))
+        info = hd.stencil_tune_info(lat)
+    finally:
+        hd.stencil_tune(1, -1)
+    assert relerr(natural(outs[0].astype(np.complex128), L, Ls), want) <= 1e-6
+    for v, o in enumerate(outs):
+        assert np.array_equal(o, outs[0]), f"tile variant {v} differs"
+    assert np.array_equal(tuned, outs[0])
+    assert 0 <= info["variant"] < 6 and info["us"][info["variant"]] > 0
+    assert all(u > 0 for u in info["us"][:6])  # every tile divides this lattice
+    assert all(u == -1 for u in info["us"][6:])
