@@ -324,6 +324,26 @@ typedef struct {
 int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x,
                const hdcr_solve_params* params, hdcr_solve_stats* stats, void* stream);
 
+/* hdcr_solve_multi: nrhs solves H x_r = b_r (r = 0..nrhs-1) by the method of
+ * hdcr_solve, advanced in lockstep so that every application of H, every
+ * smoother step, P^dag, the coarse solve and P is one launch over all nrhs
+ * fields (Section 4's solve, batched over right-hand sides, e.g. the 12
+ * spin-colour point sources of a propagator).  b and x hold nrhs C128 fields
+ * one after the other (x: initial guesses); U is C128.  Each right-hand side
+ * has its own flexible GCR coefficients; the iteration stops when every true
+ * residual |b_r - H x_r| / |b_r| <= tol, so iteration counts are shared.
+ * Requires the Chebyshev smoother and the dense coarse solve (the V-cycle is
+ * then a fixed sequence of launches); with use_graph != 0 the V-cycle is
+ * captured once into a CUDA graph on a library stream and replayed on
+ * ``stream`` every outer iteration (re-captured when U, the smoother or the
+ * coarse inverse change).  stats: nrhs entries (t_smoother and t_coarse are 0).
+ * nrhs 1..64.  Workspace (2 restart + ~9 fields per right-hand side) is cached
+ * on the coarse handle; solves on one handle must not overlap.  Synchronises
+ * ``stream``.  Errors: as hdcr_solve. */
+int hdcr_solve_multi(hdcr_coarse* co, const void* U, const void* b, void* x, int nrhs,
+                     const hdcr_solve_params* params, int use_graph, hdcr_solve_stats* stats,
+                     void* stream);
+
 /* ---------------------------------------------------------------- gauge force
  * hdcr_gauge_force: the gauge-link gradient of a solve (not in the paper;
  * derived from the operator above).  For H x = b and H y = eta, with

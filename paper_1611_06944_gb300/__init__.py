@@ -88,7 +88,7 @@ __all__ = [
     "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
-    "hdcr_solve", "hdcr_solve_into", "gauge_force", "HDCRSolve", "solve_autograd",
+    "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "gauge_force", "HDCRSolve", "solve_autograd",
 ]
 
 library_path = _lib.LIB_PATH
@@ -529,6 +529,26 @@ def hdcr_solve(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x0: torch.T
 
 
 # ------------------------------------------------------------------ gradient
+def hdcr_solve_multi(co: CoarseOperator, U: torch.Tensor, B: torch.Tensor, x0: torch.Tensor | None = None,
+                     tol: float = 1e-10, max_outer: int = 500, restart: int = 8, smoother_order: int = 10,
+                     cheb_lo: float = 1.0, cheb_hi: float = 64.0, inner_dtype: torch.dtype = torch.complex128,
+                     graph: bool = True, stream=None):
+    """H x_r = b_r for the nrhs fields of B at once (the Section 4 solve batched over
+    right-hand sides; Chebyshev smoother, dense coarse solve).  graph=True replays the
+    V-cycle from a captured CUDA graph.  Returns (X, list of per-rhs stats dicts); raises
+    HDCRError when the solve fails."""
+    if U.dtype != torch.complex128 or B.dtype != torch.complex128:
+        raise TypeError("hdcr_solve_multi takes complex128 links and sources")
+    nrhs = _nfields(co.sub.lat, B, "B")
+    X = torch.zeros_like(B) if x0 is None else x0.clone()
+    prm = _solve_params(tol, max_outer, restart, "chebyshev", smoother_order, cheb_lo, cheb_hi, "dense", 1e-4,
+                        1000, inner_dtype)
+    st = (_lib.hdcr_solve_stats * nrhs)()
+    _check(_L.hdcr_solve_multi(co.handle, _dev(U, "U"), _dev(B, "B"), _dev(X, "X"), nrhs, C_ref(prm),
+                               1 if graph else 0, st, _stream(stream)), "hdcr_solve_multi")
+    return X, [st[i].as_dict() for i in range(nrhs)]
+
+
 def gauge_force(lat: Lattice, x: torch.Tensor, w: torch.Tensor, stream=None) -> torch.Tensor:
     """F_mu(x) with dL = Re sum tr(dU F) for L = Re(eta^dag x), H x = b, w = Gamma5 H^{-1} eta.
     Returns a (4, V4, 3, 3) tensor, F[mu, x4, b, a] = (F_mu(x))_ba."""

@@ -110,6 +110,7 @@ SIGNATURES = {
     "hdcr_coarse_solve_dense": (_I, [_P, _P, _P, _I, _P]),
     "hdcr_coarse_destroy": (None, [_P]),
     "hdcr_solve": (_I, [_P, _P, _P, _P, C.POINTER(hdcr_solve_params), _ST, _P]),
+    "hdcr_solve_multi": (_I, [_P, _P, _P, _P, _I, C.POINTER(hdcr_solve_params), _I, _ST, _P]),
     "hdcr_gauge_force": (_I, [_G, _P, _P, _P, _I, _P]),
 }
 

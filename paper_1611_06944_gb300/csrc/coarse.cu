@@ -729,6 +729,7 @@ extern "C" int hdcr_prolong(const hdcr_subspace* sub, const void* coarse, void* 
 extern "C" void hdcr_coarse_destroy(hdcr_coarse* co) {
   if (!co) return;
   solve_cache_release(co);
+  multi_cache_release(co);
   if (co->A) cudaFree(co->A);
   if (co->nbr) cudaFree(co->nbr);
   if (co->Ainv) cudaFree(co->Ainv);

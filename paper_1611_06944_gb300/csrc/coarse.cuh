@@ -110,6 +110,7 @@ int coarse_invert(hdcr_coarse* co, cudaStream_t st);
 template <typename R>
 int launch_dense_solve(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st);
 void solve_cache_release(const hdcr_coarse* co);  // frees the cached solve workspace
+void multi_cache_release(const hdcr_coarse* co);  // frees the multi-RHS solve workspace and graph
 int subspace_check(const hdcr_subspace* sub);
 
 }  // namespace hdcr

@@ -108,6 +108,10 @@ void stencil_timer_begin(int kind, long long sites, cudaStream_t st, int* slot) 
   *slot = -1;
   std::lock_guard<std::mutex> lock(g_timer.mu);
   if (!g_timer.enabled) return;
+  // launches captured into a CUDA graph are not timed (their events would not
+  // be recorded by a replay)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   g_timer.all_launches[kind]++;
   g_timer.all_sites[kind] += sites;
   if (g_timer.used >= TIMER_PAIRS) return;

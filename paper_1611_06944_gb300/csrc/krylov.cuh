@@ -19,9 +19,10 @@ struct FineOp {
   Geom g;
   double M5, mf;
   const cpx<R>* U;
-  long long n() const { return g.V5 * 12; }  // complex entries of one field
+  int nrhs = 1;  // fields a vector of this operator spans (one launch applies H to all)
+  long long n() const { return g.V5 * 12 * nrhs; }  // complex entries of one vector
   int apply(const cpx<R>* in, cpx<R>* out, cudaStream_t st) const {
-    return launch_g5dwf<R>(g, M5, mf, U, in, out, 1, st);
+    return launch_g5dwf<R>(g, M5, mf, U, in, out, nrhs, st);
   }
   int apply_dot(const cpx<R>* in, cpx<R>* out, RedScratch rs, double* res, cudaStream_t st) const {
     return launch_g5dwf_dot<R>(g, M5, mf, U, in, out, rs, res, st);
