@@ -60,6 +60,9 @@ extern "C" {
 /* --------------------------------------------------------------- dtypes */
 #define HDCR_C128 0 /* complex double */
 #define HDCR_C64 1  /* complex float  */
+/* hdcr_build_coarse_op only: complex float storage, projections with one pass of
+ * TF32 tensor-core products (FP32 accumulation), relative error about 1e-3 */
+#define HDCR_C64_FAST 2
 
 typedef struct {
   int L[4]; /* Lx, Ly, Lz, Lt (4d extents, each >= 1)                     */
@@ -254,7 +257,9 @@ int hdcr_prolong(const hdcr_subspace* sub, const void* coarse, void* fine, int d
 /* ---------------------------------------------------------------- coarse operator
  * hdcr_build_coarse_op: little Dirac operator A^{ab}_{jk} = <phi_j^a | H | phi_k^b>
  * (Eq. 4.5), nonzero only for b = a and the 8 nearest coarse neighbours (the
- * sparsity noted after Eq. 4.6), stored as A[a][leg][j][k] in ``op_dtype``.  Leg
+ * sparsity noted after Eq. 4.6), stored as A[a][leg][j][k] in ``op_dtype``
+ * (HDCR_C64_FAST: stored as C64, built with single-pass TF32 products, for the
+ * mixed-precision solve whose FP64 outer iteration recovers the accuracy).  Leg
  * (mu, +-) collects the fine hops from block a into block a +- mu; on a coarse
  * extent of 2 the two legs of mu reach the same coarse site and both apply.  U
  * is C128 (converted internally when op_dtype is C64).  The subspace handle is

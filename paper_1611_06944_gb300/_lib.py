@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libhdcr.so")
 HDCR_OK = 0
 HDCR_C128 = 0
 HDCR_C64 = 1
+HDCR_C64_FAST = 2
 
 STATUS_NAMES = {
     0: "OK", -1: "BAD_ARG", -2: "BAD_GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE",

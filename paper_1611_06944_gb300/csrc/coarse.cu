@@ -6,7 +6,9 @@
 // block towards a +- mu.  Blocks span the whole fifth dimension, so the s-hops
 // and Gamma5's R5 stay inside a block.
 //   leg 0:   Y_k = H_0 phi_k on every site, A[a][0][j][k] = sum_{x in a} phi_j^dag Y_k
-//            for j <= k (A^{aa} is Hermitian; the rest is mirrored).
+//            for j <= k (A^{aa} is Hermitian; the rest is mirrored).  The FP32
+//            build instead applies all of H to the nvec fields at once (the
+//            packed stencil), projects, and subtracts the outward legs below.
 //   leg +mu: only the +mu face of block a takes part, and there the hop result
 //            is (hp; lo(hp)) after Gamma5 with hp = -1/2 U_mu(x) h (h the
 //            two-spinor projection of phi_k(x + mu)), lo = i sigma_mu (or 1 for
@@ -316,7 +318,8 @@ __global__ void __launch_bounds__(PROJ_THREADS) face_project_kernel(const cpx<R>
 // The legs not computed directly: A[a][0][j][k] = conj(A[a][0][k][j]) for j > k, and
 // A[a][-mu][j][k] = conj(A[a - mu][+mu][k][j]).
 template <typename R>
-__global__ void complete_legs_kernel(cpx<R>* __restrict__ A, const int* __restrict__ nbr, int Vc, int nvec) {
+__global__ void complete_legs_kernel(cpx<R>* __restrict__ A, const int* __restrict__ nbr, int Vc, int nvec,
+                                     bool leg0) {
   const long long n2 = (long long)nvec * nvec;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)Vc * 5 * n2) return;
@@ -327,7 +330,7 @@ __global__ void complete_legs_kernel(cpx<R>* __restrict__ A, const int* __restri
   cpx<R> v;
   int leg;
   if (w == 0) {
-    if (j <= k) return;
+    if (!leg0 || j <= k) return;
     leg = 0;
     v = A[(((long long)a * NLEGS) * nvec + k) * nvec + j];
   } else {
@@ -337,6 +340,29 @@ __global__ void complete_legs_kernel(cpx<R>* __restrict__ A, const int* __restri
     v = A[(((long long)b * NLEGS + leg_of(mu, +1)) * nvec + k) * nvec + j];
   }
   A[(((long long)a * NLEGS + leg) * nvec + j) * nvec + k] = cpx<R>(v.re, -v.im);
+}
+
+// Leg 0 from the projection of the whole of H: over block a, sum_x phi_j^dag (H phi_k)
+// (phi_k holding every block's vector k) is A^{aa} plus every leg that reaches a
+// neighbour block, so A[a][0] = P - sum_{leg > 0} A[a][leg]; the result is made
+// exactly Hermitian, (d + d^dag) / 2.  One thread per pair j <= k.
+template <typename R>
+__global__ void subtract_legs_kernel(cpx<R>* __restrict__ A, int Vc, int nvec) {
+  const long long n2 = (long long)nvec * nvec;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Vc * n2) return;
+  const int a = (int)(idx / n2);
+  const int j = (int)((idx - (long long)a * n2) / nvec), k = (int)(idx % nvec);
+  if (j > k) return;
+  cpx<R>* Aa = A + (long long)a * NLEGS * n2;
+  cpx<R> d1 = Aa[(long long)j * nvec + k], d2 = Aa[(long long)k * nvec + j];
+  for (int leg = 1; leg < NLEGS; ++leg) {
+    d1 = d1 - Aa[leg * n2 + (long long)j * nvec + k];
+    d2 = d2 - Aa[leg * n2 + (long long)k * nvec + j];
+  }
+  const cpx<R> h((R)0.5 * (d1.re + d2.re), (R)0.5 * (d1.im - d2.im));
+  Aa[(long long)j * nvec + k] = h;
+  Aa[(long long)k * nvec + j] = cpx<R>(h.re, -h.im);
 }
 
 // ------------------------------------------------------------ coarse apply
@@ -487,13 +513,13 @@ HDCR_INST_COARSE(float)
 
 template <typename R, int MU>
 static int launch_forward_leg(const Geom& g, const BlockGeom& bg, const cpx<R>* U, const cpx<R>* phi, cpx<R>* pt,
-                              cpx<R>* hf, cpx<R>* A, int nvec, cpx<R>* part, int* err, cudaStream_t st) {
+                              cpx<R>* hf, cpx<R>* A, int nvec, cpx<R>* part, int* err, int npass, cudaStream_t st) {
   const long long nf = bg.K5 / bg.b[MU];
   const long long n = (long long)bg.Vc * nf * nvec;
   face_kernel<R, MU><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, U, phi, pt, hf, nvec, nf); count_launch();
   if constexpr (sizeof(R) == 4) {
     const TcSrc src{pt, hf, nf * 6, 0, g, bg};
-    return launch_tc_project(src, A, nvec, leg_of(MU, +1), part, err, st);
+    return launch_tc_project(src, A, nvec, leg_of(MU, +1), part, err, npass, st);
   } else {
     int T = (int)(48 * 1024 / (2 * (size_t)nvec * sizeof(cpx<R>)));
     if (T > 256) T = 256;
@@ -505,9 +531,9 @@ static int launch_forward_leg(const Geom& g, const BlockGeom& bg, const cpx<R>* 
 }
 
 template <typename R>
-static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>* U, const cpx<R>* phi,
-                    cpx<R>* Y, cpx<R>* face_work, cpx<R>* A, const int* nbr, cpx<R>* part, int* err,
-                    cudaStream_t st) {
+static int build_legs(const hdcr_subspace* sub, double M5, double mf, const cpx<R>* U, const cpx<R>* phi,
+                      cpx<R>* Y, cpx<R>* face_work, cpx<R>* A, cpx<R>* part, cpx<R>* part2, int* err, int npass,
+                      bool full_y, cudaStream_t st, cudaStream_t sf, cudaEvent_t fork) {
   const Geom& g = sub->g;
   const BlockGeom& bg = sub->bg;
   const int nvec = sub->nvec;
@@ -517,28 +543,81 @@ static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>
   if (T > 16) T = 16;
   const size_t smem = 2 * (size_t)nvec * 12 * T * sizeof(cpx<R>);
   const long long n = g.V5 * nvec;
-  leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec); count_launch();
-  HDCR_LAUNCH_CHECK();
-  if constexpr (sizeof(R) == 4) {
-    const TcSrc src{phi, Y, bg.K5 * 12, 1, g, bg};
-    HDCR_TRY(launch_tc_project(src, A, nvec, 0, part, err, st));
+  if (full_y) {
+    HDCR_TRY(launch_g5dwf<R>(g, M5, mf, U, phi, Y, nvec, st));
   } else {
-    project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, 0, T, true); count_launch();
+    leg_self_kernel<R><<<num_blocks(n, 256), 256, 0, st>>>(g, bg, (R)(5.0 - M5), (R)mf, U, phi, Y, nvec); count_launch();
     HDCR_LAUNCH_CHECK();
   }
-  // forward legs on the block faces (six-component projections)
+  // forward legs on the block faces (six-component projections), on sf: they need
+  // only phi and U, and run while st applies H and projects leg 0
+  if (fork) HDCR_CUDA_TRY(cudaStreamWaitEvent(sf, fork, 0));
   long long nfmax = 0;
   for (int mu = 0; mu < 4; ++mu) nfmax = std::max(nfmax, bg.K5 / bg.b[mu]);
   cpx<R>* pt = face_work;
   cpx<R>* hf = face_work + (size_t)nvec * bg.Vc * nfmax * 6;
-  HDCR_TRY((launch_forward_leg<R, 0>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
-  HDCR_TRY((launch_forward_leg<R, 1>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
-  HDCR_TRY((launch_forward_leg<R, 2>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
-  HDCR_TRY((launch_forward_leg<R, 3>(g, bg, U, phi, pt, hf, A, nvec, part, err, st)));
+  HDCR_TRY((launch_forward_leg<R, 0>(g, bg, U, phi, pt, hf, A, nvec, part2, err, npass, sf)));
+  HDCR_TRY((launch_forward_leg<R, 1>(g, bg, U, phi, pt, hf, A, nvec, part2, err, npass, sf)));
+  HDCR_TRY((launch_forward_leg<R, 2>(g, bg, U, phi, pt, hf, A, nvec, part2, err, npass, sf)));
+  HDCR_TRY((launch_forward_leg<R, 3>(g, bg, U, phi, pt, hf, A, nvec, part2, err, npass, sf)));
+  if constexpr (sizeof(R) == 4) {
+    const TcSrc src{phi, Y, bg.K5 * 12, 1, g, bg};
+    HDCR_TRY(launch_tc_project(src, A, nvec, 0, part, err, npass, st));
+  } else {
+    project_kernel<R><<<bg.Vc, PROJ_THREADS, smem, st>>>(g, bg, phi, Y, A, nvec, 0, T, true); count_launch();
+    HDCR_LAUNCH_CHECK();
+  }
+  return HDCR_OK;
+}
+
+// The nine legs of A.  The face legs go to a second stream (forked after the
+// caller's earlier work on st and joined before the legs are completed); they
+// write other legs of A and their own partial sums.  On any failure the second
+// stream is drained before returning, so no kernel outlives the buffers.
+template <typename R>
+static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>* U, const cpx<R>* phi,
+                    cpx<R>* Y, cpx<R>* face_work, cpx<R>* A, const int* nbr, cpx<R>* part, cpx<R>* part2, int* err,
+                    int npass, cudaStream_t st) {
+  const BlockGeom& bg = sub->bg;
+  const int nvec = sub->nvec;
+  // FP32 with the packed stencil available: Y = H phi over all nvec fields in one
+  // launch (the fastest FP32 stencil), leg 0 recovered afterwards by subtracting the
+  // outward legs; otherwise Y = the in-block part of H only
+  const bool full_y = sizeof(R) == 4 && g5dwf_x2_ok(sub->g, phi, Y);
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool two = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) == cudaSuccess;
+  two = two && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(fork, st) == cudaSuccess;
+  cudaGetLastError();  // a failed optional call above leaves no sticky error
+  int status = build_legs<R>(sub, M5, mf, U, phi, Y, face_work, A, part, two ? part2 : part, err, npass, full_y,
+                             st, two ? s2 : st, two ? fork : nullptr);
+  if (two) {
+    if (status == HDCR_OK) {
+      const cudaError_t e = cudaEventRecord(join, s2);
+      if (e == cudaSuccess) {
+        const cudaError_t w = cudaStreamWaitEvent(st, join, 0);
+        if (w != cudaSuccess) status = cuda_status(w, "coarse build: join of the face legs");
+      } else {
+        status = cuda_status(e, "coarse build: join of the face legs");
+      }
+    }
+    if (status != HDCR_OK) cudaStreamSynchronize(s2);
+  }
+  if (s2) cudaStreamDestroy(s2);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  HDCR_TRY(status);
   // lower triangle of leg 0 and the backward legs from Hermiticity
   const long long nc = (long long)bg.Vc * 5 * nvec * nvec;
-  complete_legs_kernel<R><<<num_blocks(nc, 256), 256, 0, st>>>(A, nbr, bg.Vc, nvec); count_launch();
+  complete_legs_kernel<R><<<num_blocks(nc, 256), 256, 0, st>>>(A, nbr, bg.Vc, nvec, !full_y); count_launch();
   HDCR_LAUNCH_CHECK();
+  if (full_y) {
+    const long long n2 = (long long)bg.Vc * nvec * nvec;
+    subtract_legs_kernel<R><<<num_blocks(n2, 256), 256, 0, st>>>(A, bg.Vc, nvec); count_launch();
+    HDCR_LAUNCH_CHECK();
+  }
   return HDCR_OK;
 }
 
@@ -553,10 +632,13 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
     set_error("hdcr_build_coarse_op: null pointer");
     return HDCR_ERR_BAD_ARG;
   }
-  if (op_dtype != HDCR_C128 && op_dtype != HDCR_C64) {
+  if (op_dtype != HDCR_C128 && op_dtype != HDCR_C64 && op_dtype != HDCR_C64_FAST) {
     set_error("hdcr_build_coarse_op: unknown dtype %d", op_dtype);
     return HDCR_ERR_BAD_ARG;
   }
+  // HDCR_C64_FAST: stored as C64, tensor-core products in one TF32 pass
+  const int npass = op_dtype == HDCR_C64_FAST ? 1 : 3;
+  if (op_dtype == HDCR_C64_FAST) op_dtype = HDCR_C64;
   if (sub->nvec > 64) {
     set_error("hdcr_build_coarse_op: nvec = %d above the supported 64", sub->nvec);
     return HDCR_ERR_BAD_ARG;
@@ -575,7 +657,8 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
   for (int mu = 0; mu < 4; ++mu) nfmax = std::max(nfmax, bg.K5 / bg.b[mu]);
   const size_t face_bytes = cb * (size_t)2 * nvec * bg.Vc * nfmax * 6;
   // partial projections of the split tensor-core contractions (FP32 builds)
-  const size_t part_bytes = op_dtype == HDCR_C64 ? sizeof(cpx<float>) * TC_MAX_SPLIT * (size_t)bg.Vc * nvec * nvec : 0;
+  // (two sets: the face legs run on their own stream)
+  const size_t part_bytes = op_dtype == HDCR_C64 ? 2 * sizeof(cpx<float>) * TC_MAX_SPLIT * (size_t)bg.Vc * nvec * nvec : 0;
   size_t bytes = cb * (size_t)fs * nvec + face_bytes + 256 + part_bytes;
   if (conv_phi) bytes += cb * (size_t)fs * nvec;
   if (conv_u) bytes += cb * (size_t)g.V4 * 36;
@@ -642,10 +725,11 @@ extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_par
   if (s == HDCR_OK) {
     if (op_dtype == HDCR_C128)
       s = build_op<double>(sub, p->M5, p->mf, (const cpx<double>*)Ub, (const cpx<double>*)phi, (cpx<double>*)Y,
-                           (cpx<double>*)face_work, (cpx<double>*)co->A, co->nbr, nullptr, err, st);
+                           (cpx<double>*)face_work, (cpx<double>*)co->A, co->nbr, nullptr, nullptr, err, 3, st);
     else
       s = build_op<float>(sub, p->M5, p->mf, (const cpx<float>*)Ub, (const cpx<float>*)phi, (cpx<float>*)Y,
-                          (cpx<float>*)face_work, (cpx<float>*)co->A, co->nbr, (cpx<float>*)part, err, st);
+                          (cpx<float>*)face_work, (cpx<float>*)co->A, co->nbr, (cpx<float>*)part,
+                          (cpx<float>*)part + TC_MAX_SPLIT * (size_t)bg.Vc * nvec * nvec, err, npass, st);
   }
   if (s == HDCR_OK) {
     int herr = 0;

@@ -22,7 +22,7 @@
 // into registers while
 // the current one is split, stored in the canonical no-swizzle K-major layout
 // (8-row x 16-byte core matrices) and handed to the MMA issued by thread 0.
-// Three shared-memory stages rotate; an mbarrier per stage, signalled by
+// Two shared-memory stages alternate; an mbarrier per stage, signalled by
 // tcgen05.commit, says when it may be refilled, so each chunk needs one CTA
 // barrier only (between the stores and the MMA issue).  Every wait is bounded: on time-out the
 // kernel records an error, stops issuing, waits (bounded) for what it issued,
@@ -40,12 +40,19 @@ constexpr int TCP_SEG = 16;                 // chunks accumulated in tensor memo
 // MMA M: 64 when the 2 nvec rows of P fit, else 128; N = np
 __host__ __device__ inline int tcp_m(int nvec) { return 2 * nvec <= 64 ? 64 : 128; }
 __host__ __device__ inline int tcp_np(int nvec) { return (2 * nvec + 15) / 16 * 16; }
-__host__ __device__ inline int tcp_stage_bytes(int m, int np) { return 2 * m * TCP_KC * 4 + 2 * np * TCP_KC * 4; }
-// shared-memory stages: three for M = 64, two for M = 128 (what fits in 227 KB at nvec = 64)
-__host__ __device__ constexpr int tcp_nst(int m) { return m == 64 ? 3 : 2; }
+// one stage: the hi (and, with three passes, lo) parts of both operands for TCP_KC kappa
+__host__ __device__ inline int tcp_stage_bytes(int m, int np, int npass) {
+  return (npass == 3 ? 2 : 1) * (m + np) * TCP_KC * 4;
+}
+// shared-memory stages: two with three passes (at M = 64 that is 80 KB with the
+// totals, so two CTAs share an SM; three stages needed 115 KB and left one CTA,
+// 8 warps, per SM), three with one pass (65 KB).  Staging the operands through
+// shared memory with asynchronous copies instead of the register prefetch measured
+// slower on GB300 (one CTA per SM at eight chunks ahead, or two at three).
+__host__ __device__ constexpr int tcp_nst(int m, int npass) { return npass == 3 ? 2 : 3; }
 // dynamic shared memory: the stages, then the FP32 totals C[np][np + 1] (rows < 2 nvec <= np carry data)
-__host__ __device__ inline int tcp_smem_bytes(int m, int np) {
-  return tcp_nst(m) * tcp_stage_bytes(m, np) + np * (np + 1) * 4;
+__host__ __device__ inline int tcp_smem_bytes(int m, int np, int npass) {
+  return tcp_nst(m, npass) * tcp_stage_bytes(m, np, npass) + np * (np + 1) * 4;
 }
 
 // stride between the vectors of an operand
@@ -110,6 +117,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (ties away from zero), for the single-pass products
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 
 // Per chunk every thread owns up to TPT tasks: task t = (vector v, quad q) loads
 // the four complex numbers kappa = 4q .. 4q+3 of X_v and Y_v (two 16-byte loads
@@ -117,7 +130,8 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__flo
 // one 16-byte row of a core matrix each.  t -> v8 = t & 7, q = (t >> 3) & 7,
 // v = 8 (t >> 6) + v8: the eight threads of a quarter warp write eight rows of
 // one core matrix (no bank conflicts) and read eight 32-byte sectors.
-template <int TPT, int M, int TCP_NST = tcp_nst(M)>
+// The loads run two chunks ahead in registers.
+template <int TPT, int M, int NPASS, int TCP_NST = tcp_nst(M, NPASS)>
 __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kernel(TcSrc S,
                                                                                   cpx<float>* __restrict__ A,
                                                                                   int nvec, int leg,
@@ -130,12 +144,12 @@ __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kern
   const int a = blockIdx.x;
   const int tid = threadIdx.x;
   const int np = tcp_np(nvec);
-  const int stage_bytes = tcp_stage_bytes(M, np);
+  const int stage_bytes = tcp_stage_bytes(M, np, NPASS);
   const int a_bytes = M * TCP_KC * 4;
   // two accumulators of np columns each
   const uint32_t ncols = 2 * np <= 32 ? 32u : 2 * np <= 64 ? 64u : 2 * np <= 128 ? 128u : 256u;
   // zero both stages (the pad rows stay zero) and the totals, set up barriers and tensor memory
-  for (int i = tid; i < tcp_smem_bytes(M, np) / 16; i += TCP_THREADS)
+  for (int i = tid; i < tcp_smem_bytes(M, np, NPASS) / 16; i += TCP_THREADS)
     reinterpret_cast<float4*>(dsm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   float* C = reinterpret_cast<float*>(dsm + TCP_NST * stage_bytes);  // FP32 totals per accumulator row
   const int cst = np + 1;
@@ -256,13 +270,19 @@ __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kern
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
   };
-  // hi / lo rows of four consecutive kappa: 16 bytes at tile_off(row, 4q)
+  // hi / lo rows of four consecutive kappa: 16 bytes at tile_off(row, 4q) (one pass: the
+  // TF32-rounded values only)
   auto put = [&](unsigned char* hi, unsigned char* lo, int row, float e0, float e1, float e2, float e3) {
-    const float4 h = make_float4(tf32_hi(e0), tf32_hi(e1), tf32_hi(e2), tf32_hi(e3));
     const int o = tile_off(row, 4 * q);
-    *reinterpret_cast<float4*>(hi + o) = h;
-    *reinterpret_cast<float4*>(lo + o) = make_float4(e0 - h.x, e1 - h.y, e2 - h.z, e3 - h.w);
+    if constexpr (NPASS == 3) {
+      const float4 h = make_float4(tf32_hi(e0), tf32_hi(e1), tf32_hi(e2), tf32_hi(e3));
+      *reinterpret_cast<float4*>(hi + o) = h;
+      *reinterpret_cast<float4*>(lo + o) = make_float4(e0 - h.x, e1 - h.y, e2 - h.z, e3 - h.w);
+    } else {
+      *reinterpret_cast<float4*>(hi + o) = make_float4(tf32_rna(e0), tf32_rna(e1), tf32_rna(e2), tf32_rna(e3));
+    }
   };
+  constexpr int OPS = NPASS == 3 ? 2 : 1;  // hi (+ lo) tiles per operand
   long long flushed = 0;  // segments added into C so far
   float4 xa[TPT][2], ya[TPT][2], xb[TPT][2], yb[TPT][2], xc[TPT][2], yc[TPT][2];
   if (nchunks > 0) load(xa, ya);
@@ -282,7 +302,7 @@ __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kern
       flush(flushed);
       ++flushed;
     }
-    unsigned char* qb = st + 2 * a_bytes;
+    unsigned char* qb = st + OPS * a_bytes;
     const int qbytes = np * TCP_KC * 4;
 #pragma unroll
     for (int i = 0; i < TPT; ++i) {
@@ -301,15 +321,17 @@ __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kern
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ahi = smem0 + s * stage_bytes, alo = ahi + a_bytes;
-      const uint32_t bhi = ahi + 2 * a_bytes, blo = bhi + np * TCP_KC * 4;
+      const uint32_t bhi = ahi + OPS * a_bytes, blo = bhi + np * TCP_KC * 4;
       const uint32_t d = tmem + (uint32_t)(((ch / TCP_SEG) & 1) * np);
       const bool first = ch % TCP_SEG == 0;
 #pragma unroll
       for (int ks = 0; ks < TCP_KC / 8; ++ks) {
         const uint32_t off = ks * 256;  // two core matrices along K per MMA
         mma_tf32(d, smem_desc(ahi + off), smem_desc(bhi + off), idesc, (!first || ks > 0) ? 1 : 0);
-        mma_tf32(d, smem_desc(ahi + off), smem_desc(blo + off), idesc, 1);
-        mma_tf32(d, smem_desc(alo + off), smem_desc(bhi + off), idesc, 1);
+        if constexpr (NPASS == 3) {
+          mma_tf32(d, smem_desc(ahi + off), smem_desc(blo + off), idesc, 1);
+          mma_tf32(d, smem_desc(alo + off), smem_desc(bhi + off), idesc, 1);
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        (uint32_t)__cvta_generic_to_shared(&bars[s]))
@@ -384,31 +406,42 @@ int tc_project_splits(const TcSrc& S) {
   return sp < 1 ? 1 : (int)sp;
 }
 
-int launch_tc_project(const TcSrc& S, cpx<float>* A, int nvec, int leg, cpx<float>* part, int* err,
+int launch_tc_project(const TcSrc& S, cpx<float>* A, int nvec, int leg, cpx<float>* part, int* err, int npass,
                       cudaStream_t st) {
-  if (nvec > 64) {
-    set_error("tensor-core projection: nvec = %d above the supported 64", nvec);
+  if (nvec > 64 || (npass != 1 && npass != 3)) {
+    set_error("tensor-core projection: nvec = %d above the supported 64, or %d passes", nvec, npass);
     return HDCR_ERR_BAD_ARG;
   }
   const int m = tcp_m(nvec), np = tcp_np(nvec);
-  const int smem = tcp_smem_bytes(m, np);
+  const int smem = tcp_smem_bytes(m, np, npass);
   static int configured = -1;
   int dev = 0;
   HDCR_CUDA_TRY(cudaGetDevice(&dev));
   if (configured != dev) {
-    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tcp_smem_bytes(64, tcp_np(32))));
-    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tcp_smem_bytes(128, tcp_np(64))));
+    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<1, 64, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tcp_smem_bytes(64, tcp_np(32), 3)));
+    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<2, 128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tcp_smem_bytes(128, tcp_np(64), 3)));
+    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<1, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tcp_smem_bytes(64, tcp_np(32), 1)));
+    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<2, 128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tcp_smem_bytes(128, tcp_np(64), 1)));
     configured = dev;
   }
   const int sp = part ? tc_project_splits(S) : 1;
   const dim3 grid(S.bg.Vc, sp);
   cpx<float>* pp = sp > 1 ? part : nullptr;
-  if (nvec <= 32)
-    tc_project_kernel<1, 64><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
-  else
-    tc_project_kernel<2, 128><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
+  if (npass == 3) {
+    if (nvec <= 32)
+      tc_project_kernel<1, 64, 3><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
+    else
+      tc_project_kernel<2, 128, 3><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
+  } else {
+    if (nvec <= 32)
+      tc_project_kernel<1, 64, 1><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
+    else
+      tc_project_kernel<2, 128, 1><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
+  }
   count_launch();
   HDCR_LAUNCH_CHECK();
   if (sp > 1) {

@@ -23,9 +23,11 @@ struct TcSrc {
 // A[a][leg][j][k] = sum_kappa conj(X_j) Y_k for every block; *err is set when a
 // wait on the tensor cores ran out of time.  nvec <= 64.  With part non-null
 // (room for TC_MAX_SPLIT * Vc * nvec^2 complex) long contractions are
-// split over several CTAs per block and summed by a second kernel.
+// split over several CTAs per block and summed by a second kernel.  npass = 3
+// keeps the products at FP32 accuracy (TF32 hi/lo splits); npass = 1 takes the
+// TF32-rounded operands once (relative error of a product about 2^-11).
 int tc_project_splits(const TcSrc& S);
-int launch_tc_project(const TcSrc& S, cpx<float>* A, int nvec, int leg, cpx<float>* part, int* err,
+int launch_tc_project(const TcSrc& S, cpx<float>* A, int nvec, int leg, cpx<float>* part, int* err, int npass,
                       cudaStream_t st);
 
 }  // namespace hdcr

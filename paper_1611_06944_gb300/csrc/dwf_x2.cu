@@ -326,8 +326,11 @@ __device__ __forceinline__ void stage_sites(const Geom& g, int grp, X2Stage<T::s
 }
 
 // blockDim = T::sites * Ls/2: thread (site, p) = (tid / (Ls/2), tid % (Ls/2)).
-// A CTA loops over tiles (grid-stride) and, within a tile, over the right-hand
-// sides.  Every tile shape runs 16 warps per SM at 128 registers a thread.
+// A CTA loops over tiles (grid-stride).  With gridDim.y > 1 the right-hand side
+// is blockIdx.y, so the CTAs sweep the lattice one field after the other and the
+// neighbours a field's tiles share stay in L2; with gridDim.y == 1 a CTA loops
+// over all nrhs fields of its tile.  Every tile shape runs 16 warps per SM at 128
+// registers a thread.
 template <int LS, int EPI, typename T>
 __global__ void __launch_bounds__(T::sites * 8, 64 / T::sites) g5dwf_x2_kernel(
     Geom g, float diag, float mf, const cpx<float>* __restrict__ U, const cpx<float>* __restrict__ in,
@@ -342,8 +345,9 @@ __global__ void __launch_bounds__(T::sites * 8, 64 / T::sites) g5dwf_x2_kernel(
   for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
     stage_sites<T>(g, grp, sm);
     const int x4 = sm.x4[site];
+    const int r0 = gridDim.y > 1 ? (int)blockIdx.y : 0, r1 = gridDim.y > 1 ? (int)blockIdx.y + 1 : nrhs;
     if (x4 >= 0) {
-      for (int r = 0; r < nrhs; ++r)
+      for (int r = r0; r < r1; ++r)
         if constexpr (EPI == X2_CHEB)
           site_pair<LS, EPI>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot,
                              X2Cheb{ch.cur + r * fsize, ch.a, ch.b});
@@ -375,12 +379,14 @@ template <int EPI, typename T>
 static void x2_launch(const Geom& g, int blocks, float diag, float mf, const cpx<float>* U, const cpx<float>* in,
                       cpx<float>* out, int nrhs, RedScratch rs, double* result, X2Cheb ch, cudaStream_t st) {
   const int threads = T::sites * (g.Ls / 2);
+  // one grid row per right-hand side, except for the reducing epilogue (one row)
+  const dim3 grid(blocks, EPI == X2_DOT || nrhs > 65535 ? 1 : nrhs);
   if (g.Ls == 16) {
-    g5dwf_x2_kernel<16, EPI, T><<<blocks, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
+    g5dwf_x2_kernel<16, EPI, T><<<grid, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
   } else if (g.Ls == 8) {
-    g5dwf_x2_kernel<8, EPI, T><<<blocks, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
+    g5dwf_x2_kernel<8, EPI, T><<<grid, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
   } else if constexpr (T::linear && T::sites == 16) {  // other Ls: the default tile only
-    g5dwf_x2_kernel<0, EPI, T><<<blocks, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
+    g5dwf_x2_kernel<0, EPI, T><<<grid, threads, 0, st>>>(g, diag, mf, U, in, out, nrhs, rs, result, ch);
   } else {
     return;
   }

@@ -3,11 +3,14 @@
     python -m paper_1611_06944_gb300.probe stencil L dtype [reps]
     python -m paper_1611_06944_gb300.probe coarse L nvec dtype [reps]
 
-``stencil`` applies H = Gamma5 D_dwf ``reps`` times (default 4) on an L^4 x 16
-lattice with random links and field (dtype f32 or f64); ``coarse`` builds the
-little Dirac operator ``reps`` times (default 3) from nvec random basis vectors
-on 4^4 blocks of that lattice and reports its time in units of one fine
-application of H of the same precision.  For ncu captures of single kernels.
+``L`` is one extent (an L^4 lattice) or four comma-separated extents
+(e.g. 24,24,24,48); Ls = 16.  ``stencil`` applies H = Gamma5 D_dwf ``reps``
+times (default 4) with random links and field (dtype f32 or f64); ``coarse``
+builds the little Dirac operator ``reps`` times (default 3; dtype f64, f32, or
+f32fast for single-pass TF32 projections) from nvec random basis vectors on 4^4
+blocks of that lattice and reports its time in units of
+one fine application of H of the same precision.  For ncu captures of single
+kernels.
 """
 from __future__ import annotations
 
@@ -18,9 +21,14 @@ import torch
 import paper_1611_06944_gb300 as hd
 
 
-def stencil(n: int, dtype: str, reps: int = 4) -> None:
+def _extents(spec: str) -> tuple:
+    parts = [int(v) for v in spec.split(",")]
+    return tuple(parts) if len(parts) == 4 else (parts[0],) * 4
+
+
+def stencil(L: tuple, dtype: str, reps: int = 4) -> None:
     dt = torch.complex64 if dtype == "f32" else torch.complex128
-    lat = hd.Lattice((n, n, n, n), 16)
+    lat = hd.Lattice(L, 16)
     g = torch.Generator(device="cuda").manual_seed(0)
     U = torch.randn(4, lat.V4, 3, 3, dtype=dt, device="cuda", generator=g)
     x = torch.randn(lat.V4, 12, 16, dtype=dt, device="cuda", generator=g)
@@ -38,23 +46,25 @@ def stencil(n: int, dtype: str, reps: int = 4) -> None:
     us = t["ms"] / max(t["launches"], 1) * 1e3
     real = 4 if dtype == "f32" else 8
     per_site = 2 * 24 * real + 4 * 18 * real / 16   # psi in + out, links shared by the 16 s-sites
-    print(f"ok {dtype} L={n} Ls=16: {us:.2f} us per launch, {lat.V4 * 16 * per_site / (us * 1e-6) / 1e9:.1f} GB/s")
+    print(f"ok {dtype} L={L} Ls=16: {us:.2f} us per launch, {lat.V4 * 16 * per_site / (us * 1e-6) / 1e9:.1f} GB/s")
 
 
-def coarse(n: int, nvec: int, dtype: str, reps: int = 3) -> None:
-    dt = torch.complex64 if dtype == "f32" else torch.complex128
-    lat = hd.Lattice((n, n, n, n), 16)
+def coarse(L: tuple, nvec: int, dtype: str, reps: int = 3) -> None:
+    fast = dtype == "f32fast"  # single-pass TF32 projections
+    dt = torch.complex64 if dtype in ("f32", "f32fast") else torch.complex128
+    lat = hd.Lattice(L, 16)
     g = torch.Generator(device="cuda").manual_seed(0)
     U = torch.randn(4, lat.V4, 3, 3, dtype=torch.complex128, device="cuda", generator=g)
     v = torch.randn(nvec, lat.V4, 12, 16, dtype=torch.complex128, device="cuda", generator=g)
     sub = hd.subspace_from_vectors(lat, (4, 4, 4, 4), v, store_dtype=dt)
     del v
-    hd.build_coarse_op(sub, U, 1.8, 0.01, op_dtype=dt).close()
+    torch.cuda.empty_cache()
+    hd.build_coarse_op(sub, U, 1.8, 0.01, op_dtype=dt, fast=fast).close()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        hd.build_coarse_op(sub, U, 1.8, 0.01, op_dtype=dt).close()
+        hd.build_coarse_op(sub, U, 1.8, 0.01, op_dtype=dt, fast=fast).close()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
@@ -71,16 +81,16 @@ def coarse(n: int, nvec: int, dtype: str, reps: int = 3) -> None:
     torch.cuda.synchronize()
     mv = e0.elapsed_time(e1) / 10
     sub.close()
-    print(f"ok coarse {dtype} L={n} Ls=16 nvec={nvec}: build {ms:.2f} ms = {ms / mv:.1f} fine matvecs ({mv:.3f} ms)")
+    print(f"ok coarse {dtype} L={L} Ls=16 nvec={nvec}: build {ms:.2f} ms = {ms / mv:.1f} fine matvecs ({mv:.3f} ms)")
 
 
 def main(argv=None) -> int:
     a = sys.argv[1:] if argv is None else argv
     if len(a) >= 3 and a[0] == "stencil":
-        stencil(int(a[1]), a[2], int(a[3]) if len(a) > 3 else 4)
+        stencil(_extents(a[1]), a[2], int(a[3]) if len(a) > 3 else 4)
         return 0
     if len(a) >= 4 and a[0] == "coarse":
-        coarse(int(a[1]), int(a[2]), a[3], int(a[4]) if len(a) > 4 else 3)
+        coarse(_extents(a[1]), int(a[2]), a[3], int(a[4]) if len(a) > 4 else 3)
         return 0
     print(__doc__)
     return 2

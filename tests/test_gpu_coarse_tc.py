@@ -53,3 +53,49 @@ def test_fp32_coarse_op_matches_fp64_build(hd, L, Ls, block, nvec, bc):
     # leg by leg, so that a wrong leg cannot hide behind the large diagonal one
     for leg in range(9):
         assert relerr(A32[:, leg], A64[:, leg]) < 1e-4
+
+
+@pytest.mark.parametrize("L,Ls,block,nvec,bc", [CASES[0], CASES[2], CASES[3]])
+def test_single_pass_tf32_coarse_op(hd, L, Ls, block, nvec, bc):
+    """fast=True: one pass of TF32 products.  Each operand is rounded to TF32
+    (11 significant bits, relative error <= 2^-11), so a product is good to about
+    2^-10 ~ 1e-3 and, the rounding errors being as random in sign as the terms
+    themselves, an entry to about 1e-3 of its size: 4e-3 overall, 1e-2 per leg.
+    It must also differ from the three-pass build (the mode took effect)."""
+    U = synth.gauge_field(L, 0.5, 5300)
+    rng = synth.rng(5301)
+    lat = hd.Lattice(L, Ls, bc)
+    shape = (nvec, lat.V4, 12, Ls)
+    v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    Ud = dev(links(U))
+    sub64 = hd.subspace_from_vectors(lat, block, dev(v), store_dtype=torch.complex128)
+    sub32 = hd.subspace_from_vectors(lat, block, dev(v), store_dtype=torch.complex64)
+    A64 = host(hd.build_coarse_op(sub64, Ud, 1.8, 0.01).op())
+    A3 = host(hd.build_coarse_op(sub32, Ud, 1.8, 0.01, op_dtype=torch.complex64).op())
+    A1 = host(hd.build_coarse_op(sub32, Ud, 1.8, 0.01, op_dtype=torch.complex64, fast=True).op())
+    e1 = relerr(A1, A64)
+    assert e1 < 4e-3
+    assert e1 > 10 * relerr(A3, A64)
+    for leg in range(9):
+        assert relerr(A1[:, leg], A64[:, leg]) < 1e-2
+
+
+def test_hdcr_solve_with_single_pass_coarse_op(hd):
+    """The mixed-precision solve recovers full accuracy with the single-pass build:
+    true residual <= 1e-10, recomputed by the oracle."""
+    from oracle import dwf
+    from gpu_util import natural, planes
+    L, Ls, block, nvec, mf = (4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.01
+    lat = hd.Lattice(L, Ls)
+    Uh = synth.gauge_field(L, 0.3, 1000)
+    U = dev(links(Uh))
+    noise = dev(planes(synth.gaussian_fermion(L, Ls, 3001, count=nvec // 2)))
+    sub = hd.build_subspace(lat, U, noise, 1.8, mf, block, kind="chebyshev", order=100, lam_cut=0.3,
+                            store_dtype=torch.complex64)
+    co = hd.build_coarse_op(sub, U, 1.8, mf, op_dtype=torch.complex64, fast=True)
+    b = synth.gaussian_fermion(L, Ls, 2000)
+    x, st = hd.hdcr_solve(co, U, dev(planes(b)), tol=1e-10, inner_dtype=torch.complex64, max_outer=2000,
+                          restart=16)
+    xg = natural(host(x), L, Ls)
+    res = np.sqrt(dwf.norm2(b - dwf.apply_H(Uh, xg, 1.8, mf)) / dwf.norm2(b))
+    assert st["status"] == 0 and res <= 1.01e-10
