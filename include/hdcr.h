@@ -63,6 +63,15 @@ extern "C" {
 /* hdcr_build_coarse_op only: complex float storage, projections with one pass of
  * TF32 tensor-core products (FP32 accumulation), relative error about 1e-3 */
 #define HDCR_C64_FAST 2
+/* FP16 storage of a fermion field (the precision form's half-precision
+ * storage; arithmetic stays FP32): 12*V5 half2 (FP16 re, im) in the field
+ * layout below, followed by V5 FP32 scales, one per 5d site (x4, s) at index
+ * x4*Ls + s; a component is its half2 times its site's scale, chosen by the
+ * encoder as the largest |re|, |im| of the site's 24 reals (so halves lie in
+ * [-1, 1], rounded to 2^-11 of that value).  52*V5 bytes a field; nfields
+ * fields follow one another.  Used by hdcr_apply_g5dwf (with C64 links) and the
+ * two conversions below. */
+#define HDCR_H16 3
 
 typedef struct {
   int L[4]; /* Lx, Ly, Lz, Lt (4d extents, each >= 1)                     */
@@ -98,7 +107,7 @@ unsigned long long hdcr_launch_count(void);
 /* Stencil timer: hdcr_stencil_timer(1) resets and starts recording CUDA
  * events around every application of H (on the launching stream, at most
  * 16384 launches); hdcr_stencil_timer(0) stops.  hdcr_stencil_timer_read adds
- * up the recorded launches of one precision (HDCR_C128 or HDCR_C64): total
+ * up the recorded launches of one precision (HDCR_C128, HDCR_C64 or HDCR_H16): total
  * device milliseconds, number of launches and 5d sites processed.  It waits
  * for the recorded events. */
 int hdcr_stencil_timer(int enable);
@@ -114,7 +123,9 @@ int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites);
  *        - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu,s) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu,s)]
  *        - P_- psi(x,s+1) - P_+ psi(x,s-1),
  * walls psi(x,Ls) = -mf psi(x,0), psi(x,-1) = -mf psi(x,Ls-1), P_pm = (1 pm gamma5)/2,
- * R5 psi(s) = psi(Ls-1-s).  U and the nrhs fields in/out share ``dtype``.
+ * R5 psi(s) = psi(Ls-1-s).  U and the nrhs fields in/out share ``dtype``, except
+ * for HDCR_H16: fields in FP16 storage (even Ls <= 16, 16-byte aligned), U C64,
+ * arithmetic FP32, each output site re-encoded with its own scale.
  * ``in`` and ``out`` must not overlap.  Errors: BAD_ARG, BAD_GEOMETRY, CUDA.
  */
 int hdcr_apply_g5dwf(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
@@ -136,6 +147,13 @@ int hdcr_apply_g5dwf(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U
  * (-1 where a variant does not fit).  Errors: BAD_ARG. */
 int hdcr_stencil_tune(int mode, int force_variant);
 int hdcr_stencil_tune_info(const hdcr_geom* g, int nrhs, int* variant, float* us, int nus);
+
+/* FP16-storage conversions (HDCR_H16 above) of nfields fields between C128 or C64
+ * (``dtype``) and the FP16 form; buffers 16-byte aligned, distinct.  Errors: BAD_ARG. */
+int hdcr_fermion_encode_h16(const hdcr_geom* g, const void* in, int in_dtype, void* out, int nfields,
+                            void* stream);
+int hdcr_fermion_decode_h16(const hdcr_geom* g, const void* in, void* out, int out_dtype, int nfields,
+                            void* stream);
 
 /* out = Gamma5 in = gamma5 R5 in (Section 3), nfields fields; in == out not allowed. */
 int hdcr_apply_gamma5_r5(const hdcr_geom* g, const void* in, void* out, int dtype,

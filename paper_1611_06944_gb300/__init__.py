@@ -85,7 +85,8 @@ def load_library():
 
 __all__ = [
     "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
-    "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info", "cr_solve", "cr_solve_into", "library_path",
+    "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info",
+    "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
     "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "gauge_force", "HDCRSolve", "solve_autograd",
@@ -176,6 +177,51 @@ def apply_g5dwf(lat: Lattice, U: torch.Tensor, psi: torch.Tensor, M5: float, mf:
     p = _params(M5, mf)
     _check(_L.hdcr_apply_g5dwf(C_ref(g), C_ref(p), _dev(U, "U"), _dev(psi, "psi"), _dev(out, "out"),
                                _code(psi), n, _stream(stream)), "apply_g5dwf")
+    return out
+
+
+def h16_bytes(lat: Lattice) -> int:
+    """Bytes of one fermion field in FP16 storage: 12 V5 half2 and V5 FP32 site scales."""
+    return 52 * lat.V5
+
+
+def encode_h16(lat: Lattice, psi: torch.Tensor, stream=None) -> torch.Tensor:
+    """FP16 storage (half2 per complex number, one FP32 scale per 5d site) of the
+    complex128 / complex64 fields psi: a uint8 tensor (nfields, 52 V5)."""
+    n = _nfields(lat, psi, "psi")
+    out = torch.empty((n, h16_bytes(lat)), dtype=torch.uint8, device=psi.device)
+    g = lat.c_geom()
+    _check(_L.hdcr_fermion_encode_h16(C_ref(g), _dev(psi, "psi"), _code(psi), _dev(out, "out"), n,
+                                      _stream(stream)), "encode_h16")
+    return out
+
+
+def decode_h16(lat: Lattice, buf: torch.Tensor, dtype: torch.dtype = torch.complex64, stream=None) -> torch.Tensor:
+    """The fields of an FP16-storage buffer as complex numbers in the library layout."""
+    per = h16_bytes(lat)
+    if buf.dtype != torch.uint8 or buf.numel() % per:
+        raise ValueError(f"an FP16-storage buffer is uint8 with a multiple of {per} bytes")
+    n = buf.numel() // per
+    out = torch.empty((n, lat.V4, 12, lat.Ls), dtype=dtype, device=buf.device)
+    g = lat.c_geom()
+    _check(_L.hdcr_fermion_decode_h16(C_ref(g), _dev(buf, "buf"), _dev(out, "out"), _code(out), n,
+                                      _stream(stream)), "decode_h16")
+    return out if n > 1 else out[0]
+
+
+def apply_g5dwf_h16(lat: Lattice, U: torch.Tensor, buf: torch.Tensor, M5: float, mf: float,
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """H = Gamma5 D_dwf on fields in FP16 storage (FP32 arithmetic, complex64 links)."""
+    if U.dtype != torch.complex64:
+        raise TypeError("apply_g5dwf_h16 takes complex64 links")
+    per = h16_bytes(lat)
+    if buf.dtype != torch.uint8 or buf.numel() % per:
+        raise ValueError(f"an FP16-storage buffer is uint8 with a multiple of {per} bytes")
+    out = torch.empty_like(buf) if out is None else out
+    g = lat.c_geom()
+    p = _params(M5, mf)
+    _check(_L.hdcr_apply_g5dwf(C_ref(g), C_ref(p), _dev(U, "U"), _dev(buf, "buf"), _dev(out, "out"),
+                               _lib.HDCR_H16, buf.numel() // per, _stream(stream)), "apply_g5dwf_h16")
     return out
 
 
@@ -330,7 +376,9 @@ def _block_arr(block):
     return arr
 
 
-def _dt(d: torch.dtype) -> int:
+def _dt(d) -> int:
+    if isinstance(d, str) and d == "h16":
+        return _lib.HDCR_H16
     return _lib.HDCR_C128 if d == torch.complex128 else _lib.HDCR_C64
 
 

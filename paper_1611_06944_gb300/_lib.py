@@ -17,6 +17,7 @@ HDCR_OK = 0
 HDCR_C128 = 0
 HDCR_C64 = 1
 HDCR_C64_FAST = 2
+HDCR_H16 = 3
 
 STATUS_NAMES = {
     0: "OK", -1: "BAD_ARG", -2: "BAD_GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE",
@@ -88,6 +89,8 @@ SIGNATURES = {
     "hdcr_stencil_timer_count": (_I, [_I, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "hdcr_apply_g5dwf": (_I, [_G, _DP, _P, _P, _P, _I, _I, _P]),
     "hdcr_stencil_tune": (_I, [_I, _I]),
+    "hdcr_fermion_encode_h16": (_I, [_G, _P, _I, _P, _I, _P]),
+    "hdcr_fermion_decode_h16": (_I, [_G, _P, _P, _I, _I, _P]),
     "hdcr_stencil_tune_info": (_I, [_G, _I, C.POINTER(C.c_int), C.POINTER(C.c_float), _I]),
     "hdcr_apply_gamma5_r5": (_I, [_G, _P, _P, _I, _I, _P]),
     "hdcr_fermion_pack": (_I, [_G, _P, _P, _I, _I, _P]),

@@ -20,6 +20,9 @@ int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, co
 // prev <- 2 (a H in + b cur) - prev for nrhs fields (a Chebyshev step fused into the FP32 stencil)
 int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in,
                          const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st);
+// FP32 operator on FP16-stored fields (dwf_h16.cu): nrhs fields of 52 V5 bytes each
+int launch_g5dwf_h16(const Geom& g, double M5, double mf, const cpx<float>* U, const void* in, void* out, int nrhs,
+                     cudaStream_t st);
 // tile-shape autotuner of the FP32 operator: mode 1 tunes on first use, 0 keeps the
 // default tile, 2 forgets what was tuned; force_variant >= 0 pins one variant
 int x2_tune_mode(int mode, int force_variant);

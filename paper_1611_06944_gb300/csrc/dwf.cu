@@ -95,11 +95,11 @@ struct StencilTimer {
   std::mutex mu;
   bool enabled = false;
   std::vector<cudaEvent_t> ev;  // 2 per launch
-  std::vector<int> kind;        // 0 = FP64, 1 = FP32
+  std::vector<int> kind;        // 0 = FP64, 1 = FP32, 2 = FP16 storage
   std::vector<long long> sites;
   int used = 0;
-  long long all_launches[2] = {0, 0};  // every launch while enabled, timed or not
-  long long all_sites[2] = {0, 0};
+  long long all_launches[3] = {0, 0, 0};  // every launch while enabled, timed or not
+  long long all_sites[3] = {0, 0, 0};
 };
 StencilTimer g_timer;
 }  // namespace
@@ -210,6 +210,17 @@ extern "C" int hdcr_apply_g5dwf(const hdcr_geom* gp, const hdcr_dwf_params* p, c
     set_error("hdcr_apply_g5dwf: in and out must not overlap");
     return HDCR_ERR_BAD_ARG;
   }
+  if (dtype == HDCR_H16) {
+    if (g.Ls % 2 || g.Ls > 16 || ((((uintptr_t)in) | ((uintptr_t)out)) & 15) || nrhs > 65535) {
+      set_error("hdcr_apply_g5dwf: FP16 storage needs an even Ls <= 16, 16-byte aligned fields, nrhs <= 65535");
+      return HDCR_ERR_BAD_ARG;
+    }
+    int slot;
+    stencil_timer_begin(2, g.V5 * nrhs, as_stream(stream), &slot);
+    const int s = launch_g5dwf_h16(g, p->M5, p->mf, (const cpx<float>*)U, in, out, nrhs, as_stream(stream));
+    stencil_timer_end(slot, as_stream(stream));
+    return s;
+  }
   if (dtype == HDCR_C128) return launch_g5dwf<double>(g, p->M5, p->mf, U, in, out, nrhs, as_stream(stream));
   if (dtype == HDCR_C64) return launch_g5dwf<float>(g, p->M5, p->mf, U, in, out, nrhs, as_stream(stream));
   set_error("hdcr_apply_g5dwf: unknown dtype %d", dtype);
@@ -308,31 +319,30 @@ extern "C" int hdcr_stencil_timer(int enable) {
   g_timer.enabled = enable != 0;
   if (g_timer.enabled) {
     g_timer.used = 0;
-    g_timer.all_launches[0] = g_timer.all_launches[1] = 0;
-    g_timer.all_sites[0] = g_timer.all_sites[1] = 0;
+    for (int k = 0; k < 3; ++k) g_timer.all_launches[k] = g_timer.all_sites[k] = 0;
   }
   return HDCR_OK;
 }
 
 extern "C" int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites) {
-  if (!launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64)) {
+  if (!launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64 && dtype != HDCR_H16)) {
     set_error("hdcr_stencil_timer_count: bad arguments");
     return HDCR_ERR_BAD_ARG;
   }
   std::lock_guard<std::mutex> lock(g_timer.mu);
-  const int k = dtype == HDCR_C128 ? 0 : 1;
+  const int k = dtype == HDCR_C128 ? 0 : dtype == HDCR_C64 ? 1 : 2;
   *launches = g_timer.all_launches[k];
   *sites = g_timer.all_sites[k];
   return HDCR_OK;
 }
 
 extern "C" int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* launches, long long* sites) {
-  if (!total_ms || !launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64)) {
+  if (!total_ms || !launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64 && dtype != HDCR_H16)) {
     set_error("hdcr_stencil_timer_read: bad arguments");
     return HDCR_ERR_BAD_ARG;
   }
   std::lock_guard<std::mutex> lock(g_timer.mu);
-  const int want = dtype == HDCR_C128 ? 0 : 1;
+  const int want = dtype == HDCR_C128 ? 0 : dtype == HDCR_C64 ? 1 : 2;
   double ms = 0.0;
   long long nl = 0, ns = 0;
   for (int i = 0; i < g_timer.used; ++i) {

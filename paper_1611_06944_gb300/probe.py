@@ -5,7 +5,8 @@
 
 ``L`` is one extent (an L^4 lattice) or four comma-separated extents
 (e.g. 24,24,24,48); Ls = 16.  ``stencil`` applies H = Gamma5 D_dwf ``reps``
-times (default 4) with random links and field (dtype f32 or f64); ``coarse``
+times (default 4) with random links and field (dtype f32, f64, or h16 for
+FP16-stored fields); ``coarse``
 builds the little Dirac operator ``reps`` times (default 3; dtype f64, f32, or
 f32fast for single-pass TF32 projections) from nvec random basis vectors on 4^4
 blocks of that lattice and reports its time in units of
@@ -27,25 +28,32 @@ def _extents(spec: str) -> tuple:
 
 
 def stencil(L: tuple, dtype: str, reps: int = 4) -> None:
-    dt = torch.complex64 if dtype == "f32" else torch.complex128
+    h16 = dtype == "h16"  # FP16 storage, FP32 arithmetic and links
+    dt = torch.complex64 if dtype in ("f32", "h16") else torch.complex128
     lat = hd.Lattice(L, 16)
     g = torch.Generator(device="cuda").manual_seed(0)
     U = torch.randn(4, lat.V4, 3, 3, dtype=dt, device="cuda", generator=g)
     x = torch.randn(lat.V4, 12, 16, dtype=dt, device="cuda", generator=g)
+    if h16:
+        x = hd.encode_h16(lat, x)
     y = torch.empty_like(x)
+    apply = (lambda: hd.apply_g5dwf_h16(lat, U, x, 1.8, 0.01, out=y)) if h16 else \
+        (lambda: hd.apply_g5dwf(lat, U, x, 1.8, 0.01, out=y))
     for _ in range(reps):
-        hd.apply_g5dwf(lat, U, x, 1.8, 0.01, out=y)
+        apply()
     torch.cuda.synchronize()
     # event-timed launches (the inputs exceed L2 at n = 16, so every launch reads from HBM)
     hd.stencil_timer(True)
     for _ in range(reps):
-        hd.apply_g5dwf(lat, U, x, 1.8, 0.01, out=y)
+        apply()
     torch.cuda.synchronize()
-    t = hd.stencil_timer_read(dt)
+    t = hd.stencil_timer_read("h16" if h16 else dt)
     hd.stencil_timer(False)
     us = t["ms"] / max(t["launches"], 1) * 1e3
     real = 4 if dtype == "f32" else 8
     per_site = 2 * 24 * real + 4 * 18 * real / 16   # psi in + out, links shared by the 16 s-sites
+    if h16:
+        per_site = 2 * 52 + 4 * 18 * 4 / 16         # half2 spinor + FP32 scale, in and out; FP32 links
     print(f"ok {dtype} L={L} Ls=16: {us:.2f} us per launch, {lat.V4 * 16 * per_site / (us * 1e-6) / 1e9:.1f} GB/s")
 
 
