@@ -19,8 +19,17 @@ through host buffers, SM clocks during the timed region and the number of
 library kernels launched.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload two-level|precision|batching]
 Under torchrun each rank runs an independent replica (the solve does not
 shard across GPUs here); rank 0 prints one JSON line.
+
+The default workload is the one above.  Two more print their own line:
+``precision`` (24^3 x 48 x 16, eps = 0.5, mf = 0.005: FP32 stencil and its
+FP16-storage variant, the coarse operator with nvec = 32 on the tensor cores,
+the mixed-precision solve with an FP64 outer iteration to 1e-10) and
+``batching`` (16^3 x 32 x 16, the 12 spin-colour point sources solved at once
+with the graph-captured V-cycle, against 12 single solves; the coarse operator
+with nvec = 48).
 """
 from __future__ import annotations
 
@@ -57,14 +66,14 @@ FLOPS_PER_SITE = 8 * (12 + 144 + 48) + 72
 def bytes_per_site(real_bytes: int, Ls: int) -> float:
     return 2 * 12 * 2 * real_bytes + 4 * 9 * 2 * real_bytes / Ls
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal, profiling recipe)
-# DRAM traffic of one FP64 / FP32 stencil launch at 16^4 x 16 from ncu, with the hash of
+# DRAM traffic of one FP64 / FP32 / FP16-storage stencil launch at 16^4 x 16 from ncu, with the hash of
 # the stencil sources it was measured on (reported as null once the sources change)
-NCU_TRAFFIC = {"f64": 452.55e6, "f32": 205.69e6, "src_hash": "a63f417e2e28ba4e"}
+NCU_TRAFFIC = {"f64": 451.63e6, "f32": 203.95e6, "h16": 106.12e6, "src_hash": "93e5f49c49aabef4"}
 
 
 def stencil_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("dwf_stencil.cuh", "dwf.cu", "dwf_x2.cu", "hdcr_internal.cuh"):
+    for f in ("dwf_stencil.cuh", "dwf.cu", "dwf_x2.cu", "dwf_x2.cuh", "dwf_h16.cu", "hdcr_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1611_06944_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -298,6 +307,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     s32 = hd.stencil_timer_read(torch.complex64)
     hd.stencil_timer(False)
+    h16 = _stencil_rate(hd, lat, U32, hd.encode_h16(lat, b), h16=True)
+    h16["traffic"] = NCU_TRAFFIC["h16"] if NCU_TRAFFIC["src_hash"] == stencil_src_hash() else None
     pk = peaks()
     bps32 = bytes_per_site(4, LS)
     gbs32 = s32["sites"] * bps32 / (s32["ms"] * 1e-3) / 1e9
@@ -354,6 +365,7 @@ def run_ours(args, world, rank, local):
                        "hbm_peak_gbs": pk["hbm_gbs"], "peak_source": pk["source"],
                        "bytes_per_site": bps32, "avg_launch_us": round(s32["ms"] / s32["launches"] * 1e3, 2),
                        "traffic": NCU_TRAFFIC["f32"] if same_src else None},
+        "g5dwf_fp16_storage": h16,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -450,19 +462,225 @@ def run_reference(args, world, rank):
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ further workloads
+def _sync_time(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def _stencil_rate(hd, lat, U32, x, h16=False, reps=20) -> dict:
+    """Event-timed FP32 (or FP16-storage) applications of H: us per launch and GB/s of
+    algorithmic bytes (spinor in + out, links once per 4d site)."""
+    import torch
+    y = torch.empty_like(x)
+    nf = (x.numel() // (52 * lat.V5)) if h16 else hd._nfields(lat, x, "x")
+    apply = (lambda: hd.apply_g5dwf_h16(lat, U32, x, M5, MF, out=y)) if h16 else \
+        (lambda: hd.apply_g5dwf(lat, U32, x, M5, MF, out=y))
+    for _ in range(3):
+        apply()
+    torch.cuda.synchronize()
+    hd.stencil_timer(True)
+    for _ in range(reps):
+        apply()
+    torch.cuda.synchronize()
+    t = hd.stencil_timer_read("h16" if h16 else torch.complex64)
+    hd.stencil_timer(False)
+    us = t["ms"] / t["launches"] * 1e3
+    per_site = (2 * 52 if h16 else 2 * 96) + 4 * 72 / lat.Ls / nf
+    gbs = lat.V5 * nf * per_site / (us * 1e-6) / 1e9
+    pk = peaks()["hbm_gbs"]
+    return {"us": round(us, 2), "GBs": round(gbs, 1), "frac_of_hbm": round(gbs / pk, 4), "bytes_per_site": per_site,
+            "fields": nf}
+
+
+def _coarse_rebuild(hd, sub, U, mf, fast: bool, mv_ms: float, reps=3) -> dict:
+    import torch
+    hd.build_coarse_op(sub, U, M5, mf, op_dtype=torch.complex64, fast=fast).close()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        hd.build_coarse_op(sub, U, M5, mf, op_dtype=torch.complex64, fast=fast).close()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"ms": round(ms, 2), "fine_matvecs": round(ms / mv_ms, 1),
+            "projection": "single-pass TF32" if fast else "three-pass TF32 (FP32-exact)"}
+
+
+def run_precision(args, world, rank, local):
+    """24^3 x 48 x 16, eps = 0.5, mf = 0.005: the mixed-precision form."""
+    import torch
+
+    import paper_1611_06944_gb300 as hd
+    import synth
+    torch.cuda.set_device(local)
+    L, Ls, eps, mf, nvec = (24, 24, 24, 48), 16, 0.5, 0.005, 32
+    lat = hd.Lattice(L, Ls, 1)
+    Uh = synth.gauge_field(L, eps, 1002)
+    plaq = synth.plaquette(Uh)
+    U = torch.from_numpy(Uh.reshape(4, -1, 3, 3).copy()).cuda()
+    del Uh
+    U32 = U.to(torch.complex64)
+    b = synth.device_gaussian(1, lat.V5, 2002)[0].reshape(lat.V4, 12, Ls).contiguous()
+    noise = synth.device_gaussian(nvec // 2, lat.V5, 3002).reshape(nvec // 2, lat.V4, 12, Ls).contiguous()
+    x32 = b.to(torch.complex64)
+    f32 = _stencil_rate(hd, lat, U32, x32)
+    h16 = _stencil_rate(hd, lat, U32, hd.encode_h16(lat, b), h16=True)
+    # order 600 with the cut at 0.1 (orders 300 and cuts 0.3 left the solve stalled near 1e-4
+    # on this lattice; the paper's own filter is O(500-900))
+    filt = dict(kind="chebyshev", order=600, lam_cut=0.1, lam_max=8.0, filter_dtype=torch.complex64,
+                store_dtype=torch.complex64)
+    # 6^4 blocks (coarse 4^3 x 8, 16384 unknowns): the dense coarse inverse applies; with
+    # 4^4 blocks (82944 unknowns) only the coarse CR does, and it stalls the solve here
+    block = (6, 6, 6, 6)
+    solve = dict(tol=1e-10, restart=8, smoother="chebyshev", smoother_order=10, cheb_lo=1.0, cheb_hi=64.0,
+                 coarse_solver="dense", max_outer=300, inner_dtype=torch.complex64)
+    phases = {}
+
+    def step():
+        sub, t_sub = _sync_time(lambda: hd.build_subspace(lat, U, noise, M5, mf, block, **filt))
+        co, t_co = _sync_time(lambda: hd.build_coarse_op(sub, U, M5, mf, op_dtype=torch.complex64, fast=True))
+        _, t_inv = _sync_time(lambda: hd.coarse_invert(co))
+        (x, st), t_solve = _sync_time(lambda: hd.hdcr_solve(co, U, b, **solve))
+        phases.update(subspace_s=round(t_sub, 3), coarse_op_s=round(t_co, 4), coarse_invert_s=round(t_inv, 3),
+                      solve_s=round(t_solve, 3))
+        co.close()
+        return sub, x, st
+
+    for _ in range(args.warmup):
+        sub, x, st = step()
+        sub.close()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sub, x, st = step()
+        if _ + 1 < args.steps:
+            sub.close()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3 / args.steps
+    rebuild = {"6^4 blocks": {"fast": _coarse_rebuild(hd, sub, U, mf, True, f32["us"] * 1e-3),
+                              "exact": _coarse_rebuild(hd, sub, U, mf, False, f32["us"] * 1e-3)}}
+    sub.close()
+    # the 4^4 blocks of the paper's other workloads (6^3 x 12 coarse lattice)
+    sub4 = hd.build_subspace(lat, U, noise, M5, mf, BLOCK, kind="chebyshev", order=20, lam_cut=0.2, lam_max=8.0,
+                             filter_dtype=torch.complex64, store_dtype=torch.complex64)
+    rebuild["4^4 blocks"] = {"fast": _coarse_rebuild(hd, sub4, U, mf, True, f32["us"] * 1e-3),
+                             "exact": _coarse_rebuild(hd, sub4, U, mf, False, f32["us"] * 1e-3)}
+    sub4.close()
+    return {
+        "metric": METRIC, "workload_kind": "precision", "value": round(elapsed, 3), "unit": "s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "dtype": "f32 inner / f64 outer", "data": "synthetic (links on the host, noise and source drawn on the device)",
+        "config": {"workload": "precision form: 24^3x48 x 16 DWF, eps=0.5, M5=1.8, mf=0.005, 1 Gaussian source, "
+                               "nvec=32, 6^4 blocks (4^3x8 coarse)", "plaquette": round(plaq, 4),
+                   "step": "Chebyshev-filter subspace (order 600, FP32) + coarse op (TF32 tensor cores, one pass) + "
+                           "dense coarse inverse + FP64 flexible GCR with FP32 V-cycle (Chebyshev smoother) to 1e-10"},
+        "phases": phases,
+        "hdcr": {"outer_iters": st["iters"], "true_resid": st["true_resid"], "fine_matvecs_f64": st["fine_matvecs"],
+                 "fine_matvecs_f32": st["fine_matvecs_lo"], "coarse_matvecs": st["coarse_matvecs"]},
+        "g5dwf_fp32": f32, "g5dwf_fp16_storage": h16, "coarse_rebuild_nvec32": rebuild, "clocks": clk,
+    }
+
+
+def run_batching(args, world, rank, local):
+    """16^3 x 32 x 16, the 12 spin-colour point sources at once."""
+    import torch
+
+    import paper_1611_06944_gb300 as hd
+    import synth
+    torch.cuda.set_device(local)
+    L, Ls, eps, mf, nvec = (16, 16, 16, 32), 16, 0.5, 0.01, 48
+    lat = hd.Lattice(L, Ls, 1)
+    Uh = synth.gauge_field(L, eps, 1003)
+    plaq = synth.plaquette(Uh)
+    U = torch.from_numpy(Uh.reshape(4, -1, 3, 3).copy()).cuda()
+    U32 = U.to(torch.complex64)
+    # the 12 point sources at x = 0, s = 0 (component 3 spin + colour), in the library layout
+    B = torch.zeros(12, lat.V4, 12, Ls, dtype=torch.complex128, device="cuda")
+    for i in range(12):
+        B[i, 0, i, 0] = 1.0
+    noise = synth.device_gaussian(nvec // 2, lat.V5, 3003).reshape(nvec // 2, lat.V4, 12, Ls).contiguous()
+    f32_1 = _stencil_rate(hd, lat, U32, noise[0].to(torch.complex64).contiguous())
+    f32_12 = _stencil_rate(hd, lat, U32, noise[:12].to(torch.complex64).contiguous())
+    sub, t_sub = _sync_time(lambda: hd.build_subspace(lat, U, noise, M5, mf, BLOCK, kind="chebyshev", order=300,
+                                                      lam_cut=0.3, lam_max=8.0, filter_dtype=torch.complex64,
+                                                      store_dtype=torch.complex64))
+    rebuild = {"fast": _coarse_rebuild(hd, sub, U, mf, True, f32_1["us"] * 1e-3),
+               "exact": _coarse_rebuild(hd, sub, U, mf, False, f32_1["us"] * 1e-3)}
+    co, t_co = _sync_time(lambda: hd.build_coarse_op(sub, U, M5, mf, op_dtype=torch.complex64, fast=True))
+    _, t_inv = _sync_time(lambda: hd.coarse_invert(co))
+    kw = dict(tol=1e-10, restart=8, max_outer=300, inner_dtype=torch.complex64)
+    for _ in range(args.warmup):
+        hd.hdcr_solve_multi(co, U, B, graph=True, **kw)
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = hd.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        X, stats = hd.hdcr_solve_multi(co, U, B, graph=True, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = (hd.launch_count() - n0) / args.steps
+    t_multi = e0.elapsed_time(e1) / 1e3 / args.steps
+    _, t_eager = _sync_time(lambda: hd.hdcr_solve_multi(co, U, B, graph=False, **kw))
+
+    def singles():
+        its = []
+        for i in range(12):
+            _, s1 = hd.hdcr_solve(co, U, B[i].contiguous(), smoother="chebyshev", coarse_solver="dense", **kw)
+            its.append(s1["iters"])
+        return its
+
+    its, t_single = _sync_time(singles)
+    co.close()
+    sub.close()
+    return {
+        "metric": METRIC, "workload_kind": "batching", "value": round(t_multi, 3), "unit": "s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "dtype": "f32 inner / f64 outer", "data": "synthetic (links on the host, noise on the device)",
+        "config": {"workload": "batching form: 16^3x32 x 16 DWF, eps=0.5, M5=1.8, mf=0.01, 12 spin-colour point "
+                               "sources, nvec=48, 4^4 blocks (4^3x8 coarse)", "plaquette": round(plaq, 4),
+                   "step": "12-source HDCR solve to 1e-10 in lockstep (FP32 V-cycle replayed from a CUDA graph, "
+                           "FP64 outer), dense coarse inverse"},
+        "setup": {"subspace_s": round(t_sub, 3), "coarse_op_s": round(t_co, 4), "coarse_invert_s": round(t_inv, 3)},
+        "multi": {"seconds": round(t_multi, 3), "outer_iters": stats[0]["iters"],
+                  "max_true_resid": max(s["true_resid"] for s in stats), "launches_per_solve": int(launches),
+                  "eager_seconds": round(t_eager, 3)},
+        "single_solves": {"seconds": round(t_single, 3), "iters": its},
+        "g5dwf_fp32": {"nrhs1": f32_1, "nrhs12": f32_12}, "coarse_rebuild_nvec48": rebuild, "clocks": clk,
+    }
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["two-level", "precision", "batching"], default="two-level")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         line = run_reference(args, world, rank)
     else:
         import __graft_entry__  # noqa: F401  (puts the repo on sys.path)
-        line = run_ours(args, world, rank, local)
+        if args.workload == "precision":
+            line = run_precision(args, world, rank, local) if rank == 0 else None
+        elif args.workload == "batching":
+            line = run_batching(args, world, rank, local) if rank == 0 else None
+        else:
+            line = run_ours(args, world, rank, local)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

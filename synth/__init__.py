@@ -34,6 +34,7 @@ __all__ = [
     "random_su3_field",
     "gaussian_fermion",
     "point_sources",
+    "device_gaussian",
     "unit_gauge",
     "lattice_shape",
 ]
@@ -123,6 +124,19 @@ def gaussian_fermion(L, Ls: int, seed: int, count: int | None = None) -> np.ndar
         shp = (int(count),) + shp
     g = rng(seed)
     return g.standard_normal(shp) + 1j * g.standard_normal(shp)
+
+
+def device_gaussian(nfields: int, V5: int, seed: int, device="cuda", dtype=None):
+    """Gaussian complex fields drawn on the device (torch's seeded generator of that
+    device), Re and Im ~ N(0,1): a tensor (nfields, V5 * 12) of complex128 (or
+    ``dtype``).  For lattices too large to draw on the host in reasonable time; the
+    entries are independent, so the layout they are read in does not matter.
+    Deterministic for a given seed and device type, not equal to gaussian_fermion."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    dt = torch.float64 if dtype is None or dtype == torch.complex128 else torch.float32
+    x = torch.randn((int(nfields), int(V5) * 12, 2), generator=g, device=device, dtype=dt)
+    return torch.view_as_complex(x)
 
 
 def point_sources(L, Ls: int, site=(0, 0, 0, 0), s: int = 0) -> np.ndarray:
