@@ -17,6 +17,8 @@ Modules
 ``multigrid``  subspace, block projection, little Dirac operator, coarse solve,
                the two-level preconditioner and the HDCR solve (Section 4)
 ``force``      gauge-link gradient of Re(eta^dag H^-1 b) (not in the paper)
+``redblack``   red-black (even-odd) preconditioned CGNE, the comparison solver of
+               Section 5 (Table 1)
 
 Layouts follow ``synth``: gauge ``(4, Lt, Lz, Ly, Lx, 3, 3)``; fermion
 ``(..., Lt, Lz, Ly, Lx, Ls, 4, 3)`` with optional leading batch axes.
