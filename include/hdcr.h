@@ -213,6 +213,24 @@ int hdcr_cr_solve(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
                   const void* b, void* x, int dtype, double tol, int max_iter,
                   hdcr_solve_stats* stats, void* stream);
 
+/* ---------------------------------------------------------------- red-black CGNE
+ * hdcr_cgne_rb_solve: H x = b by the comparison solver of Section 5 (Table 1,
+ * "CGNE (red-black)"): with the 4d sites coloured by parity (x+y+z+t) mod 2 and
+ * D_dwf = M5 + D_hop (M5 the site-local part, D_hop the 4d hops, which join
+ * opposite parities), D x = Gamma5 b is reduced to the odd sites,
+ *   S x_o = eta_o - D_oe M5^{-1} eta_e,   S = M5 - D_oe M5^{-1} D_eo,  eta = Gamma5 b,
+ * solved by conjugate gradient on S^dag S (S^dag = Gamma5 S Gamma5), and
+ * x_e = M5^{-1} (eta_e - D_eo x_o).  FP64 throughout; U, b, x are C128; x is
+ * output (zero initial guess).  Every extent L[mu] must be even.  Stops when the
+ * Schur residual |eta~_o - S x_o| (the full residual) <= tol |b|, then recomputes
+ * |b - H x| / |b| into stats->true_resid.  stats->fine_matvecs counts
+ * whole-lattice applications of the hopping term (2 per iteration + 2).
+ * Synchronises ``stream``; workspace (11 fields) is allocated and freed by the
+ * call.  Errors: BAD_ARG, BAD_GEOMETRY (an odd extent), NOT_CONVERGED, NONFINITE,
+ * CUDA, NO_MEMORY. */
+int hdcr_cgne_rb_solve(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U, const void* b,
+                       void* x, double tol, int max_iter, hdcr_solve_stats* stats, void* stream);
+
 /* ---------------------------------------------------------------- subspace
  * hdcr_build_subspace: the near-null-space basis of Section 4.
  *   1. each of the nvec/2 Gaussian noise fields (``noise``: nvec/2 C128

@@ -89,7 +89,7 @@ __all__ = [
     "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
-    "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "gauge_force", "HDCRSolve", "solve_autograd",
+    "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "cgne_rb_solve", "gauge_force", "HDCRSolve", "solve_autograd",
 ]
 
 library_path = _lib.LIB_PATH
@@ -328,6 +328,22 @@ def cr_solve_into(lat: Lattice, U: torch.Tensor, b: torch.Tensor, x: torch.Tenso
     _check(_L.hdcr_cr_solve(C_ref(g), C_ref(p), _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), _code(b),
                             float(tol), int(max_iter), C_ref(st), _stream(stream)), "cr_solve")
     return st.as_dict()
+
+
+def cgne_rb_solve(lat: Lattice, U: torch.Tensor, b: torch.Tensor, M5: float, mf: float, tol: float = 1e-10,
+                  max_iter: int = 100000, stream=None):
+    """H x = b by red-black (even-odd) preconditioned CGNE, the comparison solver of
+    Section 5, in FP64 (every extent even).  Returns (x, stats dict); raises
+    HDCRError when the solve fails."""
+    if U.dtype != torch.complex128 or b.dtype != torch.complex128:
+        raise TypeError("cgne_rb_solve takes complex128 links and source")
+    x = torch.empty_like(b)
+    g = lat.c_geom()
+    p = _params(M5, mf)
+    st = _lib.hdcr_solve_stats()
+    _check(_L.hdcr_cgne_rb_solve(C_ref(g), C_ref(p), _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), float(tol),
+                                 int(max_iter), C_ref(st), _stream(stream)), "cgne_rb_solve")
+    return x, st.as_dict()
 
 
 def C_ref(obj):

@@ -100,6 +100,7 @@ SIGNATURES = {
     "hdcr_norm2": (_I, [_P, _SZ, _I, _P, _P]),
     "hdcr_cdot_noalloc": (_I, [_P, _P, _SZ, _I, _P, _P]),
     "hdcr_cr_solve": (_I, [_G, _DP, _P, _P, _P, _I, _D, _I, _ST, _P]),
+    "hdcr_cgne_rb_solve": (_I, [_G, _DP, _P, _P, _P, _D, _I, _ST, _P]),
     "hdcr_build_subspace": (_I, [_G, _DP, _P, _P, C.POINTER(hdcr_subspace_params), _P, C.POINTER(_P)]),
     "hdcr_subspace_from_vectors": (_I, [_G, C.POINTER(C.c_int), _I, _P, _I, _P, C.POINTER(_P)]),
     "hdcr_subspace_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
