@@ -74,3 +74,37 @@ def test_fixed_iteration_cr_counts_matvecs():
     H = lambda v: (calls.append(1), dwf.apply_H(U, v, 1.8, 0.05))[1]
     cr(H, b, fixed_iters=8)
     assert len(calls) == 8          # zero guess: one apply per step, none after the last
+
+
+def test_cr_needs_no_more_matvecs_than_cgne():
+    """Section 3: CGNE's N-th iterate lies in the Krylov space that 2N steps of CR on
+    H minimise over (D^dag D = H^2 and D^dag b = H Gamma5 b), so CR reaches at least as
+    small a residual with the same number of operator applications.  CGNE here is
+    plain CG on H^2 x = H b' (b' = Gamma5 b, the normal equations of D x = b), two
+    applications of H per step; both start from zero."""
+    L, Ls, mf = (2, 2, 2, 4), 4, 0.05
+    U = synth.gauge_field(L, 0.5, 8700)
+    b = synth.gaussian_fermion(L, Ls, 8701)
+    H = lambda v: dwf.apply_H(U, v, 1.8, mf)
+    nb = np.sqrt(dwf.norm2(b))
+    # CG on H^2 x = H b, recording |b - H x| after each step (2 applications of H)
+    x = np.zeros_like(b)
+    r = H(b)  # normal-equation residual H b - H^2 x at x = 0
+    p = r.copy()
+    rr = dwf.norm2(r)
+    cgne = []
+    for _ in range(30):
+        q = H(H(p))
+        a = rr / np.real(dwf.inner(p, q))
+        x = x + a * p
+        r = r - a * q
+        rn = dwf.norm2(r)
+        p = r + (rn / rr) * p
+        rr = rn
+        cgne.append(np.sqrt(dwf.norm2(b - H(x))) / nb)
+    for n_steps in (1, 2, 5, 10, 20, 30):
+        _, info = cr(H, b, fixed_iters=2 * n_steps)
+        r_cr = info.resid_history[-1]
+        assert r_cr <= cgne[n_steps - 1] * (1 + 1e-8), (n_steps, r_cr, cgne[n_steps - 1])
+        # "about as many": here CR is better by under 1%, the paper's approximate equality
+        assert r_cr >= 0.95 * cgne[n_steps - 1], (n_steps, r_cr, cgne[n_steps - 1])
