@@ -140,6 +140,19 @@ def ddwf(U, psi, M5: float, mf: float, bc_t: int = 1) -> np.ndarray:
     return wilson(U, psi, M5, bc_t) + d5(psi, mf)
 
 
+def ddwf_mobius(U, psi, M5: float, mf: float, b5: float, bc_t: int = 1) -> np.ndarray:
+    """Moebius domain wall with c5 = 0 (Section 3 names the Shamir operator as the
+    Moebius/Cayley form with c = 0, b = 1): the 4d part is scaled by b5,
+        (D psi)(s) = (b5 D_W + 1) psi(s) - P_- psi(s + 1) - P_+ psi(s - 1),
+    i.e. D = b5 D_W + D_5 (walls as in d5).  b5 = 1 is ddwf."""
+    return b5 * wilson(U, psi, M5, bc_t) + d5(psi, mf)
+
+
+def apply_H_mobius(U, psi, M5: float, mf: float, b5: float, bc_t: int = 1) -> np.ndarray:
+    """H = Gamma5 D for the Moebius (c5 = 0) operator."""
+    return gamma5_r5(ddwf_mobius(U, psi, M5, mf, b5, bc_t))
+
+
 def gamma5_r5(psi: np.ndarray) -> np.ndarray:
     """Gamma5 = gamma5 R5: reflect s -> Ls-1-s and multiply by gamma5."""
     return spin_mul(GAMMA5, psi[..., ::-1, :, :])

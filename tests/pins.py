@@ -61,10 +61,11 @@ def d5_matrix_s(Ls, mf, Pm, Pp) -> np.ndarray:
     return M
 
 
-def plane_wave_error(dwf, L, Ls, M5, mf, n, chi, bc_t=1) -> float:
+def plane_wave_error(dwf, L, Ls, M5, mf, n, chi, bc_t=1, b5=None) -> float:
     """Free field (U = 1): D_dwf [e^{ip.x} chi(s)] = e^{ip.x} [(b(p) + i sum g_mu sin p_mu) chi(s)
     + (D5 chi)(s)], b(p) = -M5 + sum (1 - cos p_mu), p_mu = 2 pi n_mu / L_mu
-    (t: (2 n_t + 1) pi / L_t when antiperiodic).  chi: (Ls, 4, 3)."""
+    (t: (2 n_t + 1) pi / L_t when antiperiodic).  chi: (Ls, 4, 3).  With b5 given, the
+    Moebius (c5 = 0) operator: the 4d bracket is multiplied by b5."""
     Lx, Ly, Lz, Lt = L
     p = [2 * np.pi * n[m] / L[m] for m in range(3)]
     p.append((2 * n[3] + (0 if bc_t == 1 else 1)) * np.pi / Lt)
@@ -72,9 +73,11 @@ def plane_wave_error(dwf, L, Ls, M5, mf, n, chi, bc_t=1) -> float:
     phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
     psi = phase[..., None, None, None] * chi[None, None, None, None]
     U = synth.unit_gauge(L)
-    got = dwf.ddwf(U, psi, M5, mf, bc_t)
+    got = dwf.ddwf(U, psi, M5, mf, bc_t) if b5 is None else dwf.ddwf_mobius(U, psi, M5, mf, b5, bc_t)
     b = -M5 + sum(1 - np.cos(pm) for pm in p)
     K = b * np.eye(4) + 1j * sum(dwf.GAMMA[m] * np.sin(p[m]) for m in range(4))
+    if b5 is not None:
+        K = b5 * K
     four = np.einsum("ij,sjc->sic", K, chi)
     D5 = d5_matrix_s(Ls, mf, dwf.P_MINUS, dwf.P_PLUS)
     five = (D5 @ chi.reshape(Ls * 4, 3)).reshape(Ls, 4, 3)

@@ -97,3 +97,29 @@ def test_sitewise_evaluation_matches_field_apply():
     got = dwf.apply_H_at(U, psi, sites, 1.8, 0.02, -1)
     want = np.array([full[t, z, y, x, s] for (x, y, z, t, s) in sites])
     assert relerr(got, want) < 1e-15
+
+
+# ------------------------------------------------------------ Moebius, c5 = 0
+def test_mobius_b5_one_is_shamir():
+    L, Ls = (2, 3, 2, 4), 5
+    U = synth.gauge_field(L, 0.5, 9000)
+    psi = synth.gaussian_fermion(L, Ls, 9001)
+    assert relerr(dwf.ddwf_mobius(U, psi, 1.8, 0.03, 1.0, -1), dwf.ddwf(U, psi, 1.8, 0.03, -1)) == 0.0
+
+
+@pytest.mark.parametrize("b5", [0.6, 1.7])
+def test_mobius_hermiticity(b5):
+    L, Ls = (2, 2, 4, 2), 6
+    U = synth.gauge_field(L, 0.5, 9100)
+    x = synth.gaussian_fermion(L, Ls, 9101)
+    y = synth.gaussian_fermion(L, Ls, 9102)
+    lhs = dwf.inner(x, dwf.apply_H_mobius(U, y, 1.8, 0.02, b5, -1))
+    rhs = dwf.inner(dwf.apply_H_mobius(U, x, 1.8, 0.02, b5, -1), y)
+    assert abs(lhs - rhs) <= 1e-14 * abs(lhs)
+
+
+@pytest.mark.parametrize("n", [(0, 0, 0, 0), (1, 0, 2, 3)])
+def test_mobius_free_field_plane_wave(n):
+    L, Ls = (4, 6, 4, 8), 6
+    chi = synth.gaussian_fermion((1, 1, 1, 1), Ls, 9200)[0, 0, 0, 0]
+    assert plane_wave_error(dwf, L, Ls, 1.8, 0.03, n, chi, 1, b5=1.5) < 1e-14
