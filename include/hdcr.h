@@ -155,6 +155,20 @@ int hdcr_fermion_encode_h16(const hdcr_geom* g, const void* in, int in_dtype, vo
 int hdcr_fermion_decode_h16(const hdcr_geom* g, const void* in, void* out, int out_dtype, int nfields,
                             void* stream);
 
+/* hdcr_mobius_to_shamir: the Moebius domain-wall operator with c5 = 0 and scale b5
+ * (Section 3: the Shamir operator above is the Moebius/Cayley form with c = 0,
+ * b = 1), D = b5 D_W + D_5, i.e. (D psi)(s) = (b5 D_W + 1) psi(s) - P_- psi(s+1)
+ * - P_+ psi(s-1), equals the Shamir operator of this library with links b5 U and
+ * wall height M5' = 4 - b5 (4 - M5) (D_W's hops are linear in the links).  This
+ * call writes U_out = b5 U (n complex numbers, 4*V4*9 for a gauge field, device
+ * memory, dtype C128 or C64; U_out may equal U) and *shamir = {M5', mf}; with them
+ * every other call of the library (operator, solves, subspace, coarse operator)
+ * applies to the Moebius operator.  The gauge force of a solve computed with the
+ * scaled links is the gradient with respect to U_out; with respect to U it is b5
+ * times that.  b5 > 0.  Errors: BAD_ARG. */
+int hdcr_mobius_to_shamir(const hdcr_dwf_params* mobius, double b5, const void* U, void* U_out,
+                          int dtype, size_t n, hdcr_dwf_params* shamir, void* stream);
+
 /* out = Gamma5 in = gamma5 R5 in (Section 3), nfields fields; in == out not allowed. */
 int hdcr_apply_gamma5_r5(const hdcr_geom* g, const void* in, void* out, int dtype,
                          int nfields, void* stream);

@@ -86,7 +86,7 @@ def load_library():
 __all__ = [
     "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info",
-    "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "cr_solve", "cr_solve_into", "library_path",
+    "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
     "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "cgne_rb_solve", "gauge_force", "HDCRSolve", "solve_autograd",
@@ -223,6 +223,18 @@ def apply_g5dwf_h16(lat: Lattice, U: torch.Tensor, buf: torch.Tensor, M5: float,
     _check(_L.hdcr_apply_g5dwf(C_ref(g), C_ref(p), _dev(U, "U"), _dev(buf, "buf"), _dev(out, "out"),
                                _lib.HDCR_H16, buf.numel() // per, _stream(stream)), "apply_g5dwf_h16")
     return out
+
+
+def mobius_to_shamir(U: torch.Tensor, M5: float, mf: float, b5: float, stream=None):
+    """The Moebius (c5 = 0) operator b5 D_W + D_5 as this library's Shamir operator:
+    returns (b5 U, M5', mf) with M5' = 4 - b5 (4 - M5), the scaled links computed on the
+    device.  Pass them to any call in place of (U, M5, mf)."""
+    out = torch.empty_like(U)
+    p = _params(M5, mf)
+    q = _lib.hdcr_dwf_params()
+    _check(_L.hdcr_mobius_to_shamir(C_ref(p), float(b5), _dev(U, "U"), _dev(out, "U_out"), _code(U), U.numel(),
+                                    C_ref(q), _stream(stream)), "mobius_to_shamir")
+    return out, q.M5, q.mf
 
 
 def apply_gamma5_r5(lat: Lattice, psi: torch.Tensor, out: torch.Tensor | None = None, stream=None):

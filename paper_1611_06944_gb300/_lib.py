@@ -89,6 +89,7 @@ SIGNATURES = {
     "hdcr_stencil_timer_count": (_I, [_I, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "hdcr_apply_g5dwf": (_I, [_G, _DP, _P, _P, _P, _I, _I, _P]),
     "hdcr_stencil_tune": (_I, [_I, _I]),
+    "hdcr_mobius_to_shamir": (_I, [_DP, _D, _P, _P, _I, _SZ, _DP, _P]),
     "hdcr_fermion_encode_h16": (_I, [_G, _P, _I, _P, _I, _P]),
     "hdcr_fermion_decode_h16": (_I, [_G, _P, _P, _I, _I, _P]),
     "hdcr_stencil_tune_info": (_I, [_G, _I, C.POINTER(C.c_int), C.POINTER(C.c_float), _I]),
