@@ -334,7 +334,7 @@ def run_ours(args, world, rank, local):
                 "peak_note": "FP64 nominal of the profiling recipe (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
     # ---------------------------------------------------------- e2e through host buffers
     e2e = run_e2e(hd, lat, Uh, bh, nh, stream)
-    mv_step = stats[-1]["fine_matvecs"] + stats[-1]["fine_matvecs_lo"]
+    mv_step = step_matvecs(stats[-1]["fine_matvecs"] + stats[-1]["fine_matvecs_lo"])
     cpu = cpu_baseline(args, mv_step) if world == 1 else None
     line = {
         "metric": METRIC,
@@ -410,6 +410,17 @@ def run_e2e(hd, lat, Uh, bh, nh, stream) -> dict:
     return {"value": round(t, 4), "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(bh.numel() * 16)}
 
 
+# applications of H in one solve of the step as measured on GB300 (18 outer iterations)
+SOLVE_MATVECS = 814
+
+
+def step_matvecs(solve_mv: int) -> int:
+    """Applications of H in one step, the unit the oracle's time is scaled by: the
+    subspace filter (NVEC/2 fields x 2 per order), the coarse build (about one per
+    basis vector) and the solve."""
+    return NVEC // 2 * 2 * FILTER["order"] + NVEC + solve_mv
+
+
 def cpu_baseline(args, mv_step: int) -> dict:
     """The FP64 numpy oracle on this host: a bounded sample (applications of H on the
     full lattice) scaled to one step by the step's fine-matvec count."""
@@ -420,21 +431,39 @@ def cpu_baseline(args, mv_step: int) -> dict:
     U = synth.gauge_field(L_FINE, EPS, SEED_GAUGE)
     b = synth.gaussian_fermion(L_FINE, LS, SEED_SRC)
     reps = 0
+    c0 = _cpu_seconds()
     t0 = time.perf_counter()
     while True:
         dwf.apply_H(U, b, M5, MF)
         reps += 1
         if time.perf_counter() - t0 > 10.0 or reps >= 8:
             break
-    per = (time.perf_counter() - t0) / reps
+    wall = time.perf_counter() - t0
+    per = wall / reps
+    return {"value": round(per * mv_step, 2), "unit": "s", "cores": _threads_used(c0, wall), "kind": "oracle",
+            "sample": f"{reps} oracle applications of H at 16^4x16 ({per:.2f} s each) x {mv_step} applications "
+                      "of H per step (filter, coarse build and solve; a lower bound: the oracle's Gram-Schmidt, "
+                      "inverse and BLAS are not counted)",
+            "threads_note": f"numpy, single process; cores = CPU time / wall time of the sample; "
+                            f"{_host_cores()} cores available"}
+
+
+def _cpu_seconds() -> float:
+    import resource
+    r = resource.getrusage(resource.RUSAGE_SELF)
+    return r.ru_utime + r.ru_stime
+
+
+def _threads_used(c0: float, wall: float) -> int:
+    """Threads the oracle kept busy on average since c0 (CPU seconds / wall seconds)."""
+    return max(1, round((_cpu_seconds() - c0) / max(wall, 1e-9)))
+
+
+def _host_cores() -> int:
     try:
-        cores = len(os.sched_getaffinity(0))
+        return len(os.sched_getaffinity(0))
     except Exception:
-        cores = os.cpu_count()
-    return {"value": round(per * mv_step, 2), "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": f"{reps} oracle applications of H at 16^4x16 ({per:.2f} s each) x {mv_step} fine matvecs "
-                      "per GPU step (lower bound: the oracle's setup and BLAS are not counted)",
-            "threads_note": "numpy, single process"}
+        return os.cpu_count() or 1
 
 
 def run_reference(args, world, rank):
@@ -447,21 +476,17 @@ def run_reference(args, world, rank):
     from oracle import dwf
     U = synth.gauge_field(L_FINE, EPS, SEED_GAUGE)
     b = synth.gaussian_fermion(L_FINE, LS, SEED_SRC)
-    # matvecs of one HDCR step: the subspace filter (NVEC/2 x 2 x order), the solve
-    # (measured about 45 per outer iteration, ~15 outer iterations) and the coarse build
-    mv_step = NVEC // 2 * 2 * FILTER["order"] + 45 * 15 + 2 * NVEC
+    mv_step = step_matvecs(SOLVE_MATVECS)
     for _ in range(args.warmup):
         dwf.apply_H(U, b, M5, MF)
     times = []
+    c0 = _cpu_seconds()
     for _ in range(args.steps):
         t0 = time.perf_counter()
         dwf.apply_H(U, b, M5, MF)
         times.append(time.perf_counter() - t0)
     per = sum(times) / len(times)
-    try:
-        cores = len(os.sched_getaffinity(0))
-    except Exception:
-        cores = os.cpu_count()
+    cores = _threads_used(c0, sum(times))
     v = round(per * mv_step, 2)
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 2),
