@@ -79,3 +79,43 @@ def test_bad_geometry_rejected_on_host(lib):
     st = _lib.hdcr_solve_stats()
     assert lib.hdcr_cr_solve(ctypes.byref(g), ctypes.byref(p), fake, fake, fake2, 0, -1.0, 10,
                              ctypes.byref(st), None) == -1
+
+
+def test_new_entry_points_reject_bad_arguments_on_host(lib):
+    """Argument checks of the autotuner, FP16 storage, the batched and red-black
+    solves and the Moebius conversion, all before any CUDA call."""
+    from paper_1611_06944_gb300 import _lib
+    p = _lib.hdcr_dwf_params(1.8, 0.01)
+    q = _lib.hdcr_dwf_params()
+    fake = ctypes.c_void_p(0x1000)
+    fake2 = ctypes.c_void_p(0x2000)
+    odd_ptr = ctypes.c_void_p(0x1008)  # 8-byte but not 16-byte aligned
+    st = _lib.hdcr_solve_stats()
+    g = _geom()
+    # tile autotuner: mode 0..2, force_variant >= -1
+    assert lib.hdcr_stencil_tune(3, -1) == -1
+    assert lib.hdcr_stencil_tune(1, -2) == -1
+    assert lib.hdcr_stencil_tune(1, -1) == 0
+    v = ctypes.c_int()
+    assert lib.hdcr_stencil_tune_info(ctypes.byref(g), 0, ctypes.byref(v), None, 0) == -1
+    # FP16 storage: dtype, distinct aligned buffers; the operator needs an even Ls <= 16
+    assert lib.hdcr_fermion_encode_h16(ctypes.byref(g), fake, 5, fake2, 1, None) == -1
+    assert lib.hdcr_fermion_encode_h16(ctypes.byref(g), fake, 0, fake, 1, None) == -1
+    assert lib.hdcr_fermion_encode_h16(ctypes.byref(g), odd_ptr, 0, fake2, 1, None) == -1
+    assert lib.hdcr_fermion_decode_h16(ctypes.byref(g), fake, fake2, 0, 0, None) == -1
+    g5 = _geom(Ls=5)
+    assert lib.hdcr_apply_g5dwf(ctypes.byref(g5), ctypes.byref(p), fake, fake, fake2, _lib.HDCR_H16, 1, None) == -1
+    # red-black CGNE: every extent even, tol > 0
+    godd = _geom(L=(4, 3, 4, 4))
+    assert lib.hdcr_cgne_rb_solve(ctypes.byref(godd), ctypes.byref(p), fake, fake, fake2, 1e-10, 10,
+                                  ctypes.byref(st), None) == -2
+    assert lib.hdcr_cgne_rb_solve(ctypes.byref(g), ctypes.byref(p), fake, fake, fake2, 0.0, 10,
+                                  ctypes.byref(st), None) == -1
+    # Moebius conversion: b5 > 0, a known dtype
+    assert lib.hdcr_mobius_to_shamir(ctypes.byref(p), 0.0, fake, fake2, 0, 36, ctypes.byref(q), None) == -1
+    assert lib.hdcr_mobius_to_shamir(ctypes.byref(p), 1.5, fake, fake2, 9, 36, ctypes.byref(q), None) == -1
+    # batched solve and coarse build: a null handle is refused
+    prm = _lib.hdcr_solve_params()
+    assert lib.hdcr_solve_multi(None, fake, fake, fake2, 2, ctypes.byref(prm), 1, ctypes.byref(st), None) == -1
+    h = ctypes.c_void_p()
+    assert lib.hdcr_build_coarse_op(None, ctypes.byref(p), fake, _lib.HDCR_C64_FAST, None, ctypes.byref(h)) == -1
