@@ -46,3 +46,25 @@ def test_two_rank_aggregate_is_max_over_ranks():
         assert res[r]["max_seconds"] == 2.0
         assert res[r]["total_units"] == 10
         assert abs(res[r]["seconds_per_unit"] - 0.2) < 1e-12
+
+
+def test_reference_arm_line_keeps_the_contract(monkeypatch):
+    """bench.py --impl reference on the CPU (the oracle as the reference arm): rank 0
+    prints the JSON line with the contract's keys; other ranks do no work.  Run on a
+    small lattice so that the test takes a second."""
+    import argparse
+    import bench
+    monkeypatch.setattr(bench, "L_FINE", (4, 4, 4, 4))
+    monkeypatch.setattr(bench, "LS", 8)
+    args = argparse.Namespace(steps=2, warmup=1, gpus=1, impl="reference", workload="two-level")
+    assert bench.run_reference(args, 2, 1) is None
+    line = bench.run_reference(args, 1, 0)
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "dtype",
+              "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["higher_is_better"] is False
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["unit"] == line["unit"]
+    assert "workload" in line["config"]
