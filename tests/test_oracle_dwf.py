@@ -86,6 +86,24 @@ def test_synthetic_links_are_su3():
     assert err_u < 1e-14 and err_d < 1e-14
 
 
+def test_device_gaussian_is_seeded_and_standard():
+    """The device-side noise of the large workloads: the same seed gives the same
+    numbers, and Re, Im are independent N(0, 1) (here drawn on the CPU device)."""
+    torch = pytest.importorskip("torch")
+    a = synth.device_gaussian(2, 4096, 11, device="cpu")
+    b = synth.device_gaussian(2, 4096, 11, device="cpu")
+    c = synth.device_gaussian(2, 4096, 12, device="cpu")
+    assert a.shape == (2, 4096 * 12) and a.dtype == torch.complex128
+    assert torch.equal(a, b) and not torch.equal(a, c)
+    re, im = a.real.numpy().ravel(), a.imag.numpy().ravel()
+    n = re.size
+    for x in (re, im):  # mean 0, variance 1 within a few standard errors
+        assert abs(x.mean()) < 5 / np.sqrt(n)
+        assert abs(x.var() - 1) < 5 * np.sqrt(2 / n)
+    assert abs(np.corrcoef(re, im)[0, 1]) < 5 / np.sqrt(n)
+    assert synth.device_gaussian(1, 8, 3, device="cpu", dtype=torch.complex64).dtype == torch.complex64
+
+
 def test_sitewise_evaluation_matches_field_apply():
     L, Ls = (3, 4, 2, 5), 4
     U = synth.gauge_field(L, 0.5, 61)
