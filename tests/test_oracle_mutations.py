@@ -197,3 +197,77 @@ def test_inverted_cr_beta_is_caught(monkeypatch):
     assert relerr(x, np.linalg.solve(A, b)) > 1e-3
     x_ok, _ = krylov.cr(lambda v: A @ v, b, tol=1e-12, maxiter=400)
     assert relerr(x_ok, np.linalg.solve(A, b)) < 1e-9
+
+
+# ------------------------------------------------------------ red-black CGNE and Moebius
+from oracle import redblack as rb  # noqa: E402
+from pins import dense_H_assembled  # noqa: E402
+
+
+def _rb_lu_error():
+    """Red-black CGNE against the independently assembled dense H (the pin of
+    test_oracle_redblack): relative error of the solution."""
+    L, Ls, M5, mf = (4, 2, 2, 2), 4, 1.8, 0.05
+    U = synth.gauge_field(L, 0.5, 8300)
+    b = synth.gaussian_fermion(L, Ls, 8301)
+    x, _, _ = rb.cgne_rb_solve(U, b, M5, mf, -1, tol=1e-12, maxiter=3000)
+    H = dense_H_assembled(dwf, U, Ls, M5, mf, -1)
+    xo = np.linalg.solve(H, b.ravel()).reshape(b.shape)
+    return relerr(x, xo)
+
+
+def _m5inv_error():
+    psi = synth.gaussian_fermion((2, 2, 2, 2), 8, 8100)
+    return relerr(rb.m5_apply(rb.m5_inverse(psi, 1.8, 0.03), 1.8, 0.03), psi)
+
+
+def _schur_herm_error():
+    L, Ls, M5, mf = (4, 2, 2, 4), 4, 1.8, 0.02
+    U = synth.gauge_field(L, 0.5, 8200)
+    odd = rb.parity_mask(L)
+    x = rb.on_parity(synth.gaussian_fermion(L, Ls, 8201), odd, 1)
+    y = rb.on_parity(synth.gaussian_fermion(L, Ls, 8202), odd, 1)
+    lhs = dwf.inner(x, rb.schur_apply(U, y, odd, M5, mf))
+    rhs = dwf.inner(rb.schur_dag_apply(U, x, odd, M5, mf), y)
+    return abs(lhs - rhs) / abs(lhs)
+
+
+def test_unmutated_redblack_and_mobius_pass():
+    assert _rb_lu_error() < 1e-9 and _m5inv_error() < 1e-14 and _schur_herm_error() < 1e-13
+    chi = synth.gaussian_fermion((1, 1, 1, 1), LS, 21)[0, 0, 0, 0]
+    assert plane_wave_error(dwf, (4, 6, 4, 8), LS, 1.8, 0.03, (1, 0, 2, 3), chi, 1, b5=1.5) < 1e-14
+
+
+def test_schur_without_m5_inverse_is_caught(monkeypatch):
+    def bad(U, v, odd, M5, mf, bc_t=1):  # D_oe D_eo in place of D_oe M5^{-1} D_eo
+        a = rb.on_parity(rb.dhop_apply(U, v, M5, bc_t), odd, 0)
+        c = rb.on_parity(rb.dhop_apply(U, a, M5, bc_t), odd, 1)
+        return rb.on_parity(rb.m5_apply(v, M5, mf), odd, 1) - c
+
+    monkeypatch.setattr(rb, "schur_apply", bad)
+    assert _rb_lu_error() > 1e-3
+
+
+def test_transposed_m5_inverse_is_caught(monkeypatch):
+    def bad(psi, M5, mf):
+        Ls = psi.shape[-3]
+        Minv = np.linalg.inv(rb.m5_matrix(Ls, M5, mf))
+        return np.einsum("pts,...tpc->...spc", Minv, psi)  # Minv^T
+
+    monkeypatch.setattr(rb, "m5_inverse", bad)
+    assert _m5inv_error() > 1e-3
+
+
+def test_schur_adjoint_without_gamma5_is_caught(monkeypatch):
+    monkeypatch.setattr(rb, "schur_dag_apply", lambda U, v, odd, M5, mf, bc_t=1: rb.schur_apply(U, v, odd, M5, mf, bc_t))
+    assert _schur_herm_error() > 1e-3
+
+
+def test_mobius_with_unscaled_mass_term_is_caught(monkeypatch):
+    def bad(U, psi, M5, mf, b5, bc_t=1):  # b5 on the hops only, not on (4 - M5)
+        hops = dwf.wilson(U, psi, M5, bc_t) - (4.0 - M5) * psi
+        return b5 * hops + (4.0 - M5) * psi + dwf.d5(psi, mf)
+
+    monkeypatch.setattr(dwf, "ddwf_mobius", bad)
+    chi = synth.gaussian_fermion((1, 1, 1, 1), LS, 21)[0, 0, 0, 0]
+    assert plane_wave_error(dwf, (4, 6, 4, 8), LS, 1.8, 0.03, (1, 0, 2, 3), chi, 1, b5=1.5) > 1e-3
