@@ -215,23 +215,30 @@ def coarse_op(U, sub: Subspace, M5, mf, bc_t=1) -> np.ndarray:
     """Little Dirac operator A (Vc, 9, nvec, nvec), A[a, d, j, k] = <phi_j^a|H|phi_k^{a+d}>.
 
     Leg d = (mu, sign) keeps only the fine hops reading x + sign*mu that leave
-    the block; the self leg keeps H minus every block-crossing hop.
+    the block; the self leg keeps H minus every block-crossing hop.  For each
+    leg the images Y_k of all nvec basis vectors are formed first; the block
+    inner products <phi_j^a | Y_k^a> of every (j, k) are then one batched matrix
+    product per leg (the same sums as Eq. 4.5 term by term).
     """
     g = sub.geom
     nvec = sub.nvec
     A = np.zeros((g.Vc, NLEGS, nvec, nvec), dtype=np.complex128)
     masks = {(mu, s): crossing_mask(g, mu, s)[..., None, None, None]
              for mu in range(4) for s in (+1, -1)}
-    for k in range(nvec):
-        phik = from_blocks(g, sub.Phi[k])
-        Yself = dwf.apply_H(U, phik, M5, mf, bc_t)
-        for mu in range(4):
-            for s in (+1, -1):
-                Yd = masks[(mu, s)] * dwf.apply_H_hop(U, phik, mu, s, bc_t)
-                Yself = Yself - Yd
-                A[:, leg_index(mu, s), :, k] = np.einsum(
-                    "jak,ak->aj", np.conj(sub.Phi), to_blocks(g, Yd))
-        A[:, 0, :, k] = np.einsum("jak,ak->aj", np.conj(sub.Phi), to_blocks(g, Yself))
+    phit = np.conj(np.transpose(sub.Phi, (1, 0, 2)))             # (Vc, nvec j, K)
+    phis = [from_blocks(g, sub.Phi[k]) for k in range(nvec)]
+
+    def project(Y):                                             # Y: (nvec k, Vc, K)
+        return np.matmul(phit, np.transpose(Y, (1, 2, 0)))      # (Vc, j, k)
+
+    Yself = np.stack([to_blocks(g, dwf.apply_H(U, phik, M5, mf, bc_t)) for phik in phis])
+    for mu in range(4):
+        for s in (+1, -1):
+            Yd = np.stack([to_blocks(g, masks[(mu, s)] * dwf.apply_H_hop(U, phik, mu, s, bc_t))
+                           for phik in phis])
+            Yself -= Yd
+            A[:, leg_index(mu, s)] = project(Yd)
+    A[:, 0] = project(Yself)
     return A
 
 
