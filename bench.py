@@ -59,14 +59,27 @@ SEED_GAUGE, SEED_SRC, SEED_NOISE = 1001, 2001, 3001
 FILTER = dict(kind="chebyshev", order=300, lam_cut=0.3, lam_max=8.0)
 SOLVE = dict(tol=1e-10, restart=8, smoother="chebyshev", smoother_order=10, cheb_lo=1.0, cheb_hi=64.0,
              coarse_solver="dense", max_outer=200)
-# floating-point operations per 5d site of one application of H as the kernel
-# executes them (FMA = 2): 8 hops x (12 projection + 144 SU(3) + 48 accumulate)
-# + 72 for the diagonal and the fifth-dimension hops
-FLOPS_PER_SITE = 8 * (12 + 144 + 48) + 72
+# Algorithmic floating-point operations per 5d site of one application of H (real
+# adds and multiplies, an FMA counted as 2): the Wilson hopping term in its
+# standard count, 8 hops x (12 spin projection + 132 SU(3) x half-spinor + 24
+# accumulation) - 24 (the first hop initialises the sum) = 1320; the -1/2 scale of
+# the hop sum (24), the (5 - M5) diagonal (24), adding the two (24) and the two
+# fifth-dimension hops P_-psi(s+1), P_+psi(s-1) (12 complex subtractions, 24): 1416.
+# Gamma5 and the R5 reflection are signs and a permutation (free).
+FLOPS_PER_SITE = 1320 + 4 * 24
+# FP64 instructions per 5d site the FP64 kernel issues (each one slot of the FP64
+# pipe whether add, multiply or FMA): per hop 12 projection adds, 72 for the
+# SU(3) x half-spinor (4 per complex multiply(-add)), 24 FMAs accumulating the upper
+# and the Gamma5-signed lower spins with the boundary factor; plus 24 multiplies
+# (diagonal) and 24 FMAs (fifth dimension).
+FP64_INSTR_PER_SITE = 8 * (12 + 72 + 24) + 48
+
+
 # algorithmic bytes per 5d site of one application (read psi, write H psi, links / Ls)
 def bytes_per_site(real_bytes: int, Ls: int) -> float:
     return 2 * 12 * 2 * real_bytes + 4 * 9 * 2 * real_bytes / Ls
-FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal, profiling recipe)
+
+
 # DRAM traffic of one FP64 / FP32 / FP16-storage stencil launch at 16^4 x 16 from ncu, with the hash of
 # the stencil sources it was measured on (reported as null once the sources change)
 NCU_TRAFFIC = {"f64": 451.63e6, "f32": 203.95e6, "h16": 106.12e6, "src_hash": "93e5f49c49aabef4"}
@@ -326,12 +339,21 @@ def run_ours(args, world, rank, local):
     sites64 = st64["sites"] / max(st64["launches"], 1)
     achieved = FLOPS_PER_SITE * sites64 / (ms64 * 1e-3) / 1e12
     share64 = ms64 * st64["all_launches"] / (elapsed * 1e3)   # every FP64 launch at the timed average
+    fp64_peak = hd.probe_fma_rate(torch.complex128)            # measured on this GPU, this run
+    pipe = FP64_INSTR_PER_SITE * sites64 / (ms64 * 1e-3) / (fp64_peak * 1e12 / 2)
     roofline = {"bound": "alu", "kernel": "g5dwf FP64 (H = Gamma5 D_dwf)", "achieved": round(achieved, 4),
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "peak": round(fp64_peak, 4), "unit": "TFLOP/s", "frac": round(achieved / fp64_peak, 4),
                 "traffic": NCU_TRAFFIC["f64"] if same_src else None,
-                "flops_per_site": FLOPS_PER_SITE, "avg_launch_ms": round(ms64, 4),
-                "share_of_step": round(share64, 3),
-                "peak_note": "FP64 nominal of the profiling recipe (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+                "flops_per_site": FLOPS_PER_SITE, "fp64_instr_per_site": FP64_INSTR_PER_SITE,
+                "fp64_pipe_frac": round(pipe, 4), "avg_launch_ms": round(ms64, 4),
+                "share_of_step": round(share64, 3), "peak_source": "measured",
+                "peak_note": "FP64 FMA rate measured in this run (hdcr_probe_fma_rate: independent DFMA chains "
+                             "on every SM, FMA = 2 flops); achieved counts the 1416 algorithmic flops per site, "
+                             "fp64_pipe_frac the FP64 instructions the kernel issues against the same rate"}
+    roofline_fp32 = {"bound": "hbm", "kernel": "g5dwf FP32 (H = Gamma5 D_dwf)", "achieved": round(gbs32, 1),
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(gbs32 / pk["hbm_gbs"], 4),
+                     "traffic": NCU_TRAFFIC["f32"] if same_src else None, "bytes_per_site": bps32,
+                     "peak_source": pk["source"]}
     # ---------------------------------------------------------- e2e through host buffers
     e2e = run_e2e(hd, lat, Uh, bh, nh, stream)
     mv_step = step_matvecs(stats[-1]["fine_matvecs"] + stats[-1]["fine_matvecs_lo"])
@@ -379,6 +401,7 @@ def run_ours(args, world, rank, local):
                        "traffic": NCU_TRAFFIC["f32"] if same_src else None},
         "g5dwf_fp16_storage": h16,
         "roofline": roofline,
+        "roofline_fp32": roofline_fp32,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -767,13 +790,170 @@ def run_table1(args, world, rank, local):
     }
 
 
+def run_differentiation(args, world, rank, local):
+    """8^3 x 16, Ls = 8: loss Re(eta^dag x), x = hdcr_solve(U, b) differentiated by the
+    backward (adjoint HDCR solve with the subspace rebuilt + gauge force), in complex128
+    and complex64.  value = seconds of one forward + backward in complex128; the
+    gradient's error against the FP64 oracle gradient (tests/golden, written by the
+    oracle alone) is reported for both precisions."""
+    import numpy as np
+    import torch
+
+    import paper_1611_06944_gb300 as hd
+    import synth
+    torch.cuda.set_device(local)
+    with open(os.path.join(ROOT, "tests", "golden", "grad_8x8x8x16_ls8.json")) as f:
+        gd = json.load(f)
+    L, Ls, mf = tuple(gd["lattice"]), gd["Ls"], gd["mf"]
+    lat = hd.Lattice(L, Ls, gd["bc_t"])
+    U = synth.gauge_field(L, gd["eps"], gd["seeds"]["U"]).reshape(4, -1, 3, 3)
+
+    def planes(a):
+        return np.ascontiguousarray(np.swapaxes(a.reshape(-1, Ls, 12), -1, -2))
+
+    b = planes(synth.gaussian_fermion(L, Ls, gd["seeds"]["b"]))
+    eta = planes(synth.gaussian_fermion(L, Ls, gd["seeds"]["eta"]))
+    noise = torch.from_numpy(planes(synth.gaussian_fermion(L, Ls, 6003, count=8)).reshape(8, -1, 12, Ls)).cuda()
+    want = np.array([[complex(r, i) for r, i in v] for _, _, v in gd["links"]])
+    out = {}
+    for name, dt, tol in (("c128", torch.complex128, 1e-12), ("c64", torch.complex64, 1e-7)):
+        def step():
+            Ut = torch.from_numpy(U).cuda().to(dt).requires_grad_(True)
+            bt = torch.from_numpy(b).cuda().to(dt).requires_grad_(True)
+            x = hd.solve_autograd(lat, Ut, bt, noise, gd["M5"], mf, (4, 4, 4, 4),
+                                  filter_kw=dict(kind="chebyshev", order=100),
+                                  solve_kw=dict(tol=tol, max_outer=500))
+            loss = torch.vdot(torch.from_numpy(eta).cuda().to(dt).reshape(-1), x.reshape(-1)).real
+            loss.backward()
+            return Ut.grad
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g = step()
+        e1.record()
+        torch.cuda.synchronize()
+        gU = g.cpu().numpy().astype(np.complex128)
+        got = np.array([gU[mu, x4].reshape(-1) for mu, x4, _ in gd["links"]])
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        out[name] = {"seconds_fwd_bwd": round(e0.elapsed_time(e1) / 1e3 / args.steps, 4),
+                     "grad_rel_err_vs_fp64_oracle": err, "solve_tol": tol,
+                     "sample": f"{len(gd['links'])} links (9 entries each) of dL/dU"}
+    return {"metric": METRIC, "workload_kind": "differentiation", "value": out["c128"]["seconds_fwd_bwd"],
+            "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "f64 / f32", "data": "synthetic",
+            "config": {"workload": "differentiation form: 8^3x16 x 8 DWF, eps=0.5, M5=1.8, mf=0.05, loss "
+                                   "Re(eta^dag x), nvec=16, 4^4 blocks, Chebyshev filter order 100"},
+            "c128": out["c128"], "c64": out["c64"]}
+
+
+def _extents(spec: str) -> tuple:
+    parts = [int(v) for v in spec.split(",")]
+    return tuple(parts) if len(parts) == 4 else (parts[0],) * 4
+
+
+def run_stencil(args, world, rank, local):
+    """Repeated applications of H (Ls = 16) on random device data: the kernel-level
+    workload the ncu captures in profiles/ run.  --lattice L or Lx,Ly,Lz,Lt;
+    --dtype f64, f32 or h16 (FP16 storage); --reps launches timed after as many warm-up
+    launches.  Reports the event-timed microseconds per launch and algorithmic GB/s."""
+    import torch
+
+    import paper_1611_06944_gb300 as hd
+    torch.cuda.set_device(local)
+    L, dtype, reps = _extents(args.lattice), args.dtype, args.reps
+    h16 = dtype == "h16"
+    dt = torch.complex64 if dtype in ("f32", "h16") else torch.complex128
+    lat = hd.Lattice(L, LS)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    U = torch.randn(4, lat.V4, 3, 3, dtype=dt, device="cuda", generator=g)
+    x = torch.randn(args.nrhs, lat.V4, 12, LS, dtype=dt, device="cuda", generator=g)
+    if h16:
+        x = hd.encode_h16(lat, x)
+    y = torch.empty_like(x)
+    apply = (lambda: hd.apply_g5dwf_h16(lat, U, x, M5, MF, out=y)) if h16 else \
+        (lambda: hd.apply_g5dwf(lat, U, x, M5, MF, out=y))
+    for _ in range(reps):
+        apply()
+    torch.cuda.synchronize()
+    hd.stencil_timer(True)
+    for _ in range(reps):
+        apply()
+    torch.cuda.synchronize()
+    t = hd.stencil_timer_read("h16" if h16 else dt)
+    hd.stencil_timer(False)
+    us = t["ms"] / max(t["launches"], 1) * 1e3
+    real = 4 if dt == torch.complex64 else 8
+    per_site = 2 * 24 * real + 4 * 18 * real / LS / args.nrhs  # psi in + out, links shared by the Ls sites
+    if h16:
+        per_site = 2 * 52 + 4 * 18 * 4 / LS / args.nrhs        # half2 spinor + FP32 scale in and out; FP32 links
+    gbs = lat.V5 * args.nrhs * per_site / (us * 1e-6) / 1e9
+    return {"workload_kind": "stencil", "lattice": list(L), "Ls": LS, "dtype": dtype, "nrhs": args.nrhs,
+            "us_per_launch": round(us, 2), "GBs": round(gbs, 1), "frac_of_hbm": round(gbs / peaks()["hbm_gbs"], 4),
+            "bytes_per_site": per_site, "launches": t["launches"]}
+
+
+def run_coarse(args, world, rank, local):
+    """Builds of the little Dirac operator from nvec random basis vectors on 4^4 blocks
+    (Ls = 16): --lattice, --nvec, --dtype f64, f32 or f32fast (single-pass TF32
+    projections), --reps timed builds after one warm-up; reported in units of one fine
+    application of H of the same precision."""
+    import torch
+
+    import paper_1611_06944_gb300 as hd
+    torch.cuda.set_device(local)
+    L, nvec, dtype, reps = _extents(args.lattice), args.nvec, args.dtype, args.reps
+    fast = dtype == "f32fast"
+    dt = torch.complex64 if dtype in ("f32", "f32fast") else torch.complex128
+    lat = hd.Lattice(L, LS)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    U = torch.randn(4, lat.V4, 3, 3, dtype=torch.complex128, device="cuda", generator=g)
+    v = torch.randn(nvec, lat.V4, 12, LS, dtype=torch.complex128, device="cuda", generator=g)
+    sub = hd.subspace_from_vectors(lat, BLOCK, v, store_dtype=dt)
+    del v
+    torch.cuda.empty_cache()
+    hd.build_coarse_op(sub, U, M5, MF, op_dtype=dt, fast=fast).close()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        hd.build_coarse_op(sub, U, M5, MF, op_dtype=dt, fast=fast).close()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    Ud = U.to(dt)
+    x = torch.randn(lat.V4, 12, LS, dtype=dt, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        hd.apply_g5dwf(lat, Ud, x, M5, MF, out=y)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(10):
+        hd.apply_g5dwf(lat, Ud, x, M5, MF, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    mv = e0.elapsed_time(e1) / 10
+    sub.close()
+    return {"workload_kind": "coarse", "lattice": list(L), "Ls": LS, "nvec": nvec, "block": list(BLOCK),
+            "dtype": dtype, "build_ms": round(ms, 3), "fine_matvec_ms": round(mv, 4),
+            "fine_matvecs": round(ms / mv, 1)}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["two-level", "precision", "batching", "table1"], default="two-level")
+    ap.add_argument("--workload", choices=["two-level", "precision", "batching", "table1", "differentiation",
+                                           "stencil", "coarse"], default="two-level")
+    ap.add_argument("--lattice", default="16", help="stencil/coarse: L or Lx,Ly,Lz,Lt (Ls = 16)")
+    ap.add_argument("--dtype", default="f32", help="stencil: f64|f32|h16; coarse: f64|f32|f32fast")
+    ap.add_argument("--nvec", type=int, default=24, help="coarse: basis vectors")
+    ap.add_argument("--nrhs", type=int, default=1, help="stencil: fields per launch")
+    ap.add_argument("--reps", type=int, default=4, help="stencil/coarse: timed launches or builds")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -786,6 +966,12 @@ def main(argv=None) -> int:
             line = run_batching(args, world, rank, local) if rank == 0 else None
         elif args.workload == "table1":
             line = run_table1(args, world, rank, local) if rank == 0 else None
+        elif args.workload == "differentiation":
+            line = run_differentiation(args, world, rank, local) if rank == 0 else None
+        elif args.workload == "stencil":
+            line = run_stencil(args, world, rank, local) if rank == 0 else None
+        elif args.workload == "coarse":
+            line = run_coarse(args, world, rank, local) if rank == 0 else None
         else:
             line = run_ours(args, world, rank, local)
     if rank == 0 and line is not None:

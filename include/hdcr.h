@@ -115,6 +115,13 @@ int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* launches, lo
 /* Every application of H of one precision since the timer was started,
  * including those beyond the 16384 that carry events: launches and 5d sites. */
 int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites);
+/* Measured FMA rate of the current device (a property of the machine, used as
+ * the roofline denominator of the arithmetic-bound FP64 operator; not a step of
+ * the method): every SM runs long chains of independent fused multiply-adds of
+ * one precision (HDCR_C128: FP64, HDCR_C64: FP32), five launches are timed with
+ * CUDA events on ``stream`` and *tflops receives 2 x FMAs / second / 1e12.
+ * Synchronises ``stream``.  Errors: BAD_ARG, CUDA. */
+int hdcr_probe_fma_rate(int dtype, double* tflops, void* stream);
 
 /* ---------------------------------------------------------------- fine operator
  * hdcr_apply_g5dwf: out = H in with H = Gamma5 D_dwf = gamma5 R5 D_dwf
@@ -197,19 +204,20 @@ int hdcr_cdot(const void* u, const void* v, size_t n, int dtype, double* result,
 int hdcr_norm2(const void* u, size_t n, int dtype, double* result, void* stream);
 
 /* hdcr_cdot_noalloc: the same inner product as hdcr_cdot, for callers that may
- * not let the library allocate device memory -- for example code that runs
- * while a CUDA graph is being captured (an allocation breaks the capture), or
- * a caller that keeps the whole device memory budget in its own pool.  The
- * paper has no counterpart: this is an interface of the library, not a step of
- * the method.  Its scratch (one FP64 partial sum per 4096 entries and a
- * completion counter, 1 MiB) is a fixed array compiled into the library, held
- * on every GPU that loads the library until the process exits; the call
- * allocates nothing and only launches kernels and clears the counter on
- * ``stream``.  n may not exceed HDCR_NOALLOC_MAX_N (BAD_ARG otherwise).  The
- * first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  All calls share
- * the one array: calls that overlap on the GPU (different streams) race and
- * give wrong results.  result: DEVICE pointer to 2 doubles. */
+ * not let the library allocate device memory -- for example a caller that hands
+ * all device memory to its own pool at start-up and keeps a fixed budget, or a
+ * runtime that forbids allocations after start-up.  The paper has no
+ * counterpart: this is an interface of the library, not a step of the method.
+ * Its scratch (one FP64 partial sum per 4096 entries and a completion counter,
+ * 1 MiB) is a fixed array compiled into the library, held on every GPU that
+ * loads the library until the process exits; the call allocates nothing and
+ * only launches kernels and clears the counter on ``stream``.  n may not exceed
+ * HDCR_NOALLOC_MAX_N (BAD_ARG otherwise).  The first call on a device looks up
+ * the array's device address with that device current and keeps it for the
+ * life of the process; make that first call before any stream capture, and
+ * make no call after a device reset (the kept address would be stale).  All
+ * calls share the one array: calls that overlap on the GPU (different streams)
+ * race and give wrong results.  result: DEVICE pointer to 2 doubles. */
 #define HDCR_NOALLOC_MAX_N 268435456
 int hdcr_cdot_noalloc(const void* u, const void* v, size_t n, int dtype, double* result,
                       void* stream);
@@ -412,6 +420,12 @@ int hdcr_solve_multi(hdcr_coarse* co, const void* U, const void* b, void* x, int
  */
 int hdcr_gauge_force(const hdcr_geom* g, const void* x, const void* w, void* F, int dtype,
                      void* stream);
+/* hdcr_gauge_grad: the same sum as hdcr_gauge_force, stored as the gradient of
+ * the loss with respect to the links in the gauge layout:
+ * G[mu][x4][a][b] = conj((F_mu(x))_ba) = dL/dRe U_ab + i dL/dIm U_ab (the
+ * convention of torch's complex autograd).  Errors: BAD_ARG, BAD_GEOMETRY. */
+int hdcr_gauge_grad(const hdcr_geom* g, const void* x, const void* w, void* G, int dtype,
+                    void* stream);
 
 #ifdef __cplusplus
 }

@@ -79,17 +79,26 @@ def stencil_tune_info(lat: "Lattice", nrhs: int = 1, nvariants: int = 16) -> dic
     return {"variant": v.value, "us": [round(float(x), 2) for x in us]}
 
 
+def probe_fma_rate(dtype: torch.dtype = torch.complex128, stream=None) -> float:
+    """Measured FMA rate of the current GPU in TFLOP/s (FMA = 2 flops): FP64 for
+    complex128, FP32 for complex64.  The roofline denominator of the FP64 operator."""
+    r = ctypes.c_double()
+    _check(_L.hdcr_probe_fma_rate(_dt(dtype), ctypes.byref(r), _stream(stream)), "probe_fma_rate")
+    return r.value
+
+
 def load_library():
     """Load libhdcr.so now (raises ImportError if it has not been built)."""
     return _L.hdcr_version()
 
 __all__ = [
-    "HDCRError", "Lattice", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
+    "HDCRError", "Lattice", "probe_fma_rate", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info",
     "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
-    "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "cgne_rb_solve", "gauge_force", "HDCRSolve", "solve_autograd",
+    "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "cgne_rb_solve", "gauge_force", "gauge_grad", "HDCRSolve",
+    "solve_autograd",
 ]
 
 library_path = _lib.LIB_PATH
@@ -642,36 +651,93 @@ def gauge_force(lat: Lattice, x: torch.Tensor, w: torch.Tensor, stream=None) -> 
     return F
 
 
+def gauge_grad(lat: Lattice, x: torch.Tensor, w: torch.Tensor, stream=None) -> torch.Tensor:
+    """The gauge force of (x, w) stored as the gradient with respect to the links:
+    G[mu, x4, a, b] = conj(F_mu(x)_ba) = dL/dRe U_ab + i dL/dIm U_ab (torch's convention
+    for complex gradients).  Returns a (4, V4, 3, 3) tensor of x's dtype."""
+    if x.dtype != w.dtype or _nfields(lat, x, "x") != 1 or _nfields(lat, w, "w") != 1:
+        raise ValueError("x and w must be single fields of one dtype")
+    G = torch.empty((4, lat.V4, 3, 3), dtype=x.dtype, device=x.device)
+    g = lat.c_geom()
+    _check(_L.hdcr_gauge_grad(C_ref(g), _dev(x, "x"), _dev(w, "w"), G.data_ptr(), _code(x),
+                              _stream(stream)), "gauge_grad")
+    return G
+
+
+# default true-residual target of the differentiable solve per input precision: the
+# complex64 form returns FP32 fields, for which 1e-7 is below their own rounding
+_AUTOGRAD_TOL = {torch.complex128: 1e-10, torch.complex64: 1e-7}
+
+
+def _autograd_setup(lat, U64, noise, M5, mf, block, filter_kw, dtype):
+    """Subspace and coarse operator of the differentiable solve in the precision of
+    the inputs (complex64: FP32 filter, basis and coarse operator)."""
+    kw = dict(filter_kw)
+    if dtype == torch.complex64:
+        kw.setdefault("filter_dtype", torch.complex64)
+        kw.setdefault("store_dtype", torch.complex64)
+    sub = build_subspace(lat, U64, noise, M5, mf, block, **kw)
+    co = build_coarse_op(sub, U64, M5, mf, op_dtype=sub.dtype)
+    return sub, co
+
+
+def _autograd_solve(lat, U, rhs, noise, M5, mf, block, filter_kw, solve_kw):
+    """H(U) x = rhs with a freshly built subspace and coarse operator, which are freed
+    before returning; U and rhs share their dtype (complex128 or complex64) and so
+    does x.  The outer flexible GCR runs in FP64 on the upcast inputs; with complex64
+    inputs the V-cycle (smoother, basis, coarse operator) runs in FP32."""
+    dtype = U.dtype
+    U64 = U if dtype == torch.complex128 else convert(U, torch.complex128)
+    r64 = rhs.contiguous() if dtype == torch.complex128 else convert(rhs.contiguous(), torch.complex128)
+    kw = dict(solve_kw)
+    kw.setdefault("tol", _AUTOGRAD_TOL[dtype])
+    sub, co = _autograd_setup(lat, U64, noise, M5, mf, block, filter_kw, dtype)
+    try:
+        x, st = hdcr_solve(co, U64, r64, inner_dtype=sub.dtype, **kw)
+    finally:
+        co.close()
+        sub.close()
+    return (x if dtype == torch.complex128 else convert(x, dtype)), st
+
+
 class HDCRSolve(torch.autograd.Function):
-    """x = H(U)^{-1} b by HDCR, differentiable in U and b.
+    """x = H(U)^{-1} b by HDCR, differentiable in U and b; U, b and x are complex128
+    or complex64 (one dtype for all three).
 
     Forward: build the subspace and coarse operator from ``noise`` (not
-    differentiated: the converged solution does not depend on it) and solve.
-    Backward, given g = dL/dx (torch convention): the adjoint solve H y = g with
-    the same Hermitian operator and coarse space, then dL/db = y and
-    dL/dU = F^dag per link with F the gauge force of (x, Gamma5 y).
+    differentiated: the converged solution does not depend on it), solve, and free
+    them: only U, x and the noise are kept for the backward.
+    Backward, given g = dL/dx (torch convention): the subspace and coarse operator
+    are rebuilt from the same noise, the adjoint solve H y = g runs with the same
+    Hermitian operator and coarse space, then dL/db = y and dL/dU is the gauge force
+    of (x, Gamma5 y) in gradient layout (``gauge_grad``), both in the input dtype.
+    Recomputing costs one more setup per backward and saves keeping the nvec basis
+    fields and the coarse operator alive between forward and backward.
     """
 
     @staticmethod
     def forward(ctx, U, b, lat, noise, M5, mf, block, filter_kw, solve_kw):
-        sub = build_subspace(lat, U, noise, M5, mf, block, **filter_kw)
-        co = build_coarse_op(sub, U, M5, mf, op_dtype=sub.dtype)
-        x, st = hdcr_solve(co, U, b, inner_dtype=sub.dtype, **solve_kw)
-        ctx.lat, ctx.co, ctx.solve_kw, ctx.dtype = lat, co, solve_kw, sub.dtype
-        ctx.save_for_backward(U, x)
+        if U.dtype not in _AUTOGRAD_TOL or b.dtype != U.dtype:
+            raise TypeError("solve_autograd takes complex128 or complex64 links and source of one dtype")
+        x, st = _autograd_solve(lat, U, b, noise, M5, mf, block, filter_kw, solve_kw)
+        ctx.lat, ctx.M5, ctx.mf, ctx.block = lat, M5, mf, block
+        ctx.filter_kw, ctx.solve_kw = filter_kw, solve_kw
+        ctx.save_for_backward(U, x, noise)
         ctx.stats = st
         return x
 
     @staticmethod
     def backward(ctx, gx):
-        U, x = ctx.saved_tensors
-        y, _ = hdcr_solve(ctx.co, U, gx.contiguous(), inner_dtype=ctx.dtype, **ctx.solve_kw)
-        F = gauge_force(ctx.lat, x, apply_gamma5_r5(ctx.lat, y))
-        gU = F.conj().transpose(-1, -2).contiguous()
+        U, x, noise = ctx.saved_tensors
+        y, st = _autograd_solve(ctx.lat, U, gx.to(U.dtype), noise, ctx.M5, ctx.mf, ctx.block, ctx.filter_kw,
+                                ctx.solve_kw)
+        ctx.backward_stats = st
+        gU = gauge_grad(ctx.lat, x, apply_gamma5_r5(ctx.lat, y))
         return gU, y, None, None, None, None, None, None, None
 
 
 def solve_autograd(lat: Lattice, U: torch.Tensor, b: torch.Tensor, noise: torch.Tensor, M5: float, mf: float,
                    block, filter_kw: dict | None = None, solve_kw: dict | None = None) -> torch.Tensor:
-    """Differentiable HDCR solve: see HDCRSolve."""
+    """Differentiable HDCR solve: see HDCRSolve.  ``noise`` (nvec/2 complex128 fields)
+    seeds the subspace, rebuilt identically in the backward."""
     return HDCRSolve.apply(U, b, lat, noise, M5, mf, tuple(block), filter_kw or {}, solve_kw or {})

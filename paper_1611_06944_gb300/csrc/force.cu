@@ -7,7 +7,9 @@
 //   C_ba = sum_alpha [(1 + gamma_mu) x(x, s)]_{alpha b}    conj(w(x+mu, s)_{alpha a}),
 //
 // the t-boundary phase entering through x(x+mu) and w(x+mu).
-// One thread per link (mu, x4) sums over s and spin.
+// One thread per link (mu, x4) sums over s and spin.  With GRAD the kernel
+// stores the gradient of the loss with respect to the link instead:
+// conj(F_ba) at [a][b], i.e. dL/dRe U_ab + i dL/dIm U_ab.
 #include "dwf_stencil.cuh"
 
 namespace hdcr {
@@ -65,7 +67,7 @@ __device__ __forceinline__ void proj_full(const cpx<R>* __restrict__ p, int ls, 
   }
 }
 
-template <typename R>
+template <typename R, bool GRAD>
 __global__ void __launch_bounds__(128) force_kernel(Geom g, const cpx<R>* __restrict__ x,
                                                     const cpx<R>* __restrict__ w, cpx<R>* __restrict__ F) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,13 +124,19 @@ __global__ void __launch_bounds__(128) force_kernel(Geom g, const cpx<R>* __rest
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) st(out + 3 * b + a, cpx<R>((R)(sc * acc[b][a][0]), (R)(sc * acc[b][a][1])));
+    for (int a = 0; a < 3; ++a) {
+      if (GRAD)
+        st(out + 3 * a + b, cpx<R>((R)(sc * acc[b][a][0]), (R)(-sc * acc[b][a][1])));
+      else
+        st(out + 3 * b + a, cpx<R>((R)(sc * acc[b][a][0]), (R)(sc * acc[b][a][1])));
+    }
 }
 
-template <typename R>
+template <typename R, bool GRAD>
 int launch_force(const Geom& g, const void* x, const void* w, void* F, cudaStream_t st) {
   const long long n = 4LL * g.V4;
-  force_kernel<R><<<num_blocks(n, 128), 128, 0, st>>>(g, (const cpx<R>*)x, (const cpx<R>*)w, (cpx<R>*)F); count_launch();
+  force_kernel<R, GRAD><<<num_blocks(n, 128), 128, 0, st>>>(g, (const cpx<R>*)x, (const cpx<R>*)w, (cpx<R>*)F);
+  count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -137,16 +145,27 @@ int launch_force(const Geom& g, const void* x, const void* w, void* F, cudaStrea
 
 using namespace hdcr;
 
-extern "C" int hdcr_gauge_force(const hdcr_geom* gp, const void* x, const void* w, void* F, int dtype,
-                                void* stream) {
+template <bool GRAD>
+static int gauge_force_call(const char* name, const hdcr_geom* gp, const void* x, const void* w, void* F,
+                            int dtype, void* stream) {
   Geom g;
   HDCR_TRY(make_geom(gp, &g));
   if (!x || !w || !F) {
-    set_error("hdcr_gauge_force: null pointer");
+    set_error("%s: null pointer", name);
     return HDCR_ERR_BAD_ARG;
   }
-  if (dtype == HDCR_C128) return launch_force<double>(g, x, w, F, as_stream(stream));
-  if (dtype == HDCR_C64) return launch_force<float>(g, x, w, F, as_stream(stream));
-  set_error("hdcr_gauge_force: unknown dtype %d", dtype);
+  if (dtype == HDCR_C128) return launch_force<double, GRAD>(g, x, w, F, as_stream(stream));
+  if (dtype == HDCR_C64) return launch_force<float, GRAD>(g, x, w, F, as_stream(stream));
+  set_error("%s: unknown dtype %d", name, dtype);
   return HDCR_ERR_BAD_ARG;
+}
+
+extern "C" int hdcr_gauge_force(const hdcr_geom* gp, const void* x, const void* w, void* F, int dtype,
+                                void* stream) {
+  return gauge_force_call<false>("hdcr_gauge_force", gp, x, w, F, dtype, stream);
+}
+
+extern "C" int hdcr_gauge_grad(const hdcr_geom* gp, const void* x, const void* w, void* G, int dtype,
+                               void* stream) {
+  return gauge_force_call<true>("hdcr_gauge_grad", gp, x, w, G, dtype, stream);
 }

@@ -2,12 +2,17 @@
 // allocate device memory.
 //
 // hdcr_cdot keeps its partial sums in a buffer that the library allocates with
-// cudaMalloc on first use.  Some callers cannot let a library allocate: code
-// running while a CUDA graph is being captured (an allocation would break the
-// capture), callers that own a fixed memory budget through their own pool or
-// allocator, and callers inside a context whose allocations are forbidden after
-// start-up.  This entry point keeps its scratch in a fixed array compiled into
-// the library instead, so a call only launches kernels and sets one word.
+// cudaMalloc on first use.  Some callers cannot let a library allocate: callers
+// that hand all device memory to their own pool or allocator up front and keep
+// a fixed budget, and callers in a runtime that forbids allocations after
+// start-up (a cudaMalloc there fails or stalls the caller's other streams).
+// This entry point keeps its scratch in a fixed array compiled into the library
+// instead, so a call only launches kernels and sets one word.
+//
+// The device address of the array is looked up once per device and kept for
+// the life of the process; after a cudaDeviceReset (or any other destruction
+// of the device's primary context) that address is stale, so no call may
+// follow a device reset.
 //
 // Scratch: one FP64 (re, im) partial sum per block of NOALLOC_BLOCK complex
 // entries plus a completion counter, NOALLOC_MAX_BLOCKS blocks at most (1 MiB),

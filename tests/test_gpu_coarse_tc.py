@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import dev, host, links, relerr
+from gpu_util import dev, host, links, natural, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -99,3 +99,36 @@ def test_hdcr_solve_with_single_pass_coarse_op(hd):
     xg = natural(host(x), L, Ls)
     res = np.sqrt(dwf.norm2(b - dwf.apply_H(Uh, xg, 1.8, mf)) / dwf.norm2(b))
     assert st["status"] == 0 and res <= 1.01e-10
+
+
+# 8^4 x 4 with 4^4 blocks: K = 256 x 4 x 12 = 12288 per block (384 chunks of 32),
+# so every leg-0 projection is split over 24 CTAs and summed by the reduction
+# kernel; nvec 24 and 32 run the M = 64 variant, 48 and 64 the M = 128 one with
+# two tasks per thread.
+@pytest.mark.parametrize("nvec", [24, 32, 48, 64])
+def test_tensor_core_coarse_op_matches_oracle(hd, nvec):
+    """The FP32 tensor-core builds (three-pass and single-pass TF32) against
+    oracle.multigrid.coarse_op evaluated in FP64 on the same FP32-rounded basis,
+    leg by leg.  Bounds as derived in the tests above: three passes 1e-5 overall
+    and 1e-4 per leg; one pass 4e-3 overall and 1e-2 per leg."""
+    from oracle import multigrid as mg
+    L, Ls, block, bc, mf = (8, 8, 8, 8), 4, (4, 4, 4, 4), -1, 0.01
+    U = synth.gauge_field(L, 0.5, 5400 + nvec)
+    rng = synth.rng(5500 + nvec)
+    lat = hd.Lattice(L, Ls, bc)
+    shape = (nvec, lat.V4, 12, Ls)
+    v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    sub32 = hd.subspace_from_vectors(lat, block, dev(v), store_dtype=torch.complex64)
+    Ud = dev(links(U))
+    A3 = host(hd.build_coarse_op(sub32, Ud, 1.8, mf, op_dtype=torch.complex64).op())
+    A1 = host(hd.build_coarse_op(sub32, Ud, 1.8, mf, op_dtype=torch.complex64, fast=True).op())
+    # the oracle on the basis the GPU stored (FP32 values, evaluated in FP64)
+    g = mg.Geometry(L, Ls, block)
+    phi = natural(host(sub32.vectors()), L, Ls)
+    osub = mg.Subspace(g, mg.to_blocks(g, phi))
+    A = mg.coarse_op(U, osub, 1.8, mf, bc)
+    assert relerr(A3, A) < 1e-5
+    assert relerr(A1, A) < 4e-3
+    for leg in range(9):
+        assert relerr(A3[:, leg], A[:, leg]) < 1e-4
+        assert relerr(A1[:, leg], A[:, leg]) < 1e-2

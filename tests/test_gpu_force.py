@@ -1,5 +1,8 @@
 """GPU gauge force and the differentiable HDCR solve against the FP64 oracle and
 against central finite differences."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -31,6 +34,9 @@ def test_force_kernel_matches_oracle(hd, dtype, tol, L, Ls, bc):
     want = force.gauge_force(np.zeros((4,) + synth.lattice_shape(L) + (3, 3), complex),
                              natural(xd.astype(np.complex128), L, Ls), natural(wd.astype(np.complex128), L, Ls), bc)
     assert relerr(F, want.reshape(F.shape)) < tol
+    # the gradient layout: G[mu, x4, a, b] = conj(F_ba)
+    G = host(hd.gauge_grad(hd.Lattice(L, Ls, bc), dev(xd), dev(wd))).astype(np.complex128)
+    assert relerr(G, np.conj(np.swapaxes(want, -1, -2)).reshape(G.shape)) < tol
 
 
 def _loss_and_grad(hd, lat, U, b, eta, noise, block, nvec_kw):
@@ -111,3 +117,45 @@ def test_autograd_vs_finite_differences(hd):
         fd = (dloss(Up) - dloss(Um)) / (2 * h)
         an = np.trace(1j * T @ Ul[mu, x4] @ F[mu, x4]).real
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.abs(F).max()), (mu, x4, fd, an)
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "grad_8x8x8x16_ls8.json")
+
+
+@pytest.mark.parametrize("dtype,tol,bound", [("c128", 1e-12, 1e-6), ("c64", 1e-7, 1e-4)])
+def test_autograd_differentiation_workload_matches_oracle(hd, dtype, tol, bound):
+    """The differentiation workload (8^3 x 16, Ls = 8) in complex128 and complex64:
+    the backward's dL/dU and dL/db on a seeded sample of links and components against
+    the oracle's gradient from CR converged to 1e-13 (tests/golden, written by
+    make_grad_golden.py from the oracle alone).  complex64: inputs, outputs and the
+    force kernel in FP32, V-cycle in FP32, outer iteration in FP64 to 1e-7; the error
+    against the FP64 oracle is printed and must stay below 1e-4 (SURVEY's proposal for
+    the FP32 form); complex128 must agree to 1e-6."""
+    with open(GOLDEN) as f:
+        gd = json.load(f)
+    L, Ls, mf = tuple(gd["lattice"]), gd["Ls"], gd["mf"]
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    U = synth.gauge_field(L, gd["eps"], gd["seeds"]["U"])
+    b = synth.gaussian_fermion(L, Ls, gd["seeds"]["b"])
+    eta = synth.gaussian_fermion(L, Ls, gd["seeds"]["eta"])
+    noise = synth.gaussian_fermion(L, Ls, 6003, count=8)
+    lat = hd.Lattice(L, Ls, gd["bc_t"])
+    Ut = dev(links(U), tdt).requires_grad_(True)
+    bt = dev(planes(b), tdt).requires_grad_(True)
+    x = hd.solve_autograd(lat, Ut, bt, dev(planes(noise)), gd["M5"], mf, (4, 4, 4, 4),
+                          filter_kw=dict(kind="chebyshev", order=100),
+                          solve_kw=dict(tol=tol, max_outer=500))
+    assert x.dtype == tdt
+    loss = torch.vdot(dev(planes(eta), tdt).reshape(-1), x.reshape(-1)).real
+    loss.backward()
+    assert Ut.grad.dtype == tdt and bt.grad.dtype == tdt
+    gU = host(Ut.grad).astype(np.complex128)
+    gb = host(bt.grad).astype(np.complex128)
+    got = np.array([gU[mu, x4].reshape(-1) for mu, x4, _ in gd["links"]])
+    want = np.array([[complex(r, i) for r, i in v] for _, _, v in gd["links"]])
+    gotb = np.array([gb[x4, c, s] for x4, c, s, _, _ in gd["grad_b"]])
+    wantb = np.array([complex(r, i) for _, _, _, r, i in gd["grad_b"]])
+    eU, eb = relerr(got, want), relerr(gotb, wantb)
+    el = abs(float(loss.detach()) - gd["loss"]) / abs(gd["loss"])
+    print(f"{dtype}: gradient error vs FP64 oracle: dL/dU {eU:.2e}, dL/db {eb:.2e}, loss {el:.2e}")
+    assert eU < bound and eb < bound and el < bound

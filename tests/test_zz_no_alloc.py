@@ -1,8 +1,9 @@
 """The allocation-free inner product hdcr_cdot_noalloc, called through the C ABI.
 
-Callers that may not let the library allocate device memory (stream capture,
-caller-owned memory pools) use this entry point; its scratch is a fixed array
-inside the library.  It must give the same result as hdcr_cdot, call after call
+Callers that may not let the library allocate device memory (a caller that
+keeps all device memory in its own pool, a runtime that forbids allocations
+after start-up) use this entry point; its scratch is a fixed array inside the
+library.  It must give the same result as hdcr_cdot, call after call
 (the shared scratch keeps the previous call's contents, so a stale completion
 counter or partial sum would show up on the second call), and refuse sizes its
 scratch cannot hold.  This file is collected last on purpose.
