@@ -26,6 +26,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "dwf_tma.cuh"
 #include "dwf_x2.cuh"
 #include "reduce.cuh"
 
@@ -33,20 +34,22 @@ namespace hdcr {
 
 constexpr int X2_MAX_LP = 8;   // fifth-dimension pairs per 4d site (Ls <= 16)
 
-constexpr int X2_STORE = 0, X2_DOT = 1, X2_CHEB = 2;  // epilogues of the kernel
-
-// Chebyshev step of the epilogue X2_CHEB: out <- 2 (a H in + b cur) - out
-struct X2Cheb {
-  const cpx<float>* cur;
-  float a, b;
+// Neighbours of one pair for the shared hop order: spinors and links read
+// straight from global memory, indices from the CTA's staged site data.
+struct GlobalHops {
+  const cpx<float>* in;
+  const cpx<float>* U;
+  const int* nbs;
+  const int* lis;
+  const float* cfs;
+  int ls, s0;
+  __device__ __forceinline__ PairF32 nb(int d) const { return PairF32{in + (unsigned)(nbs[d] * 12 * ls + s0), ls}; }
+  __device__ __forceinline__ const cpx<float>* link(int d) const { return U + (unsigned)(lis[d] * 9); }
+  __device__ __forceinline__ float coef(int d) const { return cfs[d]; }
 };
 
-// One pass of H over the pair (x4, s0, s0+1) of one right-hand side.  The
-// epilogue EPI: X2_STORE writes H in; X2_DOT also adds Re <in, H in> of the
-// pair's output sites into *dot (products summed in FP32 within each spin half,
-// where the terms share the sign of Gamma5, and the two halves combined in
-// FP64, where they cancel); X2_CHEB writes the next Chebyshev term
-// 2 (a H in + b cur) - prev over prev (cur, prev read at the output sites).
+// One pass of H over the pair (x4, s0, s0+1) of one right-hand side, in the
+// shared order of dwf_x2.cuh, with the epilogue EPI (store_x2).
 template <int LS, int EPI, typename Stage>
 __device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __restrict__ U, const Stage& sm,
                                           int site, int x4, int p, float diag, float mf,
@@ -55,66 +58,29 @@ __device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __res
   const int ls = ls_of<LS>(g);
   const int s0 = 2 * p;
   const unsigned base = (unsigned)(x4 * 12 * ls);
-  const cpx<float>* self = in + base + s0;
   cx2 up[2][3], lo[2][3];
+  zero_acc(up, lo);
+  const GlobalHops h{in, U, sm.nb[site], sm.li[site], sm.coef[site], ls, s0};
+  hops_first(h, up, lo);
+  hops_second(h, up, lo);
   {
-    // diagonal and fifth-dimension terms, lane by lane:
-    //   upper(s) = diag psi(s) - w psi(s-1),  lower(s) = diag psi(s) - w psi(s+1)
+    const cpx<float>* self = in + base + s0;
     const bool wl = s0 == 0, wr = s0 + 2 == ls;
     const cpx<float>* prv = in + base + (wl ? ls - 1 : s0 - 1);
     const cpx<float>* nxt = in + base + (wr ? 0 : s0 + 2);
-    const float w0 = wl ? -mf : 1.f, w1 = wr ? -mf : 1.f;
+    float4 q[12];
+    cpx<float> pv[6], nv[6];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) q[c] = ld4(self + c * ls);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const float4 q = ld4(self + c * ls);
-      const cpx<float> v = ld(prv + c * ls);
-      const int sp = c / 3, cc = c % 3;
-      up[sp][cc].re = make_float2(fmaf(-w0, v.re, diag * q.x), fmaf(-1.f, q.x, diag * q.z));
-      up[sp][cc].im = make_float2(fmaf(-w0, v.im, diag * q.y), fmaf(-1.f, q.y, diag * q.w));
+      pv[c] = ld(prv + c * ls);
+      nv[c] = ld(nxt + (c + 6) * ls);
     }
-#pragma unroll
-    for (int c = 6; c < 12; ++c) {
-      const float4 q = ld4(self + c * ls);
-      const cpx<float> v = ld(nxt + c * ls);
-      const int sp = c / 3 - 2, cc = c % 3;
-      // negated lower: psi(s+1) - diag psi(s)
-      lo[sp][cc].re = make_float2(fmaf(-diag, q.x, q.z), fmaf(-diag, q.z, w1 * v.re));
-      lo[sp][cc].im = make_float2(fmaf(-diag, q.y, q.w), fmaf(-diag, q.w, w1 * v.im));
-    }
+    local_x2(q, pv, nv, wl ? -mf : 1.f, wr ? -mf : 1.f, diag, up, lo);
   }
-  const int* nbs = sm.nb[site];
-  const float* cfs = sm.coef[site];
-  hop_x2<0, +1>(U + (unsigned)(sm.li[site][0] * 9), PairF32{in + (unsigned)(nbs[0] * 12 * ls + s0), ls}, cfs[0], up, lo);
-  hop_x2<0, -1>(U + (unsigned)(sm.li[site][1] * 9), PairF32{in + (unsigned)(nbs[1] * 12 * ls + s0), ls}, cfs[1], up, lo);
-  hop_x2<1, +1>(U + (unsigned)(sm.li[site][2] * 9), PairF32{in + (unsigned)(nbs[2] * 12 * ls + s0), ls}, cfs[2], up, lo);
-  hop_x2<1, -1>(U + (unsigned)(sm.li[site][3] * 9), PairF32{in + (unsigned)(nbs[3] * 12 * ls + s0), ls}, cfs[3], up, lo);
-  hop_x2<2, +1>(U + (unsigned)(sm.li[site][4] * 9), PairF32{in + (unsigned)(nbs[4] * 12 * ls + s0), ls}, cfs[4], up, lo);
-  hop_x2<2, -1>(U + (unsigned)(sm.li[site][5] * 9), PairF32{in + (unsigned)(nbs[5] * 12 * ls + s0), ls}, cfs[5], up, lo);
-  hop_x2<3, +1>(U + (unsigned)(sm.li[site][6] * 9), PairF32{in + (unsigned)(nbs[6] * 12 * ls + s0), ls}, cfs[6], up, lo);
-  hop_x2<3, -1>(U + (unsigned)(sm.li[site][7] * 9), PairF32{in + (unsigned)(nbs[7] * 12 * ls + s0), ls}, cfs[7], up, lo);
-  // out(Ls-1-s) = gamma5 acc(s): the pair lands at Ls-2-s0 with its lanes swapped
   const unsigned ob = base + (unsigned)(ls - 2 - s0);
-  float d[2] = {0.f, 0.f};  // upper and lower spins summed apart: no cancellation within either
-#pragma unroll
-  for (int c = 0; c < 12; ++c) {
-    const cx2 v = c < 6 ? up[c / 3][c % 3] : lo[c / 3 - 2][c % 3];
-    float4 o = make_float4(v.re.y, v.im.y, v.re.x, v.im.x);
-    if constexpr (EPI == X2_CHEB) {
-      const float4 cv = ld4(ch.cur + ob + c * ls), pv = ld4(out + ob + c * ls);
-      o = make_float4(2.f * fmaf(ch.a, o.x, ch.b * cv.x) - pv.x, 2.f * fmaf(ch.a, o.y, ch.b * cv.y) - pv.y,
-                      2.f * fmaf(ch.a, o.z, ch.b * cv.z) - pv.z, 2.f * fmaf(ch.a, o.w, ch.b * cv.w) - pv.w);
-    }
-    *reinterpret_cast<float4*>(out + ob + c * ls) = o;
-    if (EPI == X2_DOT) {
-      const float4 a = ld4(in + ob + c * ls);
-      float& e = d[c < 6 ? 0 : 1];
-      e = fmaf(a.x, o.x, e);
-      e = fmaf(a.y, o.y, e);
-      e = fmaf(a.z, o.z, e);
-      e = fmaf(a.w, o.w, e);
-    }
-  }
-  if (EPI == X2_DOT) *dot += (double)d[0] + (double)d[1];
+  *dot += store_x2<EPI>(up, lo, out + ob, in + ob, EPI == X2_CHEB ? ch.cur + ob : nullptr, ch.a, ch.b, ls);
 }
 
 // blockDim = T::sites * Ls/2: thread (site, p) = (tid / (Ls/2), tid % (Ls/2)).
@@ -165,7 +131,10 @@ __global__ void __launch_bounds__(T::sites * 8, 64 / T::sites) g5dwf_x2_kernel(
   V(3, 32, 0, 0, 0)        \
   V(4, 16, 2, 1, 1)        \
   V(5, 16, 4, 1, 1)
-constexpr int X2_VARIANTS = 6;
+constexpr int X2_L1_VARIANTS = 6;
+// variants X2_L1_VARIANTS.. are the shared-memory (TMA-staged) kernel of dwf_tma.cu,
+// one per column shape
+constexpr int X2_VARIANTS = X2_L1_VARIANTS + TMA_SHAPES;
 
 template <int EPI, typename T>
 static void x2_launch(const Geom& g, int blocks, float diag, float mf, const cpx<float>* U, const cpx<float>* in,
@@ -185,8 +154,13 @@ static void x2_launch(const Geom& g, int blocks, float diag, float mf, const cpx
   count_launch();
 }
 
-// Whether variant v applies to the lattice, its tile count, and a launch of it.
-static bool x2_variant_fits(int v, const Geom& g, int* tiles, int* sites) {
+// Whether variant v applies to the lattice (and the fields' alignment), its tile
+// count, and a launch of it.
+static bool x2_variant_fits(int v, const Geom& g, const void* in, const void* out, int* tiles, int* sites) {
+  if (v >= X2_L1_VARIANTS) {
+    *tiles = *sites = 0;
+    return tma_shape_fits(v - X2_L1_VARIANTS, g, in, out);
+  }
   switch (v) {
 #define HDCR_X2_FITS(K, A, B, C, D)        \
   case K: {                               \
@@ -203,9 +177,11 @@ static bool x2_variant_fits(int v, const Geom& g, int* tiles, int* sites) {
 }
 
 template <int EPI>
-static void x2_launch_variant(int v, const Geom& g, int blocks, float diag, float mf, const cpx<float>* U,
-                              const cpx<float>* in, cpx<float>* out, int nrhs, RedScratch rs, double* result,
-                              X2Cheb ch, cudaStream_t st) {
+static int x2_launch_variant(int v, const Geom& g, int blocks, float diag, float mf, const cpx<float>* U,
+                             const cpx<float>* in, cpx<float>* out, int nrhs, RedScratch rs, double* result,
+                             X2Cheb ch, cudaStream_t st) {
+  if (v >= X2_L1_VARIANTS)
+    return launch_g5dwf_tma(v - X2_L1_VARIANTS, EPI, g, diag, mf, U, in, out, nrhs, rs, result, ch, st);
   switch (v) {
 #define HDCR_X2_CASE(K, A, B, C, D)                                                            \
   case K:                                                                                      \
@@ -216,6 +192,7 @@ static void x2_launch_variant(int v, const Geom& g, int blocks, float diag, floa
     default:
       break;
   }
+  return HDCR_OK;
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -269,9 +246,13 @@ static int x2_tune(const Geom& g, float diag, float mf, const cpx<float>* U, con
   for (int v = 0; v < X2_VARIANTS && status == HDCR_OK; ++v) {
     int tiles, sites;
     e->us[v] = -1.f;
-    if (!x2_variant_fits(v, g, &tiles, &sites)) continue;
+    if (!x2_variant_fits(v, g, in, out, &tiles, &sites)) continue;
     constexpr int reps = 3;
-    x2_launch_variant<X2_STORE>(v, g, tiles, diag, mf, U, in, out, nrhs, none, nullptr, nc, st);  // warm
+    // a variant that cannot be launched here (e.g. no tensor-map support) is skipped
+    if (x2_launch_variant<X2_STORE>(v, g, tiles, diag, mf, U, in, out, nrhs, none, nullptr, nc, st) != HDCR_OK) {
+      cudaGetLastError();
+      continue;
+    }
     cudaEventRecord(a, st);
     for (int r = 0; r < reps; ++r)
       x2_launch_variant<X2_STORE>(v, g, tiles, diag, mf, U, in, out, nrhs, none, nullptr, nc, st);
@@ -284,11 +265,24 @@ static int x2_tune(const Geom& g, float diag, float mf, const cpx<float>* U, con
       status = cuda_status(err, "stencil autotune");
       break;
     }
+    if (v >= X2_L1_VARIANTS) {  // a shared-memory variant whose copies timed out is not used
+      int flag = 0;
+      status = tma_take_timeouts(&flag);
+      if (status != HDCR_OK) break;
+      if (flag) continue;
+    }
     e->us[v] = ms * 1e3f / reps;
     if (e->us[v] < best) {
       best = e->us[v];
       e->variant = v;
     }
+  }
+  // every variant wrote ``out``; rewrite it with the chosen one (the variants agree bit for
+  // bit, but a dropped variant may have left it half written)
+  if (status == HDCR_OK) {
+    int tiles, sites;
+    x2_variant_fits(e->variant, g, in, out, &tiles, &sites);
+    status = x2_launch_variant<X2_STORE>(e->variant, g, tiles, diag, mf, U, in, out, nrhs, none, nullptr, nc, st);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -302,7 +296,7 @@ static int x2_pick(const Geom& g, float diag, float mf, const cpx<float>* U, con
   *variant = 0;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (g_force_variant >= 0) {
-    if (x2_variant_fits(g_force_variant, g, &tiles, &sites)) *variant = g_force_variant;
+    if (x2_variant_fits(g_force_variant, g, in, out, &tiles, &sites)) *variant = g_force_variant;
     return HDCR_OK;
   }
   if (!g_tune_mode) return HDCR_OK;
@@ -333,13 +327,16 @@ int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, co
   const X2Cheb none_ch{nullptr, 0.f, 0.f};
   int v, tiles, sites;
   HDCR_TRY(x2_pick(g, diag, fmf, U, in, out, nrhs, true, st, &v));
-  x2_variant_fits(v, g, &tiles, &sites);
+  if (!x2_variant_fits(v, g, in, out, &tiles, &sites)) {  // a tuned shared-memory variant, misaligned fields
+    v = 0;
+    x2_variant_fits(v, g, in, out, &tiles, &sites);
+  }
   if (rs) {
     const int blocks = tiles < RED_MAX_BLOCKS ? tiles : RED_MAX_BLOCKS;
-    x2_launch_variant<X2_DOT>(v, g, blocks, diag, fmf, U, in, out, nrhs, *rs, result, none_ch, st);
+    HDCR_TRY(x2_launch_variant<X2_DOT>(v, g, blocks, diag, fmf, U, in, out, nrhs, *rs, result, none_ch, st));
   } else {
     RedScratch none{nullptr, nullptr};
-    x2_launch_variant<X2_STORE>(v, g, tiles, diag, fmf, U, in, out, nrhs, none, nullptr, none_ch, st);
+    HDCR_TRY(x2_launch_variant<X2_STORE>(v, g, tiles, diag, fmf, U, in, out, nrhs, none, nullptr, none_ch, st));
   }
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
@@ -350,9 +347,13 @@ int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* 
   const float diag = (float)(5.0 - M5), fmf = (float)mf;
   int v, tiles, sites;
   HDCR_TRY(x2_pick(g, diag, fmf, U, in, prev, nrhs, false, st, &v));  // prev is read: no tuning here
-  x2_variant_fits(v, g, &tiles, &sites);
+  if (!x2_variant_fits(v, g, in, prev, &tiles, &sites)) {
+    v = 0;
+    x2_variant_fits(v, g, in, prev, &tiles, &sites);
+  }
   RedScratch none{nullptr, nullptr};
-  x2_launch_variant<X2_CHEB>(v, g, tiles, diag, fmf, U, in, prev, nrhs, none, nullptr, X2Cheb{cur, a, b}, st);
+  HDCR_TRY(x2_launch_variant<X2_CHEB>(v, g, tiles, diag, fmf, U, in, prev, nrhs, none, nullptr, X2Cheb{cur, a, b},
+                                      st));
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }

@@ -17,6 +17,7 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 __device__ __forceinline__ float4 ld4(const cpx<float>* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
@@ -135,6 +136,100 @@ __device__ __forceinline__ void hop_x2(const cpx<float>* __restrict__ L, const P
       lo[1][c].im = fma2(gn, b.re, lo[1][c].im);
     }
   }
+}
+
+// The order in which every FP32 kernel variant adds up one output pair, so that
+// all variants give the same bits: first the hops y+, y-, z+, z-, t- (the ones the
+// shared-memory kernel reads from its halo and its previous plane), then x+, x-,
+// t+, then the diagonal and fifth-dimension terms.  NB(d) is the accessor of the
+// neighbour pair of hop d = 2 mu + (0 forward, 1 backward), LK(d) its link and
+// CF(d) its factor -1/2 times the boundary phase.
+template <class Hop>
+__device__ __forceinline__ void hops_first(const Hop& h, cx2 (&up)[2][3], cx2 (&lo)[2][3]) {
+  hop_x2<1, +1>(h.link(2), h.nb(2), h.coef(2), up, lo);
+  hop_x2<1, -1>(h.link(3), h.nb(3), h.coef(3), up, lo);
+  hop_x2<2, +1>(h.link(4), h.nb(4), h.coef(4), up, lo);
+  hop_x2<2, -1>(h.link(5), h.nb(5), h.coef(5), up, lo);
+  hop_x2<3, -1>(h.link(7), h.nb(7), h.coef(7), up, lo);
+}
+template <class Hop>
+__device__ __forceinline__ void hops_second(const Hop& h, cx2 (&up)[2][3], cx2 (&lo)[2][3]) {
+  hop_x2<0, +1>(h.link(0), h.nb(0), h.coef(0), up, lo);
+  hop_x2<0, -1>(h.link(1), h.nb(1), h.coef(1), up, lo);
+  hop_x2<3, +1>(h.link(6), h.nb(6), h.coef(6), up, lo);
+}
+
+__device__ __forceinline__ void zero_acc(cx2 (&up)[2][3], cx2 (&lo)[2][3]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      up[sp][c].re = up[sp][c].im = lo[sp][c].re = lo[sp][c].im = make_float2(0.f, 0.f);
+    }
+}
+
+// Adds the diagonal and fifth-dimension terms of the pair (s0, s0+1), lane by lane:
+//   upper(s) += diag psi(s) - w psi(s-1),  lower(s) += diag psi(s) - w psi(s+1)
+// (the lower accumulated negated, i.e. with the Gamma5 sign).  q[c]: the pair's
+// component c as (re_s0, im_s0, re_s0+1, im_s0+1); prv[c] = psi(s0-1) for the
+// upper components c < 6 with weight w0, nxt[c] = psi(s0+2) for the lower ones
+// c >= 6 (index c - 6) with weight w1 (1, or -mf at a wall).
+__device__ __forceinline__ void local_x2(const float4 (&q)[12], const cpx<float> (&prv)[6],
+                                         const cpx<float> (&nxt)[6], float w0, float w1, float diag,
+                                         cx2 (&up)[2][3], cx2 (&lo)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int sp = c / 3, cc = c % 3;
+    up[sp][cc].re = add2(up[sp][cc].re, make_float2(fmaf(-w0, prv[c].re, diag * q[c].x), fmaf(-1.f, q[c].x, diag * q[c].z)));
+    up[sp][cc].im = add2(up[sp][cc].im, make_float2(fmaf(-w0, prv[c].im, diag * q[c].y), fmaf(-1.f, q[c].y, diag * q[c].w)));
+  }
+#pragma unroll
+  for (int c = 6; c < 12; ++c) {
+    const int sp = c / 3 - 2, cc = c % 3;
+    lo[sp][cc].re = add2(lo[sp][cc].re, make_float2(fmaf(-diag, q[c].x, q[c].z), fmaf(-diag, q[c].z, w1 * nxt[c - 6].re)));
+    lo[sp][cc].im = add2(lo[sp][cc].im, make_float2(fmaf(-diag, q[c].y, q[c].w), fmaf(-diag, q[c].w, w1 * nxt[c - 6].im)));
+  }
+}
+
+constexpr int X2_STORE = 0, X2_DOT = 1, X2_CHEB = 2;  // epilogues of the kernels
+
+// Chebyshev step of the epilogue X2_CHEB: out <- 2 (a H in + b cur) - out
+struct X2Cheb {
+  const cpx<float>* cur;
+  float a, b;
+};
+
+// Writes the pair to its output sites: out(Ls-1-s) = gamma5 acc(s), i.e. the pair
+// at Ls-2-s0 with its lanes swapped; o, i and cur point at that output pair of
+// out, in and ch.cur (component stride ls).  X2_DOT returns Re <in, H in> of the
+// two output sites (products summed in FP32 within each spin half, where the
+// terms share the sign of Gamma5, the halves combined in FP64); X2_CHEB writes
+// 2 (a H in + b cur) - prev over prev = out.
+template <int EPI>
+__device__ __forceinline__ double store_x2(const cx2 (&up)[2][3], const cx2 (&lo)[2][3], cpx<float>* o,
+                                           const cpx<float>* i, const cpx<float>* cur, float ca, float cb,
+                                           int ls) {
+  float d[2] = {0.f, 0.f};
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const cx2 v = c < 6 ? up[c / 3][c % 3] : lo[c / 3 - 2][c % 3];
+    float4 r = make_float4(v.re.y, v.im.y, v.re.x, v.im.x);
+    if constexpr (EPI == X2_CHEB) {
+      const float4 cv = ld4(cur + c * ls), pv = ld4(o + c * ls);
+      r = make_float4(2.f * fmaf(ca, r.x, cb * cv.x) - pv.x, 2.f * fmaf(ca, r.y, cb * cv.y) - pv.y,
+                      2.f * fmaf(ca, r.z, cb * cv.z) - pv.z, 2.f * fmaf(ca, r.w, cb * cv.w) - pv.w);
+    }
+    *reinterpret_cast<float4*>(o + c * ls) = r;
+    if (EPI == X2_DOT) {
+      const float4 a = ld4(i + c * ls);
+      float& e = d[c < 6 ? 0 : 1];
+      e = fmaf(a.x, r.x, e);
+      e = fmaf(a.y, r.y, e);
+      e = fmaf(a.z, r.z, e);
+      e = fmaf(a.w, r.w, e);
+    }
+  }
+  return EPI == X2_DOT ? (double)d[0] + (double)d[1] : 0.0;
 }
 
 // Per-CTA data: for each of the SITES 4d sites of the CTA's tile and each hop

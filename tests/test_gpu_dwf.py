@@ -176,7 +176,7 @@ def test_fp32_tile_variants_identical(hd, Ls):
     want = dwf.apply_H(Ur, natural(host(p32).astype(np.complex128), L, Ls), 1.8, 0.01, -1)
     outs = []
     try:
-        for v in range(6):
+        for v in range(7):
             hd.stencil_tune(1, v)
             outs.append(host(hd.apply_g5dwf(lat, U32, p32, 1.8, 0.01)))
         hd.stencil_tune(2, -1)
@@ -188,6 +188,7 @@ def test_fp32_tile_variants_identical(hd, Ls):
     for v, o in enumerate(outs):
         assert np.array_equal(o, outs[0]), f"tile variant {v} differs"
     assert np.array_equal(tuned, outs[0])
-    assert 0 <= info["variant"] < 6 and info["us"][info["variant"]] > 0
+    assert 0 <= info["variant"] < 7 and info["us"][info["variant"]] > 0
     assert all(u > 0 for u in info["us"][:6])  # every tile divides this lattice
-    assert all(u == -1 for u in info["us"][6:])
+    assert info["us"][6] > 0                   # the shared-memory column 16 x 4 x 2 fits too
+    assert all(u == -1 for u in info["us"][7:])
