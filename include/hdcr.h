@@ -11,7 +11,14 @@
  *    calling host thread.
  *  - Field pointers are DEVICE pointers owned by the caller (e.g. the data of
  *    a torch tensor) unless a parameter says otherwise.  The library never
- *    frees them.  Handles (hdcr_subspace*, hdcr_coarse*) are owned by the
+ *    frees them.  hdcr_build_subspace, hdcr_build_coarse_op, hdcr_solve,
+ *    hdcr_apply_gamma5_r5, hdcr_gauge_force and hdcr_gauge_grad also accept
+ *    HOST pointers for their links and fields (pinned or pageable, told apart
+ *    by cudaPointerGetAttributes): the call stages each host argument through
+ *    a stream-ordered device buffer, copying inputs in before the work and
+ *    outputs back after it on ``stream``; with pinned memory the copies are
+ *    asynchronous, so synchronise the stream before reading a host output of
+ *    an asynchronous call (hdcr_solve synchronises itself).  Handles (hdcr_subspace*, hdcr_coarse*) are owned by the
  *    library: create and destroy them in pairs.
  *  - ``stream`` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls are asynchronous on that stream unless stated otherwise;
@@ -122,6 +129,12 @@ int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites);
  * CUDA events on ``stream`` and *tflops receives 2 x FMAs / second / 1e12.
  * Synchronises ``stream``.  Errors: BAD_ARG, CUDA. */
 int hdcr_probe_fma_rate(int dtype, double* tflops, void* stream);
+/* The coarse level's complex FP32 GEMMs (the rank-128 updates of the dense coarse
+ * inverse, its application to several right-hand sides) run on the tensor cores
+ * through cuBLAS's FP32 emulation on BF16 (three BF16 parts per operand, FP32
+ * accumulation).  Diagnostic: how many such GEMMs the process issued, and how many
+ * of them cuBLAS declined on that path and ran in plain FP32 instead. */
+int hdcr_tc_gemm_info(unsigned long long* calls, unsigned long long* fallbacks);
 
 /* ---------------------------------------------------------------- fine operator
  * hdcr_apply_g5dwf: out = H in with H = Gamma5 D_dwf = gamma5 R5 D_dwf

@@ -87,12 +87,20 @@ def probe_fma_rate(dtype: torch.dtype = torch.complex128, stream=None) -> float:
     return r.value
 
 
+def tc_gemm_info() -> dict:
+    """Coarse-level tensor-core GEMMs issued so far, and those that fell back to plain FP32."""
+    c = ctypes.c_ulonglong()
+    f = ctypes.c_ulonglong()
+    _check(_L.hdcr_tc_gemm_info(ctypes.byref(c), ctypes.byref(f)), "tc_gemm_info")
+    return {"calls": c.value, "fallbacks": f.value}
+
+
 def load_library():
     """Load libhdcr.so now (raises ImportError if it has not been built)."""
     return _L.hdcr_version()
 
 __all__ = [
-    "HDCRError", "Lattice", "probe_fma_rate", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
+    "HDCRError", "Lattice", "probe_fma_rate", "tc_gemm_info", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info",
     "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
@@ -149,8 +157,10 @@ def _code(t: torch.Tensor) -> int:
     raise TypeError(f"unsupported dtype {t.dtype}; use complex128 or complex64")
 
 
-def _dev(t: torch.Tensor, name: str) -> int:
-    if not t.is_cuda:
+def _dev(t: torch.Tensor, name: str, host_ok: bool = False) -> int:
+    """Pointer of a contiguous CUDA tensor; with host_ok also of a CPU tensor, for the
+    entry points that stage host buffers through the device themselves."""
+    if not t.is_cuda and not (host_ok and t.device.type == "cpu"):
         raise ValueError(f"{name} must be a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
@@ -251,7 +261,7 @@ def apply_gamma5_r5(lat: Lattice, psi: torch.Tensor, out: torch.Tensor | None = 
     n = _nfields(lat, psi, "psi")
     out = torch.empty_like(psi) if out is None else out
     g = lat.c_geom()
-    _check(_L.hdcr_apply_gamma5_r5(C_ref(g), _dev(psi, "psi"), _dev(out, "out"), _code(psi), n,
+    _check(_L.hdcr_apply_gamma5_r5(C_ref(g), _dev(psi, "psi", True), _dev(out, "out", True), _code(psi), n,
                                    _stream(stream)), "apply_gamma5_r5")
     return out
 
@@ -443,9 +453,9 @@ def build_subspace(lat: Lattice, U: torch.Tensor, noise: torch.Tensor, M5: float
     h = ctypes.c_void_p()
     g = lat.c_geom()
     p = _params(M5, mf)
-    _check(_L.hdcr_build_subspace(C_ref(g), C_ref(p), _dev(U, "U"), _dev(noise, "noise"), C_ref(sp),
+    _check(_L.hdcr_build_subspace(C_ref(g), C_ref(p), _dev(U, "U", True), _dev(noise, "noise", True), C_ref(sp),
                                   _stream(stream), ctypes.byref(h)), "build_subspace")
-    return Subspace(h, lat, block, 2 * half, store_dtype, U.device)
+    return Subspace(h, lat, block, 2 * half, store_dtype, torch.device("cuda", torch.cuda.current_device()))
 
 
 def subspace_from_vectors(lat: Lattice, block, vectors: torch.Tensor,
@@ -529,7 +539,7 @@ def build_coarse_op(sub: Subspace, U: torch.Tensor, M5: float, mf: float,
     h = ctypes.c_void_p()
     p = _params(M5, mf)
     code = _lib.HDCR_C128 if op_dtype == torch.complex128 else (_lib.HDCR_C64_FAST if fast else _lib.HDCR_C64)
-    _check(_L.hdcr_build_coarse_op(sub.handle, C_ref(p), _dev(U, "U"), code, _stream(stream),
+    _check(_L.hdcr_build_coarse_op(sub.handle, C_ref(p), _dev(U, "U", True), code, _stream(stream),
                                    ctypes.byref(h)), "build_coarse_op")
     return CoarseOperator(h, sub, op_dtype, M5, mf)
 
@@ -589,8 +599,8 @@ def hdcr_solve_into(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x: tor
     prm = _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi,
                         coarse_solver, coarse_tol, coarse_max, inner_dtype)
     st = _lib.hdcr_solve_stats()
-    status = _L.hdcr_solve(co.handle, _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), C_ref(prm), C_ref(st),
-                           _stream(stream))
+    status = _L.hdcr_solve(co.handle, _dev(U, "U", True), _dev(b, "b", True), _dev(x, "x", True), C_ref(prm),
+                           C_ref(st), _stream(stream))
     d = st.as_dict()
     d["status"] = status
     return d
@@ -613,8 +623,8 @@ def hdcr_solve(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x0: torch.T
     prm = _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi,
                         coarse_solver, coarse_tol, coarse_max, inner_dtype)
     st = _lib.hdcr_solve_stats()
-    _check(_L.hdcr_solve(co.handle, _dev(U, "U"), _dev(b, "b"), _dev(x, "x"), C_ref(prm), C_ref(st),
-                         _stream(stream)), "hdcr_solve")
+    _check(_L.hdcr_solve(co.handle, _dev(U, "U", True), _dev(b, "b", True), _dev(x, "x", True), C_ref(prm),
+                         C_ref(st), _stream(stream)), "hdcr_solve")
     return x, st.as_dict()
 
 
@@ -646,7 +656,7 @@ def gauge_force(lat: Lattice, x: torch.Tensor, w: torch.Tensor, stream=None) -> 
         raise ValueError("x and w must be single fields of one dtype")
     F = torch.empty((4, lat.V4, 3, 3), dtype=x.dtype, device=x.device)
     g = lat.c_geom()
-    _check(_L.hdcr_gauge_force(C_ref(g), _dev(x, "x"), _dev(w, "w"), F.data_ptr(), _code(x),
+    _check(_L.hdcr_gauge_force(C_ref(g), _dev(x, "x", True), _dev(w, "w", True), F.data_ptr(), _code(x),
                                _stream(stream)), "gauge_force")
     return F
 

@@ -88,6 +88,7 @@ SIGNATURES = {
     "hdcr_stencil_timer_read": (_I, [_I, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "hdcr_stencil_timer_count": (_I, [_I, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "hdcr_probe_fma_rate": (_I, [_I, C.POINTER(C.c_double), _P]),
+    "hdcr_tc_gemm_info": (_I, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
     "hdcr_apply_g5dwf": (_I, [_G, _DP, _P, _P, _P, _I, _I, _P]),
     "hdcr_stencil_tune": (_I, [_I, _I]),
     "hdcr_mobius_to_shamir": (_I, [_DP, _D, _P, _P, _I, _SZ, _DP, _P]),

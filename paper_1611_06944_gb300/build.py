@@ -80,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     same_arch = os.path.exists(stamp) and open(stamp).read().strip() == platform.machine()
     if force or jobs or not same_arch or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + ".tmp"
-        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lcublas"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -20,6 +20,7 @@
 // are both kept.
 #include <algorithm>
 
+#include "host_io.cuh"
 #include "coarse.cuh"
 #include "coarse_tc.cuh"
 #include "dwf_stencil.cuh"
@@ -625,8 +626,8 @@ static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>
 
 using namespace hdcr;
 
-extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_params* p, const void* U,
-                                    int op_dtype, void* stream, hdcr_coarse** out) {
+static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params* p, const void* U,
+                                 int op_dtype, void* stream, hdcr_coarse** out) {
   HDCR_TRY(subspace_check(sub));
   if (!p || !U || !out) {
     set_error("hdcr_build_coarse_op: null pointer");
@@ -817,5 +818,14 @@ extern "C" void hdcr_coarse_destroy(hdcr_coarse* co) {
   if (co->A) cudaFree(co->A);
   if (co->nbr) cudaFree(co->nbr);
   if (co->Ainv) cudaFree(co->Ainv);
+  if (co->dws) cudaFree(co->dws);
   delete co;
+}
+
+extern "C" int hdcr_build_coarse_op(const hdcr_subspace* sub, const hdcr_dwf_params* p, const void* U,
+                                    int op_dtype, void* stream, hdcr_coarse** out) {
+  HDCR_TRY(subspace_check(sub));
+  Staged su;  // links given in host memory are staged through the device
+  HDCR_TRY(su.in(U, (size_t)sub->g.V4 * 36 * 16, as_stream(stream)));
+  return build_coarse_op_entry(sub, p, su.ptr(), op_dtype, stream, out);
 }

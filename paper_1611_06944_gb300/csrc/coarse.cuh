@@ -79,6 +79,8 @@ struct hdcr_coarse {
   void* A;      // [Vc][9][nvec][nvec]
   int* nbr;     // [Vc][9] coarse site reached by each leg
   void* Ainv;   // dense inverse (FP32 complex, n = Vc*nvec, n x n) then its column gather index (n ints)
+  void* dws;    // workspace of the multi-right-hand-side dense solve (grown on demand)
+  size_t dws_bytes;
   double M5, mf;
   int device;
 };
@@ -107,6 +109,9 @@ struct CoarseOp {
 
 int coarse_check(const hdcr_coarse* co);
 int coarse_invert(hdcr_coarse* co, cudaStream_t st);
+// makes the dense solve of nrhs right-hand sides ready to run without allocating
+// (workspace and cuBLAS handle); call outside a stream capture
+int dense_solve_prepare(hdcr_coarse* co, int nrhs);
 template <typename R>
 int launch_dense_solve(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st);
 void solve_cache_release(const hdcr_coarse* co);  // frees the cached solve workspace

@@ -15,15 +15,21 @@
 // col_j <- (I + U K^T) col_j, K^T selecting the panel's rows and U (n x P)
 // accumulating the u_k (with later interchanges applied to its rows).  The P
 // steps on the panel's own columns run as one grid-wide launch each (a thread
-// per row; the last CTA to finish also picks the next pivot), then a tiled
-// complex GEMM applies the rank-P update to all other columns.  The row
-// interchanges amount to a permutation of the inverse's columns, which the
-// matrix-vector product applies as a gather of the input vector.
+// per row; the last CTA to finish also picks the next pivot), then the rank-P
+// update of all other columns is one complex GEMM on the tensor cores
+// (coarse_gemm.cuh: cuBLAS, FP32 emulated on BF16 tensor cores).  The panel is
+// wide (P = 128) so that the update's K is long enough for the tensor cores and
+// the n/P passes over the matrix stay few.  The row interchanges amount to a
+// permutation of the inverse's columns, which the matrix-vector product applies
+// as a gather of the input vector; for several right-hand sides the vectors are
+// gathered once and multiplied by the matrix in one GEMM, which reads the
+// matrix once.
 #include <climits>
 #include <utility>
 #include <vector>
 
 #include "coarse.cuh"
+#include "coarse_gemm.cuh"
 
 namespace hdcr {
 
@@ -48,8 +54,7 @@ __global__ void assemble_dense_kernel(const cpx<float>* __restrict__ A, const in
   }
 }
 
-constexpr int GJ_P = 32;      // panel width
-constexpr int GJ_TILE = 64;   // tile of the rank-P update (rows and columns)
+constexpr int GJ_P = 128;     // panel width
 constexpr int GJ_ROWS = 64;   // rows (threads) per CTA of the panel kernels
 constexpr int GJ_MAX_N = 32768;
 constexpr int GJ_MAX_CTAS = GJ_MAX_N / GJ_ROWS;
@@ -169,11 +174,11 @@ __global__ void __launch_bounds__(GJ_ROWS) gj_step_kernel(int n, int k0, int l, 
   cpx<float>* __restrict__ Wout = odd ? w.W[0] : w.W[1];
   cpx<float>* __restrict__ Uout = odd ? w.U[0] : w.U[1];
   const int t = threadIdx.x;
-  if (t < GJ_P) {
-    rk[t] = Win[(long long)t * n + p];
-    ruk[t] = Uin[(long long)t * n + p];
-    rp[t] = Win[(long long)t * n + k];
-    rup[t] = Uin[(long long)t * n + k];
+  for (int c = t; c < GJ_P; c += GJ_ROWS) {  // the panel may be wider than the CTA
+    rk[c] = Win[(long long)c * n + p];
+    ruk[c] = Uin[(long long)c * n + p];
+    rp[c] = Win[(long long)c * n + k];
+    rup[c] = Uin[(long long)c * n + k];
   }
   __syncthreads();
   const cpx<float> d = rk[l];
@@ -221,85 +226,33 @@ __global__ void __launch_bounds__(GJ_ROWS) gj_step_kernel(int n, int k0, int l, 
   if (l + 1 < pw) pivot_select(m, bi, k + 1, w);
 }
 
-// End of a panel: the panel's row interchanges on every column outside it (a
-// thread per column applies them in order), the panel's rows copied to T, and
-// the eliminated panel columns written back into M.
-__global__ void gj_panel_apply_kernel(cpx<float>* __restrict__ M, int n, int k0, int pw,
-                                      const cpx<float>* __restrict__ Wfin, GJWork w) {
-  const long long total = (long long)n + (long long)n * pw;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    if (e < n) {
-      const int j = (int)e;
-      if (j >= k0 && j < k0 + pw) continue;
-      for (int l = 0; l < pw; ++l) {
-        const int k = k0 + l, p = w.perm[k];
-        if (p != k) {
-          const cpx<float> a = M[(long long)k * n + j], b = M[(long long)p * n + j];
-          M[(long long)k * n + j] = b;
-          M[(long long)p * n + j] = a;
-        }
+// End of a panel, before the update: the panel's row interchanges on every
+// column outside it (a thread per column applies them in order) and the panel's
+// rows copied to T.
+__global__ void gj_panel_swap_kernel(cpx<float>* __restrict__ M, int n, int k0, int pw, GJWork w) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    if (j >= k0 && j < k0 + pw) continue;
+    for (int l = 0; l < pw; ++l) {
+      const int k = k0 + l, p = w.perm[k];
+      if (p != k) {
+        const cpx<float> a = M[(long long)k * n + j], b = M[(long long)p * n + j];
+        M[(long long)k * n + j] = b;
+        M[(long long)p * n + j] = a;
       }
-      for (int l = 0; l < pw; ++l) w.T[(long long)l * n + j] = M[(long long)(k0 + l) * n + j];
-    } else {
-      const long long f = e - n;
-      const int c = (int)(f / n), i = (int)(f - (long long)c * n);
-      M[(long long)i * n + k0 + c] = Wfin[f];
     }
+    for (int l = 0; l < pw; ++l) w.T[(long long)l * n + j] = M[(long long)(k0 + l) * n + j];
   }
 }
 
-// M[i][j] += sum_c U[i][c] T[c][j] for every j outside the panel (64 x 64 tiles, 4 x 4 per thread)
-__global__ void __launch_bounds__(256) gj_update_tiled_kernel(cpx<float>* __restrict__ M, int n, int k0, int pw,
-                                                              const cpx<float>* __restrict__ Ufin,
-                                                              const cpx<float>* __restrict__ T) {
-  __shared__ cpx<float> sU[GJ_P][GJ_TILE + 1];
-  __shared__ cpx<float> sT[GJ_P][GJ_TILE];
-  const int i0 = blockIdx.y * GJ_TILE, j0 = blockIdx.x * GJ_TILE;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < GJ_P * GJ_TILE; e += 256) {
-    const int c = e / GJ_TILE, r = e % GJ_TILE;
-    const int i = i0 + r;
-    sU[c][r] = (i < n && c < pw) ? Ufin[(long long)c * n + i] : cpx<float>(0.f, 0.f);
-    const int j = j0 + r;
-    sT[c][r] = (j < n && c < pw) ? T[(long long)c * n + j] : cpx<float>(0.f, 0.f);
-  }
-  __syncthreads();
-  const int ty = tid / 16, tx = tid % 16;
-  float ar[4][4], ai[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = 0.f;
-  for (int c = 0; c < GJ_P; ++c) {
-    cpx<float> u[4], t[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) u[a] = sU[c][ty + 16 * a];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) t[b] = sT[c][tx + 16 * b];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        ar[a][b] = fmaf(u[a].re, t[b].re, ar[a][b]);
-        ar[a][b] = fmaf(-u[a].im, t[b].im, ar[a][b]);
-        ai[a][b] = fmaf(u[a].re, t[b].im, ai[a][b]);
-        ai[a][b] = fmaf(u[a].im, t[b].re, ai[a][b]);
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = i0 + ty + 16 * a;
-    if (i >= n) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = j0 + tx + 16 * b;
-      if (j >= n || (j >= k0 && j < k0 + pw)) continue;
-      cpx<float> m = M[(long long)i * n + j];
-      m.re += ar[a][b];
-      m.im += ai[a][b];
-      M[(long long)i * n + j] = m;
-    }
+// After the update (which also touched the panel's columns): the eliminated panel
+// columns written into M.
+__global__ void gj_panel_store_kernel(cpx<float>* __restrict__ M, int n, int k0, int pw,
+                                      const cpx<float>* __restrict__ Wfin) {
+  const long long total = (long long)n * pw;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(f / n), i = (int)(f - (long long)c * n);
+    M[(long long)i * n + k0 + c] = Wfin[f];
   }
 }
 
@@ -335,14 +288,71 @@ __global__ void dense_gemv_kernel(const cpx<float>* __restrict__ M, const int* _
   }
 }
 
+// xg[r][j] = x[r][pi[j]] in FP32
+template <typename R>
+__global__ void dense_gather_kernel(const cpx<R>* __restrict__ x, const int* __restrict__ pi, int n, int nrhs,
+                                    cpx<float>* __restrict__ xg) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n), j = (int)(e - (long long)r * n);
+    const cpx<R> v = ld(x + (long long)r * n + __ldg(pi + j));
+    st(xg + e, cpx<float>((float)v.re, (float)v.im));
+  }
+}
+
+template <typename R>
+__global__ void dense_out_kernel(const cpx<float>* __restrict__ y32, cpx<R>* __restrict__ y, long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const cpx<float> v = ld(y32 + e);
+    st(y + e, cpx<R>((R)v.re, (R)v.im));
+  }
+}
+
+int dense_solve_prepare(hdcr_coarse* co, int nrhs) {
+  if (nrhs <= 1) return HDCR_OK;
+  HDCR_TRY(gemm_prepare());
+  const size_t n = (size_t)co->bg.Vc * co->nvec;
+  const size_t need = sizeof(cpx<float>) * n * (size_t)nrhs * 2;
+  if (co->dws_bytes >= need) return HDCR_OK;
+  if (co->dws) cudaFree(co->dws);
+  co->dws = nullptr;
+  co->dws_bytes = 0;
+  HDCR_CUDA_TRY(cudaMalloc(&co->dws, need));
+  co->dws_bytes = need;
+  return HDCR_OK;
+}
+
 template <typename R>
 int launch_dense_solve(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st) {
   const int n = co->bg.Vc * co->nvec;
-  const long long rows = (long long)n * nrhs;
   const cpx<float>* M = (const cpx<float>*)co->Ainv;
-  dense_gemv_kernel<R><<<num_blocks(rows, 8, 152 * 16), 256, 0, st>>>(M, (const int*)(M + (long long)n * n), n, in,
-                                                                       out, nrhs); count_launch();
+  const int* pi = (const int*)(M + (long long)n * n);
+  if (nrhs == 1) {  // one vector: a bandwidth-bound matrix-vector product on the CUDA cores
+    dense_gemv_kernel<R><<<num_blocks(n, 8, 152 * 16), 256, 0, st>>>(M, pi, n, in, out, 1);
+    count_launch();
+    HDCR_LAUNCH_CHECK();
+    return HDCR_OK;
+  }
+  // several: gather once, one GEMM on the tensor cores (the matrix is read once)
+  const long long tot = (long long)n * nrhs;
+  if (co->dws_bytes < sizeof(cpx<float>) * (size_t)tot * 2) {
+    set_error("dense coarse solve: workspace for %d right-hand sides not prepared", nrhs);
+    return HDCR_ERR_BAD_ARG;
+  }
+  cpx<float>* xg = (cpx<float>*)co->dws;
+  cpx<float>* y32 = sizeof(R) == 4 ? (cpx<float>*)out : xg + tot;
+  dense_gather_kernel<R><<<num_blocks(tot, 256, 4096), 256, 0, st>>>(in, pi, n, nrhs, xg);
+  count_launch();
   HDCR_LAUNCH_CHECK();
+  // out (column-major n x nrhs) = M xg, M row-major = (its column-major view)^T
+  HDCR_TRY(cgemm_tc('T', 'N', n, nrhs, n, 1.f, M, n, xg, n, 0.f, y32, n, st));
+  if (sizeof(R) == 8) {
+    dense_out_kernel<R><<<num_blocks(tot, 256, 4096), 256, 0, st>>>(y32, out, tot);
+    count_launch();
+    HDCR_LAUNCH_CHECK();
+  }
   return HDCR_OK;
 }
 template int launch_dense_solve<double>(const hdcr_coarse*, const cpx<double>*, cpx<double>*, int, cudaStream_t);
@@ -389,18 +399,22 @@ int coarse_invert(hdcr_coarse* co, cudaStream_t st) {
   if (s == HDCR_OK) s = launch_convert(co->A, co->dtype, A32, HDCR_C64, na, st);
   if (s == HDCR_OK) {
     assemble_dense_kernel<<<num_blocks(na, 256, 8192), 256, 0, st>>>(A32, co->nbr, Vc, nvec, (cpx<float>*)M); count_launch();
-    const int tiles = (int)((n + GJ_TILE - 1) / GJ_TILE);
     const int ctas = (int)((n + GJ_ROWS - 1) / GJ_ROWS);
-    for (long long k0 = 0; k0 < n; k0 += GJ_P) {
+    s = gemm_prepare();
+    for (long long k0 = 0; k0 < n && s == HDCR_OK; k0 += GJ_P) {
       const int pw = (int)(n - k0 < GJ_P ? n - k0 : GJ_P);
       gj_panel_init_kernel<<<ctas, GJ_ROWS, 0, st>>>((const cpx<float>*)M, (int)n, (int)k0, pw, w); count_launch();
       for (int l = 0; l < pw; ++l) {
         gj_step_kernel<<<ctas, GJ_ROWS, 0, st>>>((int)n, (int)k0, l, pw, w); count_launch();
       }
-      gj_panel_apply_kernel<<<num_blocks(n + n * pw, 256, 4096), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw,
-                                                                               w.W[pw & 1], w); count_launch();
-      gj_update_tiled_kernel<<<dim3(tiles, tiles), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw, w.U[pw & 1],
-                                                                  w.T); count_launch();
+      gj_panel_swap_kernel<<<num_blocks(n, 256, 4096), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw, w);
+      count_launch();
+      // M[i][j] += sum_c U[i][c] T[c][j]: in the column-major view (M^T) that is T^T U^T, with
+      // T^T (n x pw) and U (n x pw) both stored column-major with leading dimension n
+      s = cgemm_tc('N', 'T', (int)n, (int)n, pw, 1.f, w.T, n, w.U[pw & 1], n, 1.f, (cpx<float>*)M, n, st);
+      gj_panel_store_kernel<<<num_blocks(n * pw, 256, 4096), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw,
+                                                                          w.W[pw & 1]);
+      count_launch();
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) s = cuda_status(e, "Gauss-Jordan elimination");
@@ -457,5 +471,7 @@ extern "C" int hdcr_coarse_solve_dense(const hdcr_coarse* co, const void* in, vo
     set_error("hdcr_coarse_solve_dense: bad pointers or nrhs");
     return HDCR_ERR_BAD_ARG;
   }
+  // the workspace of several right-hand sides is internal state of the handle
+  HDCR_TRY(dense_solve_prepare(const_cast<hdcr_coarse*>(co), nrhs));
   return launch_dense_solve<float>(co, (const cpx<float>*)in, (cpx<float>*)out, nrhs, as_stream(stream));
 }

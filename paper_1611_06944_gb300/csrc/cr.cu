@@ -11,6 +11,8 @@
 // reduction epilogues (last block) advance those scalars.
 #include <chrono>
 
+#include <mutex>
+
 #include "dwf_stencil.cuh"
 #include "krylov.cuh"
 
@@ -263,6 +265,26 @@ int launch_diff_norm(const cpx<R>* b, const cpx<R>* y, long long n, RedScratch r
 HDCR_INST_CR(double)
 HDCR_INST_CR(float)
 
+void cr_graph_free(CRGraph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  *g = CRGraph();
+}
+
+int capture_stream(cudaStream_t* s) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  HDCR_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("capture stream: device %d beyond the 64 supported", dev);
+    return HDCR_ERR_BAD_ARG;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev]) HDCR_CUDA_TRY(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+  *s = streams[dev];
+  return HDCR_OK;
+}
+
 template <typename R>
 static int cr_solve_impl(const Geom& g, const hdcr_dwf_params* p, const void* U, const void* b, void* x,
                          double tol, int max_iter, hdcr_solve_stats* stats, cudaStream_t st) {
@@ -274,8 +296,11 @@ static int cr_solve_impl(const Geom& g, const hdcr_dwf_params* p, const void* U,
   cfg.tol = tol;
   cfg.max_iter = max_iter;
   cfg.check_every = sizeof(R) == 8 ? 2 : 8;
+  CRGraph graph;  // the iterations between host checks replay from one CUDA graph
+  cfg.graph = &graph;
   CRResult res;
   int s = cr_run<R>(H, (const cpx<R>*)b, (cpx<R>*)x, w, cfg, &res, st);
+  cr_graph_free(&graph);
   double tr = -1.0;
   if (s == HDCR_OK) {
     s = true_residual2<R>(H, (const cpx<R>*)b, (const cpx<R>*)x, w.Ar, w.rb.rs, &w.dev()->tr, st);

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <vector>
 
+#include "host_io.cuh"
 #include "blas.cuh"
 #include "dwf_stencil.cuh"
 
@@ -245,8 +246,8 @@ extern "C" int hdcr_stencil_tune_info(const hdcr_geom* gp, int nrhs, int* varian
   return x2_tune_info(g, nrhs, variant, us, nus);
 }
 
-extern "C" int hdcr_apply_gamma5_r5(const hdcr_geom* gp, const void* in, void* out, int dtype,
-                                    int nfields, void* stream) {
+static int gamma5_r5_entry(const hdcr_geom* gp, const void* in, void* out, int dtype, int nfields,
+                           void* stream) {
   Geom g;
   HDCR_TRY(make_geom(gp, &g));
   if (!in || !out || nfields < 1 || in == out) {
@@ -358,4 +359,19 @@ extern "C" int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* l
   *launches = nl;
   *sites = ns;
   return HDCR_OK;
+}
+
+extern "C" int hdcr_apply_gamma5_r5(const hdcr_geom* gp, const void* in, void* out, int dtype,
+                                    int nfields, void* stream) {
+  Geom g;
+  HDCR_TRY(make_geom(gp, &g));
+  const size_t cb = dtype_complex_bytes(dtype);
+  if (!cb || nfields < 1) return gamma5_r5_entry(gp, in, out, dtype, nfields, stream);
+  // fields given in host memory are staged through the device
+  cudaStream_t st = as_stream(stream);
+  Staged si, so;
+  HDCR_TRY(si.in(in, (size_t)nfields * g.V5 * 12 * cb, st));
+  HDCR_TRY(so.out(out, (size_t)nfields * g.V5 * 12 * cb, st, false));
+  HDCR_TRY(gamma5_r5_entry(gp, si.ptr(), so.ptr(), dtype, nfields, stream));
+  return so.finish();
 }

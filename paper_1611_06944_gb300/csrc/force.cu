@@ -11,6 +11,7 @@
 // stores the gradient of the loss with respect to the link instead:
 // conj(F_ba) at [a][b], i.e. dL/dRe U_ab + i dL/dIm U_ab.
 #include "dwf_stencil.cuh"
+#include "host_io.cuh"
 
 namespace hdcr {
 
@@ -154,10 +155,22 @@ static int gauge_force_call(const char* name, const hdcr_geom* gp, const void* x
     set_error("%s: null pointer", name);
     return HDCR_ERR_BAD_ARG;
   }
-  if (dtype == HDCR_C128) return launch_force<double, GRAD>(g, x, w, F, as_stream(stream));
-  if (dtype == HDCR_C64) return launch_force<float, GRAD>(g, x, w, F, as_stream(stream));
-  set_error("%s: unknown dtype %d", name, dtype);
-  return HDCR_ERR_BAD_ARG;
+  const size_t cb = dtype_complex_bytes(dtype);
+  if (!cb) {
+    set_error("%s: unknown dtype %d", name, dtype);
+    return HDCR_ERR_BAD_ARG;
+  }
+  // fields given in host memory are staged through the device
+  cudaStream_t st = as_stream(stream);
+  Staged sx, sw, sf;
+  HDCR_TRY(sx.in(x, (size_t)g.V5 * 12 * cb, st));
+  HDCR_TRY(sw.in(w, (size_t)g.V5 * 12 * cb, st));
+  HDCR_TRY(sf.out(F, (size_t)g.V4 * 36 * cb, st, false));
+  if (dtype == HDCR_C128)
+    HDCR_TRY((launch_force<double, GRAD>(g, sx.ptr(), sw.ptr(), sf.ptr(), st)));
+  else
+    HDCR_TRY((launch_force<float, GRAD>(g, sx.ptr(), sw.ptr(), sf.ptr(), st)));
+  return sf.finish();
 }
 
 extern "C" int hdcr_gauge_force(const hdcr_geom* gp, const void* x, const void* w, void* F, int dtype,

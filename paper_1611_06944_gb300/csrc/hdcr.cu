@@ -14,6 +14,7 @@
 #include <mutex>
 #include <vector>
 
+#include "host_io.cuh"
 #include "chebyshev.cuh"
 #include "coarse.cuh"
 
@@ -114,6 +115,7 @@ struct SolveCache {
   std::vector<double> cheb_c;
   RedBuffers rb{};       // outer reductions; scal: [0..127] MGS coefficients, 128.. scalars
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  CRGraph cgraph;        // the coarse CR's iterations between host checks, replayed every V-cycle
 };
 
 template <typename R>
@@ -137,6 +139,7 @@ void solve_cache_free(SolveCache* c) {
   if (!c) return;
   if (c->inner == HDCR_C128) free_inner<double>(c);
   if (c->inner == HDCR_C64) free_inner<float>(c);
+  cr_graph_free(&c->cgraph);
   if (c->mem) cudaFree(c->mem);
   red_buffers_free(&c->rb);
   for (int i = 0; i < 6; ++i)
@@ -237,6 +240,7 @@ static int coarse_solve(const hdcr_coarse* co, SolveCache* c, const hdcr_solve_p
   ccfg.max_iter = prm->coarse_max;
   ccfg.x_zero = true;
   ccfg.check_every = 8;
+  ccfg.graph = &c->cgraph;
   CoarseOp<R> A{co};
   CRResult res;
   HDCR_TRY(cr_run<R>(A, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, cw, ccfg, &res, st));
@@ -431,8 +435,8 @@ void solve_cache_release(const hdcr_coarse* co) {
 }
 }  // namespace hdcr
 
-extern "C" int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x,
-                          const hdcr_solve_params* prm, hdcr_solve_stats* stats, void* stream) {
+static int solve_entry(hdcr_coarse* co, const void* U, const void* b, void* x, const hdcr_solve_params* prm,
+                       hdcr_solve_stats* stats, void* stream) {
   HDCR_TRY(coarse_check(co));
   if (!U || !b || !x || !prm || b == x) {
     set_error("hdcr_solve: null pointer or b == x");
@@ -479,4 +483,24 @@ extern "C" int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x
   if (prm->inner_dtype == HDCR_C128)
     return solve_impl<double>(co, cache, U, (const cpx<double>*)b, (cpx<double>*)x, prm, stats, st);
   return solve_impl<float>(co, cache, U, (const cpx<double>*)b, (cpx<double>*)x, prm, stats, st);
+}
+
+extern "C" int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x,
+                          const hdcr_solve_params* prm, hdcr_solve_stats* stats, void* stream) {
+  HDCR_TRY(coarse_check(co));
+  if (!U || !b || !x || b == x) {
+    set_error("hdcr_solve: null pointer or b == x");
+    return HDCR_ERR_BAD_ARG;
+  }
+  // links, source and solution given in host memory are staged through the device
+  cudaStream_t st = as_stream(stream);
+  const size_t field = (size_t)co->g.V5 * 12 * 16;
+  Staged su, sb, sx;
+  HDCR_TRY(su.in(U, (size_t)co->g.V4 * 36 * 16, st));
+  HDCR_TRY(sb.in(b, field, st));
+  HDCR_TRY(sx.out(x, field, st, true));
+  const int s = solve_entry(co, su.ptr(), sb.ptr(), sx.ptr(), prm, stats, stream);
+  HDCR_TRY(sx.finish());
+  if (sx.ptr() != x) HDCR_CUDA_TRY(cudaStreamSynchronize(st));
+  return s;
 }

@@ -41,6 +41,7 @@ int cuda_status(cudaError_t e, const char* what);
 // number of kernels this library has launched in the process (a diagnostic)
 void count_launch();
 void count_launches(unsigned long long n);  // kernels a replayed CUDA graph launched
+void uncount_launches(unsigned long long n);  // kernels counted while captured, not launched
 unsigned long long launches_so_far();
 
 // --------------------------------------------------------------- geometry

@@ -178,6 +178,7 @@ struct MultiCache {
   int graph_fine = 0;
   const void* key_U = nullptr;
   const void* key_Ainv = nullptr;
+  const void* key_dws = nullptr;  // the dense solve's workspace the graph was captured with
   double key_lo = 0, key_hi = 0;
   int key_order = -1;
 };
@@ -389,7 +390,7 @@ static int solve_multi_impl(const hdcr_coarse* co, MultiCache* c, const void* U,
     if (!(bb[q] == 0.0 || rr[q] <= tol2[q])) converged = false;
   }
   // the graph bakes in U (FP64 inner), the dense inverse and the smoother: re-capture when they change
-  const bool graph_ok = use_graph && c->exec && c->key_U == U && c->key_Ainv == co->Ainv &&
+  const bool graph_ok = use_graph && c->exec && c->key_U == U && c->key_Ainv == co->Ainv && c->key_dws == co->dws &&
                         c->key_order == prm->smoother_order && c->key_lo == prm->cheb_lo &&
                         c->key_hi == prm->cheb_hi;
   bool have_graph = graph_ok;
@@ -410,6 +411,7 @@ static int solve_multi_impl(const hdcr_coarse* co, MultiCache* c, const void* U,
           HDCR_TRY(capture_vcycle<R>(co, Hin, c, prm));
           c->key_U = U;
           c->key_Ainv = co->Ainv;
+          c->key_dws = co->dws;
           c->key_order = prm->smoother_order;
           c->key_lo = prm->cheb_lo;
           c->key_hi = prm->cheb_hi;
@@ -547,6 +549,7 @@ extern "C" int hdcr_solve_multi(hdcr_coarse* co, const void* U, const void* b, v
   }
   cudaStream_t st = as_stream(stream);
   if (!co->Ainv) HDCR_TRY(coarse_invert(co, st));
+  HDCR_TRY(dense_solve_prepare(co, nrhs));  // before any capture: the coarse solve then allocates nothing
   MultiCache* cache = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mcache_mutex);

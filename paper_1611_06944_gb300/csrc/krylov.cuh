@@ -55,12 +55,31 @@ int crwork_alloc(CRWork<R>* w, long long n);
 template <typename R>
 void crwork_free(CRWork<R>* w);
 
+// A CUDA graph of check_every consecutive CR iterations (update of x and r, copy of
+// |r|^2 to the host, H r with <r, H r>, update of p and H p) on fixed buffers,
+// captured once on a library stream and replayed on the run's stream: in
+// convergence mode the iterations between two host checks then cost one launch.
+// Replays give the same bits as the eager launches (the same kernels in the same
+// order).  Owned by the caller, who keeps it while the buffers it names stay the
+// same (cr_run re-captures when they change) and frees it with cr_graph_free.
+struct CRGraph {
+  cudaGraphExec_t exec = nullptr;
+  const void* key[6] = {};
+  long long n = 0;
+  int ck = 0;
+  unsigned long long kernels = 0;  // kernels one replay launches
+};
+void cr_graph_free(CRGraph* g);
+// the current device's stream for captures (created once, non-blocking)
+int capture_stream(cudaStream_t* s);
+
 struct CRConfig {
   double tol = 1e-10;   // relative residual target (convergence mode)
   int max_iter = 10000;
   int fixed_iters = -1; // >= 0: run exactly this many iterations, no test, no host sync
   bool x_zero = false;  // x is zero on entry: skip the initial H x
   int check_every = 4;  // host convergence test every k iterations
+  CRGraph* graph = nullptr;  // convergence mode: replay the iterations from this graph
 };
 
 struct CRResult {
@@ -145,8 +164,69 @@ int cr_run(const Op& A, const cpx<R>* b, cpx<R>* x, CRWork<R>& w, const CRConfig
   out.matvecs++;
   HDCR_TRY(launch_cr_setup_ap<R>(w.Ar, w.Ap, n, rs, s, st));
   const int ck = cfg.check_every > 0 ? (cfg.check_every < PINNED_RING ? cfg.check_every : PINNED_RING) : 1;
+  int k0 = 0;  // iterations done by graph replays
+  if (!fixed && cfg.graph) {
+    CRGraph* gr = cfg.graph;
+    const void* key[6] = {x, w.r, w.p, w.Ar, w.Ap, ring};
+    bool same = gr->exec && gr->n == n && gr->ck == ck;
+    for (int i = 0; i < 6 && same; ++i) same = gr->key[i] == key[i];
+    if (!same) {
+      cr_graph_free(gr);
+      cudaStream_t cs;
+      HDCR_TRY(capture_stream(&cs));
+      const unsigned long long before = launches_so_far();
+      HDCR_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      int cap = HDCR_OK;
+      for (int i = 0; i < ck && cap == HDCR_OK; ++i) {
+        cap = launch_cr_update_xr<R>(x, w.r, w.p, w.Ap, n, rs, s, cs);
+        if (cap == HDCR_OK && cudaMemcpyAsync(ring + i, &s->rr, sizeof(double), cudaMemcpyDeviceToHost, cs) !=
+                                  cudaSuccess)
+          cap = HDCR_ERR_CUDA;
+        if (cap == HDCR_OK) cap = A.apply_dot(w.r, w.Ar, rs, &s->gamma_new, cs);
+        if (cap == HDCR_OK) cap = launch_cr_update_p<R>(w.r, w.p, w.Ar, w.Ap, n, rs, s, cs);
+      }
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+      if (cap == HDCR_OK && ee == cudaSuccess) {
+        if (cudaGraphInstantiate(&gr->exec, graph, 0) != cudaSuccess) gr->exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      gr->kernels = launches_so_far() - before;
+      uncount_launches(gr->kernels);  // captured, not launched
+      gr->n = n;
+      gr->ck = ck;
+      for (int i = 0; i < 6; ++i) gr->key[i] = key[i];
+    }
+    // whole chunks from the graph while they fit under niter; the rest runs eagerly below
+    while (gr->exec && k0 + ck <= niter) {
+      HDCR_CUDA_TRY(cudaGraphLaunch(gr->exec, st));
+      count_launches(gr->kernels);
+      k0 += ck;
+      out.iters = k0;
+      out.matvecs += ck;
+      HDCR_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int i = 0; i < ck; ++i) {
+        const double rr = ring[i];
+        if (!(rr == rr) || rr > 1e300) {
+          set_error("CR: non-finite residual at iteration %d", k0 - ck + i + 1);
+          if (res) *res = out;
+          return HDCR_ERR_NONFINITE;
+        }
+        out.rel_resid = sqrt(rr / scale2);
+        if (rr <= cfg.tol * cfg.tol * scale2) {
+          out.converged = true;
+          break;
+        }
+      }
+      if (out.converged) {
+        if (res) *res = out;
+        return HDCR_OK;
+      }
+    }
+  }
   int pending = 0;
-  for (int k = 0; k < niter; ++k) {
+  for (int k = k0; k < niter; ++k) {
     HDCR_TRY(launch_cr_update_xr<R>(x, w.r, w.p, w.Ap, n, rs, s, st));
     out.iters = k + 1;
     if (!fixed) {

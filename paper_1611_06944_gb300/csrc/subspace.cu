@@ -4,6 +4,7 @@
 //   -> restriction to blocks (Eq. 4.1) -> block orthonormalisation, so that
 //   P_S = sum |phi_k^b><phi_k^b| (Eq. 4.3) is a projector.
 // All of it runs in FP64; the basis is then stored in the requested dtype.
+#include "host_io.cuh"
 #include "chebyshev.cuh"
 #include "coarse.cuh"
 
@@ -366,7 +367,11 @@ extern "C" int hdcr_build_subspace(const hdcr_geom* gp, const hdcr_dwf_params* p
     return HDCR_ERR_BAD_ARG;
   }
   *out = nullptr;
-  return build_subspace_impl(g, bg, p, U, noise, sp, as_stream(stream), out);
+  cudaStream_t st = as_stream(stream);
+  Staged su, sn;
+  HDCR_TRY(su.in(U, (size_t)g.V4 * 36 * 16, st));
+  HDCR_TRY(sn.in(noise, (size_t)(sp->nvec / 2) * g.V5 * 12 * 16, st));
+  return build_subspace_impl(g, bg, p, su.ptr(), sn.ptr(), sp, st, out);
 }
 
 extern "C" int hdcr_subspace_from_vectors(const hdcr_geom* gp, const int block[4], int nvec,
