@@ -1,0 +1,85 @@
+"""Oracle: the continued-fraction overlap operator of Section 3.  Test
+infrastructure only (the tests and the CPU baseline use it; the CUDA library
+never does).
+
+Section 3 notes that the continued-fraction form of the overlap operator with
+the Hermitian Wilson kernel H = H_W is already Hermitian indefinite and prints
+it for five components: a block-tridiagonal matrix whose diagonal blocks are
+H, -H, H, -H and R gamma5 + beta_0 H, and whose off-diagonal blocks are the
+scalars 1/sqrt(beta_0 beta_1), 1/sqrt(beta_1 beta_2), 1/sqrt(beta_2 beta_3) and
+1/sqrt(beta_3) (symmetric).
+
+Readings:
+* H = gamma5 D_W, D_W the Wilson operator of ``oracle.dwf`` with mass -M5 (the
+  kernel of the domain-wall operator of the same section).
+* Other sizes: N components (N >= 2) with N - 1 coefficients beta_0..beta_{N-2};
+  diagonal (-1)^i H for i < N - 1 and R gamma5 + beta_0 H for the last; coupling
+  1/sqrt(beta_i beta_{i+1}) between components i and i + 1 for i < N - 2 and
+  1/sqrt(beta_{N-2}) between N - 2 and N - 1.  N = 5 is the printed matrix.
+* A field stores its N components where a domain-wall field stores s: shape
+  (..., Lt, Lz, Ly, Lx, N, 4, 3).
+
+Eliminating the first N - 1 components leaves, on the last one, the Schur
+complement R gamma5 + beta_0 H - c_{N-2}^2 K_{N-2}(H)^{-1} with the continued
+fraction K_0 = H, K_i = (-1)^i H - c_{i-1}^2 K_{i-1}^{-1} (c_i the couplings): a
+rational function of H, which is how the overlap's sign function enters.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dwf
+
+
+def couplings(beta) -> np.ndarray:
+    """The N - 1 off-diagonal scalars for N = len(beta) + 1 components."""
+    b = np.asarray(beta, dtype=float)
+    n = len(b)
+    c = np.empty(n)
+    for i in range(n - 1):
+        c[i] = 1.0 / np.sqrt(b[i] * b[i + 1])
+    c[n - 1] = 1.0 / np.sqrt(b[n - 1])
+    return c
+
+
+def diag_scales(beta) -> np.ndarray:
+    """The factor of H on each diagonal block: (-1)^i, and beta_0 on the last."""
+    n = len(beta) + 1
+    s = np.array([(-1.0) ** i for i in range(n)])
+    s[-1] = beta[0]
+    return s
+
+
+def apply_HW(U, psi, M5: float, bc_t: int = 1) -> np.ndarray:
+    """H_W = gamma5 D_W on every component."""
+    return dwf.spin_mul(dwf.GAMMA5, dwf.wilson(U, psi, M5, bc_t))
+
+
+def apply_cf(U, psi, M5: float, beta, R: float, bc_t: int = 1) -> np.ndarray:
+    """The continued-fraction operator on an N-component field (N = len(beta) + 1)."""
+    n = psi.shape[-3]
+    if n != len(beta) + 1:
+        raise ValueError("the field must have len(beta) + 1 components")
+    hw = apply_HW(U, psi, M5, bc_t)
+    s = diag_scales(beta)
+    c = couplings(beta)
+    out = hw * s[:, None, None]
+    out[..., n - 1, :, :] += R * dwf.spin_mul(dwf.GAMMA5, psi[..., n - 1, :, :])
+    for i in range(n - 1):
+        out[..., i, :, :] += c[i] * psi[..., i + 1, :, :]
+        out[..., i + 1, :, :] += c[i] * psi[..., i, :, :]
+    return out
+
+
+def schur_last(hw_eigvals, beta, R, g5, V):
+    """The Schur complement on the last component from the continued fraction of
+    the eigenvalues of H (V its eigenvectors as columns, g5 gamma5 as a matrix in
+    the same basis as V's rows): R g5 + V diag(f(lambda)) V^dag."""
+    c = couplings(beta)
+    n = len(beta) + 1
+    lam = np.asarray(hw_eigvals, dtype=float)
+    K = lam.copy()                       # K_0 = lambda
+    for i in range(1, n - 1):
+        K = (-1.0) ** i * lam - c[i - 1] ** 2 / K
+    f = beta[0] * lam - c[n - 2] ** 2 / K if n > 1 else beta[0] * lam
+    return R * g5 + (V * f) @ np.conj(V.T)

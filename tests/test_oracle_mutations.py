@@ -271,3 +271,107 @@ def test_mobius_with_unscaled_mass_term_is_caught(monkeypatch):
     monkeypatch.setattr(dwf, "ddwf_mobius", bad)
     chi = synth.gaussian_fermion((1, 1, 1, 1), LS, 21)[0, 0, 0, 0]
     assert plane_wave_error(dwf, (4, 6, 4, 8), LS, 1.8, 0.03, (1, 0, 2, 3), chi, 1, b5=1.5) > 1e-3
+
+
+# ------------------------------------------------------------- third level (oracle/level2.py)
+def _l2_galerkin_error():
+    """|A2 (densified) - P2^dag A P2| / |P2^dag A P2| with dense matrices built independently."""
+    from oracle import level2 as l2
+    from test_oracle_level2 import _dense_A, _dense_P2
+    g = l2.CoarseGeometry((6, 4, 4, 6), 4, (3, 2, 2, 3))
+    A = l2.random_coarse_op(g, 61)
+    rng = np.random.default_rng(62)
+    v = rng.standard_normal((4, g.Vc, 4)) + 1j * rng.standard_normal((4, g.Vc, 4))
+    Phi2 = l2.basis_from_vectors(g, v)
+    P = _dense_P2(g, Phi2)
+    brute = np.conj(P.T) @ _dense_A(A, g) @ P
+    return np.abs(l2.level2_dense(l2.level2_op(A, g, Phi2), g) - brute).max() / np.abs(brute).max()
+
+
+def test_unmutated_level2_oracle_passes():
+    assert _l2_galerkin_error() < 1e-12
+
+
+def test_level2_leg_without_block_mask_is_caught(monkeypatch):
+    from oracle import level2 as l2
+    monkeypatch.setattr(l2, "crossing_mask", lambda g, mu, sign: np.ones((g.Vc, 1)))
+    assert _l2_galerkin_error() > 1e-3
+
+
+def test_level2_leg_in_the_wrong_direction_is_caught(monkeypatch):
+    from oracle import level2 as l2
+    orig = l2.apply_leg
+    monkeypatch.setattr(l2, "apply_leg", lambda A, g, c, mu, sign: orig(A, g, c, mu, -sign))
+    assert _l2_galerkin_error() > 1e-3
+
+
+def test_level2_projection_without_conjugate_is_caught(monkeypatch):
+    from oracle import level2 as l2
+    orig_conj = l2.np.conj
+
+    class NoConjNp:
+        def __getattr__(self, name):
+            return getattr(np, name)
+
+        @staticmethod
+        def conj(x):
+            return x
+
+    monkeypatch.setattr(l2, "np", NoConjNp())
+    try:
+        err = _l2_galerkin_error()
+    finally:
+        monkeypatch.setattr(l2, "np", np)
+    assert orig_conj is np.conj and err > 1e-3
+
+
+def test_coarse_gamma5_with_wrong_ordering_is_caught(monkeypatch):
+    """The split must follow the level-1 basis's chirality ordering (the P_+ half first);
+    alternating signs would mix chiralities, which the definite-chirality pin sees."""
+    from oracle import level2 as l2
+    monkeypatch.setattr(l2, "gamma5_coarse", lambda nvec: np.array([(-1.0) ** i for i in range(nvec)]))
+    g5_true = np.concatenate([np.ones(3), -np.ones(3)])
+    rng = np.random.default_rng(63)
+    v = rng.standard_normal((2, 16, 6)) + 1j * rng.standard_normal((2, 16, 6))
+    s = l2.chiral_split(v, 6)
+    assert not np.allclose(s[:2] * g5_true, s[:2])
+
+
+# ------------------------------------------------------------- continued fraction (oracle/overlap.py)
+def _cf_printed_error():
+    from oracle import overlap as ov
+    from test_oracle_overlap import BETA, R, _dense_cf, _printed_matrix
+    U = synth.gauge_field((2, 2, 2, 2), 0.5, 81)
+    P = _printed_matrix(U, BETA, R)
+    return np.abs(_dense_cf(U, BETA, R) - P).max() / np.abs(P).max()
+
+
+def test_unmutated_cf_oracle_passes():
+    assert _cf_printed_error() < 1e-13
+
+
+def test_cf_without_alternating_signs_is_caught(monkeypatch):
+    from oracle import overlap as ov
+    orig = ov.diag_scales
+    monkeypatch.setattr(ov, "diag_scales", lambda beta: np.abs(orig(beta)))
+    assert _cf_printed_error() > 1e-3
+
+
+def test_cf_last_coupling_with_both_betas_is_caught(monkeypatch):
+    """The last coupling is 1/sqrt(beta_{N-2}), not 1/sqrt(beta_{N-2} beta_0)."""
+    from oracle import overlap as ov
+    orig = ov.couplings
+
+    def bad(beta):
+        c = orig(beta).copy()
+        c[-1] = 1.0 / np.sqrt(beta[-1] * beta[0])
+        return c
+
+    monkeypatch.setattr(ov, "couplings", bad)
+    assert _cf_printed_error() > 1e-3
+
+
+def test_cf_without_gamma5_on_the_kernel_is_caught(monkeypatch):
+    from oracle import overlap as ov
+    monkeypatch.setattr(ov, "apply_HW", lambda U, psi, M5, bc_t=1: dwf.wilson(U, psi, M5, bc_t))
+    assert _cf_printed_error() > 1e-3
