@@ -357,6 +357,41 @@ int hdcr_coarse_solve_dense(const hdcr_coarse* co, const void* in, void* out, in
                             void* stream);
 void hdcr_coarse_destroy(hdcr_coarse* co);
 
+/* ---------------------------------------------------------------- third level
+ * hdcr_coarse_build_level2: the two-level construction of Section 4 applied to
+ * the coarse operator A itself (Section 5: recursion solves the coarse system
+ * more exactly).  nvec2/2 Gaussian noise vectors on the coarse lattice (``noise``:
+ * C128 coarse vectors [v][a][k], drawn by the caller) are each smoothed by
+ * ``smooth_iters`` CR steps on A x = 0 and normalised, split by the coarse Gamma5
+ * (+1 on the first nvec/2 basis components of a site, -1 on the rest: the level-1
+ * basis vectors have definite Gamma5 chirality), restricted to blocks of
+ * block[0..3] coarse sites times all nvec components and orthonormalised by
+ * modified Gram-Schmidt twice per block (FP64); then A2 = P2^dag A P2 (9 legs on
+ * the level-2 lattice) is built and inverted densely (FP32).  The level is kept
+ * in the coarse handle (rebuilt by a new call, freed with it) and used by
+ * hdcr_solve's HDCR_COARSE_RECURSIVE solver, whose V-cycle one level down takes
+ * ``cycle_smooth`` CR steps on A as its smoother.  Every block[mu] must divide
+ * the coarse extent into >= 2; nvec2 even, 2..64.  Synchronises ``stream``.
+ * Errors: BAD_ARG, BAD_GEOMETRY, RANK_DEFICIENT, NONFINITE, CUDA, NO_MEMORY. */
+typedef struct {
+  int nvec2;         /* level-2 basis size after the split (even)          */
+  int block[4];      /* level-2 block in coarse sites                      */
+  int smooth_iters;  /* CR steps smoothing each level-2 noise vector       */
+  int cycle_smooth;  /* CR steps of the smoother of the recursive V-cycle  */
+} hdcr_level2_params;
+int hdcr_coarse_build_level2(hdcr_coarse* co, const hdcr_level2_params* p, const void* noise,
+                             void* stream);
+/* nvec2 (0 without a third level) and the level-2 lattice extents. */
+int hdcr_coarse_level2_info(const hdcr_coarse* co, int* nvec2, int L2[4]);
+/* Copies the level-2 basis (C128, [nvec2][Vc][nvec]) and A2 (C128,
+ * [Vc2][9][nvec2][nvec2]) into device buffers. */
+int hdcr_coarse_level2_get(const hdcr_coarse* co, void* vectors, void* op, void* stream);
+/* out = A^{-1} in (one coarse vector in the coarse operator's dtype) by the
+ * recursive solver to |in - A out| <= tol |in|; *iters receives the GCR
+ * iterations.  Synchronises ``stream``.  Errors: BAD_ARG, NONFINITE, CUDA. */
+int hdcr_coarse_solve_level2(const hdcr_coarse* co, const void* in, void* out, double tol,
+                             int max_iter, int* iters, void* stream);
+
 /* ---------------------------------------------------------------- HDCR solve
  * hdcr_solve: H x = b (Section 4) by flexible GCR(restart) in FP64 on H,
  * preconditioned by the two-level V-cycle
@@ -368,8 +403,10 @@ void hdcr_coarse_destroy(hdcr_coarse* co);
  *                            Chebyshev approximation of 1/y on
  *                            [cheb_lo, cheb_hi] (Section 4: order 10 on [1, 64]).
  * Coarse solvers: HDCR_COARSE_CR (CR on A to ``coarse_tol``, cap
- * ``coarse_max``) or HDCR_COARSE_DENSE (the dense inverse of
- * hdcr_coarse_invert, computed on first use).  inner_dtype C128 runs the
+ * ``coarse_max``), HDCR_COARSE_DENSE (the dense inverse of
+ * hdcr_coarse_invert, computed on first use) or HDCR_COARSE_RECURSIVE (flexible
+ * GCR on A to ``coarse_tol``, cap ``coarse_max``, preconditioned by the third
+ * level built by hdcr_coarse_build_level2).  inner_dtype C128 runs the
  * smoother and coarse correction in FP64 (the dense inverse is FP32 in either
  * case); C64 runs them in FP32 (FP32 basis and coarse operator required) while
  * the outer FGCR, its orthogonalisation and the true residual stay FP64.  The
@@ -382,6 +419,7 @@ void hdcr_coarse_destroy(hdcr_coarse* co);
 #define HDCR_SMOOTHER_CHEBYSHEV 1
 #define HDCR_COARSE_CR 0
 #define HDCR_COARSE_DENSE 1
+#define HDCR_COARSE_RECURSIVE 2 /* FGCR on A with the third level (hdcr_coarse_build_level2) */
 
 typedef struct {
   double tol;         /* true relative residual target, e.g. 1e-10           */
@@ -419,6 +457,33 @@ int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x,
 int hdcr_solve_multi(hdcr_coarse* co, const void* U, const void* b, void* x, int nrhs,
                      const hdcr_solve_params* params, int use_graph, hdcr_solve_stats* stats,
                      void* stream);
+
+/* ---------------------------------------------------------------- continued-fraction overlap
+ * hdcr_apply_cf_overlap: out = H_cf in for the continued-fraction form of the
+ * overlap operator (Section 3), which the paper prints for five components as the
+ * Hermitian-indefinite block-tridiagonal matrix with diagonal blocks H, -H, H, -H,
+ * R gamma5 + beta_0 H and scalar off-diagonal blocks 1/sqrt(beta_0 beta_1),
+ * 1/sqrt(beta_1 beta_2), 1/sqrt(beta_2 beta_3), 1/sqrt(beta_3), where H = gamma5 D_W is
+ * the Hermitian Wilson kernel with mass -M5 (the 4d part of D_dwf above).  For
+ * ncomp = N components (2..16): diagonal (-1)^i H for i < N-1 and R gamma5 + beta_0 H
+ * last, coupling 1/sqrt(beta_i beta_{i+1}) between i and i+1 for i < N-2 and
+ * 1/sqrt(beta_{N-2}) between N-2 and N-1 (beta[0..N-2] > 0).  The N components are
+ * stored as the fifth coordinate of a fermion field: g->Ls must equal ncomp.  U and
+ * the nrhs fields share ``dtype`` (C128 or C64).  Errors: BAD_ARG, BAD_GEOMETRY. */
+typedef struct {
+  int ncomp;        /* N, the number of components (2..16)  */
+  double beta[15];  /* beta_0 .. beta_{N-2}                  */
+  double R;         /* coefficient of gamma5 on the last one */
+} hdcr_cf_params;
+int hdcr_apply_cf_overlap(const hdcr_geom* g, double M5, const hdcr_cf_params* cf, const void* U,
+                          const void* in, void* out, int dtype, int nrhs, void* stream);
+/* CR (Section 3) on H_cf x = b in ``dtype``, as hdcr_cr_solve: x holds the initial
+ * guess, the true residual |b - H_cf x| / |b| is recomputed into stats->true_resid;
+ * the iterations between host checks replay from a captured CUDA graph.
+ * Synchronises ``stream``.  Errors: BAD_ARG, NOT_CONVERGED, NONFINITE, CUDA. */
+int hdcr_cf_cr_solve(const hdcr_geom* g, double M5, const hdcr_cf_params* cf, const void* U,
+                     const void* b, void* x, int dtype, double tol, int max_iter,
+                     hdcr_solve_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------- gauge force
  * hdcr_gauge_force: the gauge-link gradient of a solve (not in the paper;

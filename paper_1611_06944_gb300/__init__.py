@@ -102,9 +102,10 @@ def load_library():
 __all__ = [
     "HDCRError", "Lattice", "probe_fma_rate", "tc_gemm_info", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info",
-    "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
+    "apply_cf_overlap", "cf_cr_solve", "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
+    "build_level2", "level2_get", "coarse_solve_level2",
     "hdcr_solve", "hdcr_solve_into", "hdcr_solve_multi", "cgne_rb_solve", "gauge_force", "gauge_grad", "HDCRSolve",
     "solve_autograd",
 ]
@@ -197,6 +198,41 @@ def apply_g5dwf(lat: Lattice, U: torch.Tensor, psi: torch.Tensor, M5: float, mf:
     _check(_L.hdcr_apply_g5dwf(C_ref(g), C_ref(p), _dev(U, "U"), _dev(psi, "psi"), _dev(out, "out"),
                                _code(psi), n, _stream(stream)), "apply_g5dwf")
     return out
+
+
+def _cf_params(beta, R: float) -> _lib.hdcr_cf_params:
+    p = _lib.hdcr_cf_params()
+    p.ncomp = len(beta) + 1
+    for i, b in enumerate(beta):
+        p.beta[i] = float(b)
+    p.R = float(R)
+    return p
+
+
+def apply_cf_overlap(lat: Lattice, U: torch.Tensor, psi: torch.Tensor, M5: float, beta, R: float,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The continued-fraction overlap operator of Section 3 on len(beta) + 1 components,
+    stored as the fifth coordinate (lat.Ls must be len(beta) + 1)."""
+    if U.dtype != psi.dtype:
+        raise TypeError("U and psi must share a dtype")
+    n = _nfields(lat, psi, "psi")
+    out = torch.empty_like(psi) if out is None else out
+    g = lat.c_geom()
+    _check(_L.hdcr_apply_cf_overlap(C_ref(g), float(M5), C_ref(_cf_params(beta, R)), _dev(U, "U"), _dev(psi, "psi"),
+                                    _dev(out, "out"), _code(psi), n, _stream(stream)), "apply_cf_overlap")
+    return out
+
+
+def cf_cr_solve(lat: Lattice, U: torch.Tensor, b: torch.Tensor, M5: float, beta, R: float, tol: float = 1e-10,
+                max_iter: int = 100000, stream=None):
+    """CR on the continued-fraction operator.  Returns (x, stats dict)."""
+    x = torch.zeros_like(b)
+    st = _lib.hdcr_solve_stats()
+    g = lat.c_geom()
+    _check(_L.hdcr_cf_cr_solve(C_ref(g), float(M5), C_ref(_cf_params(beta, R)), _dev(U, "U"), _dev(b, "b"),
+                               _dev(x, "x"), _code(b), float(tol), int(max_iter), C_ref(st), _stream(stream)),
+           "cf_cr_solve")
+    return x, st.as_dict()
 
 
 def h16_bytes(lat: Lattice) -> int:
@@ -569,6 +605,54 @@ def coarse_solve_dense(co: CoarseOperator, c: torch.Tensor, stream=None) -> torc
     return out
 
 
+def build_level2(co: CoarseOperator, noise: torch.Tensor, block, nvec2: int | None = None, smooth_iters: int = 10,
+                 cycle_smooth: int = 4, stream=None) -> None:
+    """The third level of the coarse solve (Section 4's construction applied to A, the
+    recursion of Section 5): level-2 basis from nvec2/2 complex128 coarse noise vectors
+    (shape (nvec2/2, Vc, nvec)), blocks of ``block`` coarse sites, A2 and its dense
+    inverse, kept in ``co`` for coarse_solver="recursive"."""
+    if noise.dtype != torch.complex128:
+        raise TypeError("level-2 noise must be complex128")
+    per = co.sub.Vc * co.sub.nvec
+    half = noise.numel() // per
+    if noise.numel() != half * per or half < 1:
+        raise ValueError("noise must hold nvec2/2 coarse vectors")
+    prm = _lib.hdcr_level2_params()
+    prm.nvec2 = int(nvec2 if nvec2 is not None else 2 * half)
+    for i in range(4):
+        prm.block[i] = int(block[i])
+    prm.smooth_iters = int(smooth_iters)
+    prm.cycle_smooth = int(cycle_smooth)
+    _check(_L.hdcr_coarse_build_level2(co.handle, C_ref(prm), _dev(noise, "noise", True), _stream(stream)),
+           "build_level2")
+
+
+def level2_get(co: CoarseOperator, stream=None):
+    """(basis, A2) of the third level as complex128: (nvec2, Vc, nvec) and (Vc2, 9, nvec2, nvec2)."""
+    n2 = ctypes.c_int()
+    L2 = (ctypes.c_int * 4)()
+    _check(_L.hdcr_coarse_level2_info(co.handle, ctypes.byref(n2), L2), "level2_info")
+    if n2.value == 0:
+        raise ValueError("the coarse operator has no third level")
+    Vc2 = L2[0] * L2[1] * L2[2] * L2[3]
+    dev = co.sub.device
+    vec = torch.empty((n2.value, co.sub.Vc, co.sub.nvec), dtype=torch.complex128, device=dev)
+    op = torch.empty((Vc2, 9, n2.value, n2.value), dtype=torch.complex128, device=dev)
+    _check(_L.hdcr_coarse_level2_get(co.handle, vec.data_ptr(), op.data_ptr(), _stream(stream)), "level2_get")
+    return vec, op
+
+
+def coarse_solve_level2(co: CoarseOperator, c: torch.Tensor, tol: float = 1e-10, max_iter: int = 500,
+                        stream=None):
+    """A^{-1} c for one coarse vector (the operator's dtype) by the recursive solver;
+    returns (x, iterations)."""
+    out = torch.empty_like(c)
+    it = ctypes.c_int()
+    _check(_L.hdcr_coarse_solve_level2(co.handle, _dev(c, "c"), _dev(out, "out"), float(tol), int(max_iter),
+                                       ctypes.byref(it), _stream(stream)), "coarse_solve_level2")
+    return out, it.value
+
+
 def _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi, coarse_solver,
                   coarse_tol, coarse_max, inner_dtype):
     prm = _lib.hdcr_solve_params()
@@ -579,7 +663,8 @@ def _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, ch
     prm.smoother_order = int(smoother_order)
     prm.cheb_lo = float(cheb_lo)
     prm.cheb_hi = float(cheb_hi)
-    prm.coarse_solver = {"cr": _lib.HDCR_COARSE_CR, "dense": _lib.HDCR_COARSE_DENSE}[coarse_solver]
+    prm.coarse_solver = {"cr": _lib.HDCR_COARSE_CR, "dense": _lib.HDCR_COARSE_DENSE,
+                         "recursive": _lib.HDCR_COARSE_RECURSIVE}[coarse_solver]
     prm.coarse_tol = float(coarse_tol)
     prm.coarse_max = int(coarse_max)
     prm.inner_dtype = _dt(inner_dtype)

@@ -51,6 +51,15 @@ HDCR_SMOOTHER_CR = 0
 HDCR_SMOOTHER_CHEBYSHEV = 1
 HDCR_COARSE_CR = 0
 HDCR_COARSE_DENSE = 1
+HDCR_COARSE_RECURSIVE = 2
+
+
+class hdcr_level2_params(C.Structure):
+    _fields_ = [("nvec2", C.c_int), ("block", C.c_int * 4), ("smooth_iters", C.c_int), ("cycle_smooth", C.c_int)]
+
+
+class hdcr_cf_params(C.Structure):
+    _fields_ = [("ncomp", C.c_int), ("beta", C.c_double * 15), ("R", C.c_double)]
 
 
 class hdcr_subspace_params(C.Structure):
@@ -117,8 +126,14 @@ SIGNATURES = {
     "hdcr_coarse_invert": (_I, [_P, _P]),
     "hdcr_coarse_solve_dense": (_I, [_P, _P, _P, _I, _P]),
     "hdcr_coarse_destroy": (None, [_P]),
+    "hdcr_coarse_build_level2": (_I, [_P, C.POINTER(hdcr_level2_params), _P, _P]),
+    "hdcr_coarse_level2_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "hdcr_coarse_level2_get": (_I, [_P, _P, _P, _P]),
+    "hdcr_coarse_solve_level2": (_I, [_P, _P, _P, _D, _I, C.POINTER(C.c_int), _P]),
     "hdcr_solve": (_I, [_P, _P, _P, _P, C.POINTER(hdcr_solve_params), _ST, _P]),
     "hdcr_solve_multi": (_I, [_P, _P, _P, _P, _I, C.POINTER(hdcr_solve_params), _I, _ST, _P]),
+    "hdcr_apply_cf_overlap": (_I, [_G, _D, C.POINTER(hdcr_cf_params), _P, _P, _P, _I, _I, _P]),
+    "hdcr_cf_cr_solve": (_I, [_G, _D, C.POINTER(hdcr_cf_params), _P, _P, _P, _I, _D, _I, _ST, _P]),
     "hdcr_gauge_force": (_I, [_G, _P, _P, _P, _I, _P]),
     "hdcr_gauge_grad": (_I, [_G, _P, _P, _P, _I, _P]),
 }

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "host_io.cuh"
+#include "level2.cuh"
 #include "coarse.cuh"
 #include "coarse_tc.cuh"
 #include "dwf_stencil.cuh"
@@ -819,6 +820,7 @@ extern "C" void hdcr_coarse_destroy(hdcr_coarse* co) {
   if (co->nbr) cudaFree(co->nbr);
   if (co->Ainv) cudaFree(co->Ainv);
   if (co->dws) cudaFree(co->dws);
+  level2_free(co->l2);
   delete co;
 }
 

@@ -70,6 +70,10 @@ struct hdcr_subspace {
   mutable size_t build_ws_bytes = 0;
 };
 
+namespace hdcr {
+struct Level2;
+}
+
 struct hdcr_coarse {
   const hdcr_subspace* sub;  // borrowed: must outlive the coarse handle
   hdcr::Geom g;
@@ -81,6 +85,7 @@ struct hdcr_coarse {
   void* Ainv;   // dense inverse (FP32 complex, n = Vc*nvec, n x n) then its column gather index (n ints)
   void* dws;    // workspace of the multi-right-hand-side dense solve (grown on demand)
   size_t dws_bytes;
+  hdcr::Level2* l2;  // third level of the coarse solve (hdcr_coarse_build_level2), or null
   double M5, mf;
   int device;
 };

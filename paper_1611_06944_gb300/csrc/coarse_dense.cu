@@ -72,6 +72,7 @@ struct GJWork {
   unsigned int* counter;  // zero between launches
   int* perm;           // perm[k]: row interchanged with row k at step k
   int* status;         // 1 + k of the first zero or non-finite pivot
+  unsigned int* bar;   // grid barrier of the panel kernel: arrivals, generation, time-out flag
 };
 
 __device__ __forceinline__ float pivot_metric(cpx<float> v) {
@@ -86,12 +87,50 @@ __device__ __forceinline__ void better(float& m, int& i, float om, int oi) {
   }
 }
 
-// argmax over the CTA (largest metric, lowest row on ties), then over the grid:
-// the last CTA to finish picks the pivot of step k and records it in perm[k]
-__device__ void pivot_select(float m, int i, int k, const GJWork& w) {
-  __shared__ float sm[GJ_ROWS / 32];
-  __shared__ int si[GJ_ROWS / 32];
-  __shared__ bool last;
+// Grid-wide barrier of the cooperative panel kernel (all its CTAs are resident):
+// generation counting, every wait bounded.  A CTA that gives up sets bar[2]; the
+// kernel's result is then discarded (the host reports TIMEOUT).
+__device__ __forceinline__ bool gj_grid_barrier(unsigned int* bar, unsigned int& gen) {
+  __shared__ bool timed_out;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicExch(&bar[1], gen + 1u);
+    } else {
+      for (int it = 0; ((volatile unsigned int*)bar)[1] == gen; ++it) {
+        if (it > (1 << 22)) {
+          atomicExch(&bar[2], 1u);
+          break;
+        }
+        if (it > 32) __nanosleep(64);
+      }
+    }
+    __threadfence();
+    timed_out = ((volatile unsigned int*)bar)[2] != 0u;  // one reading for the whole CTA
+  }
+  __syncthreads();
+  ++gen;
+  return !timed_out;
+}
+
+// a complex FP32 number read through L2 only: other CTAs wrote it during this launch,
+// so a line this SM cached earlier may be stale
+__device__ __forceinline__ cpx<float> ldcg_c(const cpx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return cpx<float>(v.x, v.y);
+}
+
+constexpr int GJ_PARTS = 4;                    // threads sharing a row in the panel kernel
+constexpr int GJ_COOP_T = GJ_ROWS * GJ_PARTS;  // threads per CTA of the panel kernel
+
+// argmax over the CTA's threads, written to the CTA's candidate slot
+__device__ __forceinline__ void gj_cta_candidate(float m, int i, const GJWork& w) {
+  __shared__ float sm[GJ_COOP_T / 32];
+  __shared__ int si[GJ_COOP_T / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
@@ -102,128 +141,144 @@ __device__ void pivot_select(float m, int i, int k, const GJWork& w) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 1; q < GJ_ROWS / 32; ++q) better(m, i, sm[q], si[q]);
+    for (int q = 1; q < GJ_COOP_T / 32; ++q) better(m, i, sm[q], si[q]);
     w.cand_m[blockIdx.x] = m;
     w.cand_i[blockIdx.x] = i;
-    __threadfence();
-    last = atomicAdd(w.counter, 1u) == gridDim.x - 1;
   }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  m = -1.f;
-  i = INT_MAX;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += GJ_ROWS) better(m, i, __ldcg(w.cand_m + b), __ldcg(w.cand_i + b));
+}
+
+// the pivot of step k from every CTA's candidate (each CTA reduces them all, in the
+// same order, so all agree); CTA 0 records it
+__device__ __forceinline__ int gj_grid_pivot(int k, const GJWork& w) {
+  __shared__ float sm[GJ_COOP_T / 32];
+  __shared__ int si[GJ_COOP_T / 32];
+  __shared__ int piv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float m = -1.f;
+  int i = INT_MAX;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += GJ_COOP_T) better(m, i, __ldcg(w.cand_m + b), __ldcg(w.cand_i + b));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
     better(m, i, __shfl_down_sync(0xffffffffu, m, off), __shfl_down_sync(0xffffffffu, i, off));
-  __syncthreads();
   if (lane == 0) {
     sm[warp] = m;
     si[warp] = i;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 1; q < GJ_ROWS / 32; ++q) better(m, i, sm[q], si[q]);
+    for (int q = 1; q < GJ_COOP_T / 32; ++q) better(m, i, sm[q], si[q]);
     if (!(m > 0.f) || !(m < 3.0e38f)) {
-      atomicCAS(w.status, 0, 1 + k);
+      if (blockIdx.x == 0) atomicCAS(w.status, 0, 1 + k);
       i = k;  // carry on without an interchange; the result is discarded
     }
-    w.perm[k] = i;
-    *w.counter = 0u;
+    if (blockIdx.x == 0) w.perm[k] = i;
+    piv = i;
   }
+  __syncthreads();
+  return piv;
 }
 
-// Start of a panel: W = M[:, k0:k0+pw] (zero beyond pw), U = 0, pivot of step k0.
-__global__ void __launch_bounds__(GJ_ROWS) gj_panel_init_kernel(const cpx<float>* __restrict__ M, int n, int k0,
-                                                                int pw, GJWork w) {
-  const int i = blockIdx.x * GJ_ROWS + threadIdx.x;
+// One whole panel in one cooperative launch: W = M[:, k0:k0+pw], U = 0, then the pw
+// steps of gj_step_kernel with the pivot searches and the hand-over between steps
+// done through a grid barrier instead of a launch per step.  Each row is shared by
+// GJ_PARTS threads, which take every GJ_PARTS-th panel column (rows grid-stride).
+__global__ void __launch_bounds__(GJ_COOP_T) gj_panel_coop_kernel(const cpx<float>* __restrict__ M, int n, int k0,
+                                                                  int pw, GJWork w) {
+  __shared__ cpx<float> rk[GJ_P], ruk[GJ_P];
+  __shared__ cpx<float> rp[GJ_P], rup[GJ_P];
+  unsigned int gen = ((volatile unsigned int*)w.bar)[1];
+  const int t = threadIdx.x;
+  const int rl = t % GJ_ROWS, part = t / GJ_ROWS;  // row of the CTA's chunk, column share
+  const int stride = gridDim.x * GJ_ROWS;
   float m = -1.f;
   int bi = INT_MAX;
-  if (i < n) {
+  for (int i = blockIdx.x * GJ_ROWS + rl; i < n; i += stride) {
     const cpx<float>* row = M + (long long)i * n + k0;
-#pragma unroll 8
-    for (int c = 0; c < GJ_P; ++c) {
+    for (int c = part; c < GJ_P; c += GJ_PARTS) {
       const cpx<float> v = c < pw ? row[c] : cpx<float>(0.f, 0.f);
       w.W[0][(long long)c * n + i] = v;
       w.U[0][(long long)c * n + i] = cpx<float>(0.f, 0.f);
       w.U[1][(long long)c * n + i] = cpx<float>(0.f, 0.f);
-      if (c == 0 && i >= k0) {
-        m = pivot_metric(v);
-        bi = i;
-      }
+      if (c == 0 && i >= k0) better(m, bi, pivot_metric(v), i);
     }
   }
-  pivot_select(m, bi, k0, w);
-}
-
-// Step k = k0 + l of the panel.  Rows k and p = perm[k] are interchanged on the
-// fly (each CTA reads both from the input buffer), then every row i gets
-//   u_i = -W[i][l] / W[k][l]  (u_k = 1 / W[k][l] - 1),
-//   W[i][c] += u_i W[k][c] for c != l,  W[i][l] = [i == k] + u_i,
-//   U[i][c] += u_i U[k][c] for c < l,   U[i][l] = u_i,
-// and the CTAs together pick the pivot of step k + 1 from the new column l + 1.
-__global__ void __launch_bounds__(GJ_ROWS) gj_step_kernel(int n, int k0, int l, int pw, GJWork w) {
-  __shared__ cpx<float> rk[GJ_P], ruk[GJ_P];  // new row k (old row p)
-  __shared__ cpx<float> rp[GJ_P], rup[GJ_P];  // new row p (old row k)
-  const int k = k0 + l;
-  const int p = w.perm[k];
-  const bool odd = l & 1;
-  const cpx<float>* __restrict__ Win = odd ? w.W[1] : w.W[0];
-  const cpx<float>* __restrict__ Uin = odd ? w.U[1] : w.U[0];
-  cpx<float>* __restrict__ Wout = odd ? w.W[0] : w.W[1];
-  cpx<float>* __restrict__ Uout = odd ? w.U[0] : w.U[1];
-  const int t = threadIdx.x;
-  for (int c = t; c < GJ_P; c += GJ_ROWS) {  // the panel may be wider than the CTA
-    rk[c] = Win[(long long)c * n + p];
-    ruk[c] = Uin[(long long)c * n + p];
-    rp[c] = Win[(long long)c * n + k];
-    rup[c] = Uin[(long long)c * n + k];
-  }
-  __syncthreads();
-  const cpx<float> d = rk[l];
-  const float dm = d.re * d.re + d.im * d.im;
-  const float inv = dm > 0.f ? 1.f / dm : 0.f;
-  const cpx<float> pinv(d.re * inv, -d.im * inv);
-  const int i = blockIdx.x * GJ_ROWS + t;
-  float m = -1.f;
-  int bi = INT_MAX;
-  if (i < n) {
-    const bool is_k = i == k, is_p = i == p && p != k;
-    const cpx<float>* src = Win + i;
-    const cpx<float>* srcu = Uin + i;
-    auto wsrc = [&](int c) { return is_k ? rk[c] : (is_p ? rp[c] : src[(long long)c * n]); };
-    auto usrc = [&](int c) { return is_k ? ruk[c] : (is_p ? rup[c] : srcu[(long long)c * n]); };
-    const cpx<float> wl = wsrc(l);
-    const cpx<float> u = is_k ? cpx<float>(pinv.re - 1.f, pinv.im)
-                              : cpx<float>(-(wl.re * pinv.re - wl.im * pinv.im), -(wl.re * pinv.im + wl.im * pinv.re));
-#pragma unroll 8
-    for (int c = 0; c < GJ_P; ++c) {
-      cpx<float> v;
-      if (c == l) {
-        v = cpx<float>(u.re + (is_k ? 1.f : 0.f), u.im);
-      } else {
-        v = wsrc(c);
-        const cpx<float> r = rk[c];
+  for (int l = 0; l < pw; ++l) {
+    const int k = k0 + l;
+    gj_cta_candidate(m, bi, w);
+    if (!gj_grid_barrier(w.bar, gen)) return;  // a barrier timed out: give up (the result is discarded)
+    const int p = gj_grid_pivot(k, w);
+    const bool odd = l & 1;
+    const cpx<float>* Win = odd ? w.W[1] : w.W[0];
+    const cpx<float>* Uin = odd ? w.U[1] : w.U[0];
+    cpx<float>* Wout = odd ? w.W[0] : w.W[1];
+    cpx<float>* Uout = odd ? w.U[0] : w.U[1];
+    for (int c = t; c < GJ_P; c += GJ_COOP_T) {
+      rk[c] = ldcg_c(Win + (long long)c * n + p);
+      ruk[c] = ldcg_c(Uin + (long long)c * n + p);
+      rp[c] = ldcg_c(Win + (long long)c * n + k);
+      rup[c] = ldcg_c(Uin + (long long)c * n + k);
+    }
+    __syncthreads();
+    const cpx<float> d = rk[l];
+    const float dm = d.re * d.re + d.im * d.im;
+    const float inv = dm > 0.f ? 1.f / dm : 0.f;
+    const cpx<float> pinv(d.re * inv, -d.im * inv);
+    m = -1.f;
+    bi = INT_MAX;
+    for (int i = blockIdx.x * GJ_ROWS + rl; i < n; i += stride) {
+      const bool is_k = i == k, is_p = i == p && p != k;
+      auto wsrc = [&](int c) { return is_k ? rk[c] : (is_p ? rp[c] : ldcg_c(Win + (long long)c * n + i)); };
+      auto usrc = [&](int c) { return is_k ? ruk[c] : (is_p ? rup[c] : ldcg_c(Uin + (long long)c * n + i)); };
+      const cpx<float> wl = wsrc(l);  // every part of the row forms the same multiplier
+      const cpx<float> u = is_k ? cpx<float>(pinv.re - 1.f, pinv.im)
+                                : cpx<float>(-(wl.re * pinv.re - wl.im * pinv.im), -(wl.re * pinv.im + wl.im * pinv.re));
+      for (int c = part; c < pw; c += GJ_PARTS) {
+        cpx<float> v;
+        if (c == l) {
+          v = cpx<float>(u.re + (is_k ? 1.f : 0.f), u.im);
+        } else {
+          v = wsrc(c);
+          const cpx<float> r = rk[c];
+          v.re += u.re * r.re - u.im * r.im;
+          v.im += u.re * r.im + u.im * r.re;
+        }
+        Wout[(long long)c * n + i] = v;
+        if (c == l + 1 && i > k) better(m, bi, pivot_metric(v), i);
+      }
+      for (int c = part; c < l; c += GJ_PARTS) {
+        cpx<float> v = usrc(c);
+        const cpx<float> r = ruk[c];
         v.re += u.re * r.re - u.im * r.im;
         v.im += u.re * r.im + u.im * r.re;
+        Uout[(long long)c * n + i] = v;
       }
-      Wout[(long long)c * n + i] = v;
-      if (c == l + 1 && i > k) {
-        m = pivot_metric(v);
-        bi = i;
-      }
+      if (l % GJ_PARTS == part) Uout[(long long)l * n + i] = u;
     }
-    for (int c = 0; c < l; ++c) {
-      cpx<float> v = usrc(c);
-      const cpx<float> r = ruk[c];
-      v.re += u.re * r.re - u.im * r.im;
-      v.im += u.re * r.im + u.im * r.re;
-      Uout[(long long)c * n + i] = v;
-    }
-    Uout[(long long)l * n + i] = u;
+    __syncthreads();  // rk .. rup are refilled by the next step
   }
-  if (l + 1 < pw) pivot_select(m, bi, k + 1, w);
+}
+
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// The operands of the rank-pw update as three-term TF32 products (3xTF32): with
+// x = hi(x) + lo(x), hi the TF32 truncation, U T ~ hi(U) hi(T) + hi(U) lo(T) + lo(U) hi(T),
+// which one GEMM with K = 3 pw computes from Ucat = [hi U | hi U | lo U] and
+// Tcat = [hi T | lo T | hi T] (both n x 3pw, column-major with leading dimension n).
+__global__ void gj_split3_kernel(const cpx<float>* __restrict__ U, const cpx<float>* __restrict__ T, int n, int pw,
+                                 cpx<float>* __restrict__ Ucat, cpx<float>* __restrict__ Tcat) {
+  const long long total = (long long)n * pw;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const cpx<float> u = U[e], t = T[e];
+    const cpx<float> uh(tf32_trunc(u.re), tf32_trunc(u.im)), th(tf32_trunc(t.re), tf32_trunc(t.im));
+    const cpx<float> ul(u.re - uh.re, u.im - uh.im), tl(t.re - th.re, t.im - th.im);
+    Ucat[e] = uh;
+    Ucat[e + total] = uh;
+    Ucat[e + 2 * total] = ul;
+    Tcat[e] = th;
+    Tcat[e + total] = tl;
+    Tcat[e + 2 * total] = th;
+  }
 }
 
 // End of a panel, before the update: the panel's row interchanges on every
@@ -347,7 +402,7 @@ int launch_dense_solve(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int
   count_launch();
   HDCR_LAUNCH_CHECK();
   // out (column-major n x nrhs) = M xg, M row-major = (its column-major view)^T
-  HDCR_TRY(cgemm_tc('T', 'N', n, nrhs, n, 1.f, M, n, xg, n, 0.f, y32, n, st));
+  HDCR_TRY(cgemm_tc('T', 'N', n, nrhs, n, 1.f, M, n, xg, n, 0.f, y32, n, st, TC_BF16X9));
   if (sizeof(R) == 8) {
     dense_out_kernel<R><<<num_blocks(tot, 256, 4096), 256, 0, st>>>(y32, out, tot);
     count_launch();
@@ -372,8 +427,8 @@ int coarse_invert(hdcr_coarse* co, cudaStream_t st) {
   void* aux = nullptr;
   HDCR_CUDA_TRY(cudaMalloc(&M, mbytes + sizeof(int) * (size_t)n));
   const long long na = (long long)Vc * NLEGS * nvec * nvec;
-  const size_t abytes = sizeof(cpx<float>) * (size_t)(5 * n * GJ_P + na) +
-                        sizeof(float) * GJ_MAX_CTAS + sizeof(int) * (size_t)(GJ_MAX_CTAS + n + 2) + 256;
+  const size_t abytes = sizeof(cpx<float>) * (size_t)(11 * n * GJ_P + na) +
+                        sizeof(float) * GJ_MAX_CTAS + sizeof(int) * (size_t)(GJ_MAX_CTAS + n + 5) + 256;
   cudaError_t e = cudaMalloc(&aux, abytes);
   if (e != cudaSuccess) {
     cudaFree(M);
@@ -386,32 +441,51 @@ int coarse_invert(hdcr_coarse* co, cudaStream_t st) {
   w.U[0] = base + 2 * n * GJ_P;
   w.U[1] = base + 3 * n * GJ_P;
   w.T = base + 4 * n * GJ_P;
-  cpx<float>* A32 = base + 5 * n * GJ_P;
+  cpx<float>* Ucat = base + 5 * n * GJ_P;
+  cpx<float>* Tcat = base + 8 * n * GJ_P;
+  cpx<float>* A32 = base + 11 * n * GJ_P;
   w.cand_m = (float*)(A32 + na);
   w.cand_i = (int*)(w.cand_m + GJ_MAX_CTAS);
   w.perm = w.cand_i + GJ_MAX_CTAS;
   w.status = w.perm + n;
   w.counter = (unsigned int*)(w.status + 1);
+  w.bar = w.counter + 1;
   int s = HDCR_OK;
   e = cudaMemsetAsync(M, 0, mbytes, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st);  // status and counter
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 5 * sizeof(int), st);  // status, counter, barrier
   if (e != cudaSuccess) s = cuda_status(e, "dense coarse inverse: clear");
   if (s == HDCR_OK) s = launch_convert(co->A, co->dtype, A32, HDCR_C64, na, st);
   if (s == HDCR_OK) {
     assemble_dense_kernel<<<num_blocks(na, 256, 8192), 256, 0, st>>>(A32, co->nbr, Vc, nvec, (cpx<float>*)M); count_launch();
-    const int ctas = (int)((n + GJ_ROWS - 1) / GJ_ROWS);
+    // the panel kernel runs cooperatively: as many CTAs as fit on the device at once
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_panel_coop_kernel, GJ_COOP_T, 0);
+    long long ctas = (n + GJ_ROWS - 1) / GJ_ROWS;
+    if (ctas > (long long)sms * per_sm) ctas = (long long)sms * per_sm;
+    if (ctas > GJ_MAX_CTAS) ctas = GJ_MAX_CTAS;
     s = gemm_prepare();
     for (long long k0 = 0; k0 < n && s == HDCR_OK; k0 += GJ_P) {
       const int pw = (int)(n - k0 < GJ_P ? n - k0 : GJ_P);
-      gj_panel_init_kernel<<<ctas, GJ_ROWS, 0, st>>>((const cpx<float>*)M, (int)n, (int)k0, pw, w); count_launch();
-      for (int l = 0; l < pw; ++l) {
-        gj_step_kernel<<<ctas, GJ_ROWS, 0, st>>>((int)n, (int)k0, l, pw, w); count_launch();
+      const cpx<float>* Mc = (const cpx<float>*)M;
+      int ni = (int)n, k0i = (int)k0, pwi = pw;
+      void* args[] = {(void*)&Mc, (void*)&ni, (void*)&k0i, (void*)&pwi, (void*)&w};
+      e = cudaLaunchCooperativeKernel((const void*)gj_panel_coop_kernel, dim3((unsigned)ctas), dim3(GJ_COOP_T), args,
+                                      0, st);
+      count_launch();
+      if (e != cudaSuccess) {
+        s = cuda_status(e, "Gauss-Jordan panel (cooperative launch)");
+        break;
       }
       gj_panel_swap_kernel<<<num_blocks(n, 256, 4096), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw, w);
       count_launch();
       // M[i][j] += sum_c U[i][c] T[c][j]: in the column-major view (M^T) that is T^T U^T, with
-      // T^T (n x pw) and U (n x pw) both stored column-major with leading dimension n
-      s = cgemm_tc('N', 'T', (int)n, (int)n, pw, 1.f, w.T, n, w.U[pw & 1], n, 1.f, (cpx<float>*)M, n, st);
+      // T^T (n x pw) and U (n x pw) both stored column-major with leading dimension n; as
+      // three TF32 products in one GEMM of K = 3 pw on the tensor cores
+      gj_split3_kernel<<<num_blocks(n * pw, 256, 4096), 256, 0, st>>>(w.U[pw & 1], w.T, (int)n, pw, Ucat, Tcat);
+      count_launch();
+      s = cgemm_tc('N', 'T', (int)n, (int)n, 3 * pw, 1.f, Tcat, n, Ucat, n, 1.f, (cpx<float>*)M, n, st, TC_TF32);
       gj_panel_store_kernel<<<num_blocks(n * pw, 256, 4096), 256, 0, st>>>((cpx<float>*)M, (int)n, (int)k0, pw,
                                                                           w.W[pw & 1]);
       count_launch();
@@ -420,12 +494,17 @@ int coarse_invert(hdcr_coarse* co, cudaStream_t st) {
     if (e != cudaSuccess) s = cuda_status(e, "Gauss-Jordan elimination");
   }
   std::vector<int> hperm(n);
-  int hstatus = 0;
+  int hstatus = 0, htimeout = 0;
   if (s == HDCR_OK) {
     e = cudaMemcpyAsync(hperm.data(), w.perm, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, w.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&htimeout, w.bar + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = cuda_status(e, "Gauss-Jordan pivots");
+  }
+  if (s == HDCR_OK && htimeout != 0) {
+    set_error("dense coarse inverse: a grid barrier of the panel kernel timed out");
+    s = HDCR_ERR_TIMEOUT;
   }
   if (s == HDCR_OK && hstatus != 0) {
     set_error("dense coarse inverse: zero or non-finite pivot at column %d", hstatus - 1);

@@ -66,7 +66,8 @@ int gemm_prepare() {
 }
 
 int cgemm_tc(char ta, char tb, int m, int n, int k, float alpha, const cpx<float>* A, long long lda,
-             const cpx<float>* B, long long ldb, float beta, cpx<float>* C, long long ldc, cudaStream_t st) {
+             const cpx<float>* B, long long ldb, float beta, cpx<float>* C, long long ldc, cudaStream_t st,
+             TcMode mode) {
   if (m == 0 || n == 0) return HDCR_OK;
   cublasHandle_t h;
   HDCR_TRY(handle_of(&h));
@@ -78,15 +79,17 @@ int cgemm_tc(char ta, char tb, int m, int n, int k, float alpha, const cpx<float
   g_calls.fetch_add(1);
   const cuComplex a = make_cuComplex(alpha, 0.f), b = make_cuComplex(beta, 0.f);
   const cublasOperation_t oa = ta == 'T' ? CUBLAS_OP_T : CUBLAS_OP_N, ob = tb == 'T' ? CUBLAS_OP_T : CUBLAS_OP_N;
+  const cublasComputeType_t ct =
+      mode == TC_TF32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
   s = cublasGemmEx(h, oa, ob, m, n, k, &a, A, CUDA_C_32F, (int)lda, B, CUDA_C_32F, (int)ldb, &b, C, CUDA_C_32F,
-                   (int)ldc, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+                   (int)ldc, ct, CUBLAS_GEMM_DEFAULT);
   if (s == CUBLAS_STATUS_NOT_SUPPORTED) {
     // a shape the emulated path does not take (e.g. its workspace would not fit): plain FP32
     g_fallbacks.fetch_add(1);
     s = cublasGemmEx(h, oa, ob, m, n, k, &a, A, CUDA_C_32F, (int)lda, B, CUDA_C_32F, (int)ldb, &b, C, CUDA_C_32F,
                      (int)ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
   }
-  if (s != CUBLAS_STATUS_SUCCESS) return blas_status(s, "cublasGemmEx (complex FP32 on BF16x9 tensor cores)");
+  if (s != CUBLAS_STATUS_SUCCESS) return blas_status(s, "cublasGemmEx (complex FP32 on the tensor cores)");
   count_launch();
   return HDCR_OK;
 }

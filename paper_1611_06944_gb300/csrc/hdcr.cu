@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "host_io.cuh"
+#include "level2.cuh"
 #include "chebyshev.cuh"
 #include "coarse.cuh"
 
@@ -229,6 +230,13 @@ static int smooth(const FineOp<R>& H, SolveCache* c, const hdcr_solve_params* pr
 template <typename R>
 static int coarse_solve(const hdcr_coarse* co, SolveCache* c, const hdcr_solve_params* prm, VStats* vs,
                         cudaStream_t st) {
+  if (prm->coarse_solver == HDCR_COARSE_RECURSIVE) {
+    int it = 0;
+    HDCR_TRY(level2_solve<R>(co, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, prm->coarse_tol, prm->coarse_max, &it,
+                             st));
+    vs->coarse += it;
+    return HDCR_OK;
+  }
   if (prm->coarse_solver == HDCR_COARSE_DENSE) {
     vs->coarse_dense++;
     return launch_dense_solve<R>(co, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, 1, st);
@@ -445,7 +453,8 @@ static int solve_entry(hdcr_coarse* co, const void* U, const void* b, void* x, c
   if (!(prm->tol > 0.0) || prm->max_outer < 1 || prm->restart < 1 || prm->restart > 64 ||
       prm->smoother_order < 0 || !(prm->coarse_tol > 0.0) || prm->coarse_max < 1 ||
       (prm->smoother_kind != HDCR_SMOOTHER_CR && prm->smoother_kind != HDCR_SMOOTHER_CHEBYSHEV) ||
-      (prm->coarse_solver != HDCR_COARSE_CR && prm->coarse_solver != HDCR_COARSE_DENSE)) {
+      (prm->coarse_solver != HDCR_COARSE_CR && prm->coarse_solver != HDCR_COARSE_DENSE &&
+       prm->coarse_solver != HDCR_COARSE_RECURSIVE)) {
     set_error("hdcr_solve: bad parameters");
     return HDCR_ERR_BAD_ARG;
   }
@@ -464,6 +473,10 @@ static int solve_entry(hdcr_coarse* co, const void* U, const void* b, void* x, c
     return HDCR_ERR_BAD_ARG;
   }
   if (prm->coarse_solver == HDCR_COARSE_DENSE && !co->Ainv) HDCR_TRY(coarse_invert(co, as_stream(stream)));
+  if (prm->coarse_solver == HDCR_COARSE_RECURSIVE && !co->l2) {
+    set_error("hdcr_solve: the recursive coarse solve needs a third level (hdcr_coarse_build_level2)");
+    return HDCR_ERR_BAD_ARG;
+  }
   cudaStream_t st = as_stream(stream);
   SolveCache* cache = nullptr;
   {
