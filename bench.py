@@ -82,7 +82,7 @@ def bytes_per_site(real_bytes: int, Ls: int) -> float:
 
 # DRAM traffic of one FP64 / FP32 / FP16-storage stencil launch at 16^4 x 16 from ncu, with the hash of
 # the stencil sources it was measured on (reported as null once the sources change)
-NCU_TRAFFIC = {"f64": 451.63e6, "f32": 203.95e6, "h16": 106.12e6, "src_hash": "93e5f49c49aabef4"}
+NCU_TRAFFIC = {"f64": 453.70e6, "f32": 202.68e6, "h16": 106.41e6, "src_hash": "b199c32a821e8083"}
 
 
 def stencil_src_hash() -> str:
@@ -636,8 +636,10 @@ def run_precision(args, world, rank, local):
     # on this lattice; the paper's own filter is O(500-900))
     filt = dict(kind="chebyshev", order=600, lam_cut=0.1, lam_max=8.0, filter_dtype=torch.complex64,
                 store_dtype=torch.complex64)
-    # 6^4 blocks (coarse 4^3 x 8, 16384 unknowns): the dense coarse inverse applies; with
-    # 4^4 blocks (82944 unknowns) only the coarse CR does, and it stalls the solve here
+    # 6^4 blocks (coarse 4^3 x 8, 16384 unknowns): the dense coarse inverse applies.  With
+    # 4^4 blocks (82944 unknowns, beyond the dense inverse) the coarse solve is the recursive
+    # one (measured below); coarse CR to 1e-6 also converges but needs ~3000 CR iterations
+    # per coarse solve
     block = (6, 6, 6, 6)
     solve = dict(tol=1e-10, restart=8, smoother="chebyshev", smoother_order=10, cheb_lo=1.0, cheb_hi=64.0,
                  coarse_solver="dense", max_outer=300, inner_dtype=torch.complex64)
@@ -679,12 +681,13 @@ def run_precision(args, world, rank, local):
                              "exact": _coarse_rebuild(hd, sub4, U, mf, False, f32["us"] * 1e-3)}
     co4, t_co4 = _sync_time(lambda: hd.build_coarse_op(sub4, U, M5, mf, op_dtype=torch.complex64, fast=True))
     cvec = sub4.Vc * nvec                        # one coarse vector
-    n2 = synth.device_gaussian(16, -(-cvec // 12), 3012)[:, :cvec].reshape(16, sub4.Vc, nvec).contiguous()
-    _, t_l2 = _sync_time(lambda: hd.build_level2(co4, n2, (2, 2, 2, 2), smooth_iters=10, cycle_smooth=4))
-    solve4 = dict(solve, coarse_solver="recursive", coarse_tol=1e-8, coarse_max=200)
+    half2 = 32                                   # 64 level-2 vectors
+    n2 = synth.device_gaussian(half2, -(-cvec // 12), 3012)[:, :cvec].reshape(half2, sub4.Vc, nvec).contiguous()
+    _, t_l2 = _sync_time(lambda: hd.build_level2(co4, n2, (2, 2, 2, 2), smooth_iters=200, cycle_smooth=16))
+    solve4 = dict(solve, coarse_solver="recursive", coarse_tol=1e-6, coarse_max=100)
     (x4, st4), t_solve4 = _sync_time(lambda: hd.hdcr_solve(co4, U, b, **solve4))
     recursive = {"blocks": list(BLOCK), "coarse_unknowns": sub4.Vc * nvec, "level2_blocks": [2, 2, 2, 2],
-                 "level2_unknowns": sub4.Vc // 16 * 32, "subspace_s": round(t_sub4, 3),
+                 "level2_unknowns": sub4.Vc // 16 * 2 * half2, "subspace_s": round(t_sub4, 3),
                  "coarse_op_s": round(t_co4, 4), "level2_build_s": round(t_l2, 3), "solve_s": round(t_solve4, 3),
                  "outer_iters": st4["iters"], "coarse_gcr_iters": st4["coarse_matvecs"],
                  "true_resid": st4["true_resid"], "fine_matvecs_f32": st4["fine_matvecs_lo"],
@@ -929,6 +932,8 @@ def run_stencil(args, world, rank, local):
     if h16:
         x = hd.encode_h16(lat, x)
     y = torch.empty_like(x)
+    if args.variant >= 0:
+        hd.stencil_tune(0, args.variant)
     apply = (lambda: hd.apply_g5dwf_h16(lat, U, x, M5, MF, out=y)) if h16 else \
         (lambda: hd.apply_g5dwf(lat, U, x, M5, MF, out=y))
     for _ in range(reps):
@@ -940,6 +945,7 @@ def run_stencil(args, world, rank, local):
     torch.cuda.synchronize()
     t = hd.stencil_timer_read("h16" if h16 else dt)
     hd.stencil_timer(False)
+    chosen = hd.stencil_tune_info(lat, args.nrhs)["variant"] if dtype == "f32" and args.variant < 0 else args.variant
     us = t["ms"] / max(t["launches"], 1) * 1e3
     real = 4 if dt == torch.complex64 else 8
     per_site = 2 * 24 * real + 4 * 18 * real / LS / args.nrhs  # psi in + out, links shared by the Ls sites
@@ -948,7 +954,7 @@ def run_stencil(args, world, rank, local):
     gbs = lat.V5 * args.nrhs * per_site / (us * 1e-6) / 1e9
     return {"workload_kind": "stencil", "lattice": list(L), "Ls": LS, "dtype": dtype, "nrhs": args.nrhs,
             "us_per_launch": round(us, 2), "GBs": round(gbs, 1), "frac_of_hbm": round(gbs / peaks()["hbm_gbs"], 4),
-            "bytes_per_site": per_site, "launches": t["launches"]}
+            "bytes_per_site": per_site, "launches": t["launches"], "variant": chosen}
 
 
 def run_coarse(args, world, rank, local):
@@ -1010,6 +1016,8 @@ def main(argv=None) -> int:
     ap.add_argument("--nvec", type=int, default=24, help="coarse: basis vectors")
     ap.add_argument("--nrhs", type=int, default=1, help="stencil: fields per launch")
     ap.add_argument("--reps", type=int, default=4, help="stencil/coarse: timed launches or builds")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="stencil f32: run this tile variant (0-5 L1-tiled, 6 TMA-staged) instead of tuning")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":

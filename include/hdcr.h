@@ -397,7 +397,12 @@ int hdcr_coarse_solve_level2(const hdcr_coarse* co, const void* in, void* out, d
  * preconditioned by the two-level V-cycle
  *     z1 = S r;  z2 = z1 + P A^{-1} P^dag (r - H z1);  z = z2 + S (r - H z2).
  * For a linear smoother and an exact coarse solve this is the composite
- * M_outer = S P_L + P_R S + Q - S P_L H S of Section 4.  Smoothers:
+ * M_outer = S P_L + P_R S + Q - S P_L H S of Section 4 (``cycle`` =
+ * HDCR_CYCLE_SYMMETRIC).  HDCR_CYCLE_POST drops the first smoothing:
+ *     z1 = P A^{-1} P^dag r;  z = z1 + S (r - H z1),
+ * whose error propagator is (1 - S H)(1 - Q H): half the smoother's fine
+ * applications per cycle, not Hermitian (flexible GCR does not need it).
+ * Smoothers:
  *   HDCR_SMOOTHER_CR         ``smoother_order`` CR steps from zero (nonlinear);
  *   HDCR_SMOOTHER_CHEBYSHEV  S = H p(H^2), p the order-``smoother_order``
  *                            Chebyshev approximation of 1/y on
@@ -420,6 +425,8 @@ int hdcr_coarse_solve_level2(const hdcr_coarse* co, const void* in, void* out, d
 #define HDCR_COARSE_CR 0
 #define HDCR_COARSE_DENSE 1
 #define HDCR_COARSE_RECURSIVE 2 /* FGCR on A with the third level (hdcr_coarse_build_level2) */
+#define HDCR_CYCLE_SYMMETRIC 0  /* smoother before and after the coarse correction */
+#define HDCR_CYCLE_POST 1       /* coarse correction, then the smoother            */
 
 typedef struct {
   double tol;         /* true relative residual target, e.g. 1e-10           */
@@ -433,6 +440,7 @@ typedef struct {
   double coarse_tol;  /* relative residual of the coarse CR, e.g. 1e-4       */
   int coarse_max;     /* cap on coarse CR iterations                         */
   int inner_dtype;    /* HDCR_C128 or HDCR_C64                               */
+  int cycle;          /* HDCR_CYCLE_SYMMETRIC or HDCR_CYCLE_POST             */
 } hdcr_solve_params;
 
 int hdcr_solve(hdcr_coarse* co, const void* U, const void* b, void* x,

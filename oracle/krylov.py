@@ -1,8 +1,8 @@
 """Oracle: Krylov solvers for a Hermitian (indefinite) operator.
 
-* ``cr`` -- conjugate residual, the solver Section 3 of the paper builds on
-  ("relaxes the Hermitian positive definite constraint of conjugate
-  gradients to only Hermitian indefinite").  The paper does not print the
+* ``cr`` -- conjugate residual, the solver Section 3 of the paper builds on:
+  unlike conjugate gradients it needs the operator to be Hermitian only, not
+  positive definite.  The paper does not print the
   recursion; the textbook form used here is:
 
       r = b - A x,  p = r,  Ar = A r,  Ap = Ar,  gamma = <r, Ar>

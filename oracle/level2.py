@@ -8,8 +8,8 @@ Section 4 is repeated with the coarse operator A (Eq. 4.5) in place of H and the
 coarse lattice in place of the fine one.
 
 1. Level-2 vectors: Gaussian noise on the coarse lattice, each smoothed by a
-   fixed number of conjugate-residual steps on A x = 0 (the "inverse iteration
-   applied to Gaussian noise" of Section 4 with A for H), then normalised.
+   fixed number of conjugate-residual steps on A x = 0 (Section 4's inverse
+   iteration on Gaussian noise, with A in place of H), then normalised.
 2. Chiral split with the coarse Gamma5.  Every level-1 basis vector has definite
    Gamma5 chirality (the nvec/2 P_+ vectors first, then the P_- ones), so
    P^dag Gamma5 P = Gamma5c = diag(+1 x nvec/2, -1 x nvec/2) on every coarse site;

@@ -2,12 +2,13 @@
 
 Steps, in the paper's order and notation:
 
-1. Subspace vectors phi_k: "inverse iteration applied to Gaussian noise"
+1. Subspace vectors phi_k: inverse iteration on Gaussian noise vectors
    (Section 4, option i).  Reading: each noise vector x0 gets a fixed number
    of conjugate-residual iterations on H x = 0 starting from x0 (10 by
    default), then is normalised.
-2. Chiral split (Section 4, "projected into left handed and right handed
-   chiralities", a "gamma5 compatible approach" that removes near-zero
+2. Chiral split (Section 4: each vector is split into its left- and
+   right-handed parts, which keeps the coarse operator compatible with
+   gamma5 and removes near-zero
    eigenvalues of the coarse operator).  Reading: the chirality is that of
    Gamma5 = gamma5 R5, the involution with D_dwf^dag = Gamma5 D_dwf Gamma5
    (the 5d counterpart of gamma5 for Wilson fermions), so each vector v
@@ -16,7 +17,7 @@ Steps, in the paper's order and notation:
    |eigenvalue| of H, whereas a split by the 4d gamma5 alone creates spurious
    near-zero coarse eigenvalues (both shown in the tests).  Ordering read
    here: the nvec/2 P_+ vectors first, then the nvec/2 P_- vectors
-   ("chirality-major"); the coarse dimension is nvec.
+   (chirality-major); the coarse dimension is nvec.
 3. Block restriction phi_k^b (Eq. 4.1), blocks of ``block`` = (bx, by, bz, bt)
    sites times the full fifth dimension.
 4. Block orthonormalisation so that P_S = sum |phi_k^b><phi_k^b| (Eq. 4.3) is
@@ -299,17 +300,24 @@ def smoother(U, r, p: HDCRParams):
     return z
 
 
-def vcycle(U, sub: Subspace, A, r, p: HDCRParams, S=None, Qc=None):
+def vcycle(U, sub: Subspace, A, r, p: HDCRParams, S=None, Qc=None, cycle: str = "symmetric"):
     """B r = z2 + S (r - H z2),  z2 = z1 + Q (r - H z1),  z1 = S r  (Section 4).
 
     ``S`` (fine smoother) and ``Qc`` (coarse inverse on coarse vectors) may be
     replaced by callables, e.g. a linear smoother and an exact coarse solve.
+    cycle="post" (a reading, not the paper's composite): the first smoothing is
+    dropped, B r = z1 + S (r - H z1) with z1 = Q r.
     """
     H = lambda v: dwf.apply_H(U, v, p.M5, p.mf, p.bc_t)
     if S is None:
         S = lambda v: smoother(U, v, p)
     if Qc is None:
         Qc = lambda c: coarse_solve(A, sub.geom, c, p.coarse_tol, p.coarse_max)[0]
+    if cycle == "post":
+        z1 = prolong(sub, Qc(restrict(sub, r)))
+        return z1 + S(r - H(z1))
+    if cycle != "symmetric":
+        raise ValueError("cycle must be 'symmetric' or 'post'")
     z1 = S(r)
     r1 = r - H(z1)
     z2 = z1 + prolong(sub, Qc(restrict(sub, r1)))
@@ -327,8 +335,7 @@ def hdcr_solve(U, sub: Subspace, A, b, p: HDCRParams, x0=None):
 # ------------------------------------------------- Chebyshev variants (Section 4, Fig. 1)
 def chebyshev_inverse_coeffs(lo: float, hi: float, order: int) -> np.ndarray:
     """Coefficients c_0..c_order of the truncated Chebyshev series of f(y) = 1/y on
-    [lo, hi] (Section 4: "an order 10 Chebyshev polynomial approximation to 1/x in
-    the range [1.0, 64.0]"), from Chebyshev-Gauss quadrature with 4*(order+1) nodes:
+    [lo, hi] (Section 4's smoother: order 10 on [1, 64]), from Chebyshev-Gauss quadrature with 4*(order+1) nodes:
     p(y) = c_0/2 + sum_{k>=1} c_k T_k(t), t = (2y - hi - lo)/(hi - lo)."""
     m = 4 * (order + 1)
     theta = np.pi * (np.arange(m) + 0.5) / m

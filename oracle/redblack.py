@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Section 5 compares HDCR with "CGNE (red-black)" on the same operator (Table 1).
+Section 5 compares HDCR with red-black preconditioned CGNE on the same operator (Table 1).
 The paper does not write the red-black decomposition out; the standard one for
 the Shamir domain-wall operator of ``dwf`` is taken:
 

@@ -605,8 +605,8 @@ def coarse_solve_dense(co: CoarseOperator, c: torch.Tensor, stream=None) -> torc
     return out
 
 
-def build_level2(co: CoarseOperator, noise: torch.Tensor, block, nvec2: int | None = None, smooth_iters: int = 10,
-                 cycle_smooth: int = 4, stream=None) -> None:
+def build_level2(co: CoarseOperator, noise: torch.Tensor, block, nvec2: int | None = None, smooth_iters: int = 200,
+                 cycle_smooth: int = 16, stream=None) -> None:
     """The third level of the coarse solve (Section 4's construction applied to A, the
     recursion of Section 5): level-2 basis from nvec2/2 complex128 coarse noise vectors
     (shape (nvec2/2, Vc, nvec)), blocks of ``block`` coarse sites, A2 and its dense
@@ -654,7 +654,7 @@ def coarse_solve_level2(co: CoarseOperator, c: torch.Tensor, tol: float = 1e-10,
 
 
 def _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi, coarse_solver,
-                  coarse_tol, coarse_max, inner_dtype):
+                  coarse_tol, coarse_max, inner_dtype, cycle="symmetric"):
     prm = _lib.hdcr_solve_params()
     prm.tol = float(tol)
     prm.max_outer = int(max_outer)
@@ -668,6 +668,7 @@ def _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, ch
     prm.coarse_tol = float(coarse_tol)
     prm.coarse_max = int(coarse_max)
     prm.inner_dtype = _dt(inner_dtype)
+    prm.cycle = {"symmetric": _lib.HDCR_CYCLE_SYMMETRIC, "post": _lib.HDCR_CYCLE_POST}[cycle]
     return prm
 
 
@@ -676,13 +677,13 @@ def hdcr_solve_into(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x: tor
                     smoother: str = "chebyshev", smoother_order: int = 10, cheb_lo: float = 1.0,
                     cheb_hi: float = 64.0, coarse_solver: str = "dense", coarse_tol: float = 1e-4,
                     coarse_max: int = 1000, inner_dtype: torch.dtype = torch.complex128,
-                    stream=None) -> dict:
+                    cycle: str = "symmetric", stream=None) -> dict:
     """hdcr_solve with a caller-owned x (initial guess in, iterate out).  Returns the
     stats dict, including a failed solve's status, without raising."""
     if U.dtype != torch.complex128 or b.dtype != torch.complex128 or x.dtype != torch.complex128:
         raise TypeError("hdcr_solve takes complex128 links, source and solution")
     prm = _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi,
-                        coarse_solver, coarse_tol, coarse_max, inner_dtype)
+                        coarse_solver, coarse_tol, coarse_max, inner_dtype, cycle)
     st = _lib.hdcr_solve_stats()
     status = _L.hdcr_solve(co.handle, _dev(U, "U", True), _dev(b, "b", True), _dev(x, "x", True), C_ref(prm),
                            C_ref(st), _stream(stream))
@@ -695,10 +696,13 @@ def hdcr_solve(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x0: torch.T
                tol: float = 1e-10, max_outer: int = 500, restart: int = 8,
                smoother: str = "chebyshev", smoother_order: int = 10, cheb_lo: float = 1.0,
                cheb_hi: float = 64.0, coarse_solver: str = "dense", coarse_tol: float = 1e-4,
-               coarse_max: int = 1000, inner_dtype: torch.dtype = torch.complex128, stream=None):
+               coarse_max: int = 1000, inner_dtype: torch.dtype = torch.complex128, cycle: str = "symmetric",
+               stream=None):
     """H x = b by flexible GCR preconditioned with the two-level V-cycle (Section 4).
     smoother "chebyshev" (S = H p(H^2), p ~ 1/y on [cheb_lo, cheb_hi]) or "cr"
-    (smoother_order CR steps); coarse_solver "dense" (exact, FP32 inverse) or "cr".
+    (smoother_order CR steps); coarse_solver "dense" (exact, FP32 inverse), "cr" or
+    "recursive" (third level); cycle "symmetric" (smoother before and after the coarse
+    correction, Section 4's composite) or "post" (coarse correction, then smoother).
     Returns (x, stats dict); raises HDCRError when the solve fails."""
     if U.dtype != torch.complex128 or b.dtype != torch.complex128:
         raise TypeError("hdcr_solve takes complex128 links and source")
@@ -706,7 +710,7 @@ def hdcr_solve(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x0: torch.T
         raise ValueError("hdcr_solve takes one right-hand side")
     x = torch.zeros_like(b) if x0 is None else x0.clone()
     prm = _solve_params(tol, max_outer, restart, smoother, smoother_order, cheb_lo, cheb_hi,
-                        coarse_solver, coarse_tol, coarse_max, inner_dtype)
+                        coarse_solver, coarse_tol, coarse_max, inner_dtype, cycle)
     st = _lib.hdcr_solve_stats()
     _check(_L.hdcr_solve(co.handle, _dev(U, "U", True), _dev(b, "b", True), _dev(x, "x", True), C_ref(prm),
                          C_ref(st), _stream(stream)), "hdcr_solve")
@@ -717,7 +721,7 @@ def hdcr_solve(co: CoarseOperator, U: torch.Tensor, b: torch.Tensor, x0: torch.T
 def hdcr_solve_multi(co: CoarseOperator, U: torch.Tensor, B: torch.Tensor, x0: torch.Tensor | None = None,
                      tol: float = 1e-10, max_outer: int = 500, restart: int = 8, smoother_order: int = 10,
                      cheb_lo: float = 1.0, cheb_hi: float = 64.0, inner_dtype: torch.dtype = torch.complex128,
-                     graph: bool = True, stream=None):
+                     graph: bool = True, cycle: str = "symmetric", stream=None):
     """H x_r = b_r for the nrhs fields of B at once (the Section 4 solve batched over
     right-hand sides; Chebyshev smoother, dense coarse solve).  graph=True replays the
     V-cycle from a captured CUDA graph.  Returns (X, list of per-rhs stats dicts); raises
@@ -727,7 +731,7 @@ def hdcr_solve_multi(co: CoarseOperator, U: torch.Tensor, B: torch.Tensor, x0: t
     nrhs = _nfields(co.sub.lat, B, "B")
     X = torch.zeros_like(B) if x0 is None else x0.clone()
     prm = _solve_params(tol, max_outer, restart, "chebyshev", smoother_order, cheb_lo, cheb_hi, "dense", 1e-4,
-                        1000, inner_dtype)
+                        1000, inner_dtype, cycle)
     st = (_lib.hdcr_solve_stats * nrhs)()
     _check(_L.hdcr_solve_multi(co.handle, _dev(U, "U"), _dev(B, "B"), _dev(X, "X"), nrhs, C_ref(prm),
                                1 if graph else 0, st, _stream(stream)), "hdcr_solve_multi")

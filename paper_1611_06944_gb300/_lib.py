@@ -52,6 +52,8 @@ HDCR_SMOOTHER_CHEBYSHEV = 1
 HDCR_COARSE_CR = 0
 HDCR_COARSE_DENSE = 1
 HDCR_COARSE_RECURSIVE = 2
+HDCR_CYCLE_SYMMETRIC = 0
+HDCR_CYCLE_POST = 1
 
 
 class hdcr_level2_params(C.Structure):
@@ -75,7 +77,7 @@ class hdcr_solve_params(C.Structure):
         ("tol", C.c_double), ("max_outer", C.c_int), ("restart", C.c_int),
         ("smoother_kind", C.c_int), ("smoother_order", C.c_int), ("cheb_lo", C.c_double),
         ("cheb_hi", C.c_double), ("coarse_solver", C.c_int), ("coarse_tol", C.c_double),
-        ("coarse_max", C.c_int), ("inner_dtype", C.c_int),
+        ("coarse_max", C.c_int), ("inner_dtype", C.c_int), ("cycle", C.c_int),
     ]
 
 

@@ -266,6 +266,26 @@ static int vcycle(const hdcr_coarse* co, const FineOp<R>& H, SolveCache* c, cons
   cpx<R>* t2 = (cpx<R>*)c->t2;
   cpx<R>* e = (cpx<R>*)c->e;
   const int nb = num_blocks(fs, 256, 4096);
+  if (prm->cycle == HDCR_CYCLE_POST) {
+    // z1 = P A^{-1} P^dag r;  z = z1 + S (r - H z1)
+    HDCR_CUDA_TRY(cudaEventRecord(c->ev[0], st));
+    HDCR_CUDA_TRY(cudaEventRecord(c->ev[1], st));
+    HDCR_CUDA_TRY(cudaEventRecord(c->ev[2], st));
+    HDCR_TRY(launch_restrict<R>(co->sub, r, (cpx<R>*)c->c_rhs, 1, st));
+    HDCR_TRY(coarse_solve<R>(co, c, prm, vs, st));
+    HDCR_TRY(launch_prolong<R>(co->sub, (const cpx<R>*)c->c_sol, (const cpx<R>*)nullptr, z, 1, st));
+    HDCR_CUDA_TRY(cudaEventRecord(c->ev[3], st));
+    HDCR_TRY(H.apply(z, t1, st));
+    vs->fine++;
+    sub_kernel<R><<<nb, 256, 0, st>>>(r, t1, t2, fs); count_launch();
+    HDCR_LAUNCH_CHECK();
+    HDCR_CUDA_TRY(cudaEventRecord(c->ev[4], st));
+    HDCR_TRY(smooth<R>(H, c, prm, t2, e, vs, st));
+    add_kernel<R><<<nb, 256, 0, st>>>(z, e, fs); count_launch();
+    HDCR_LAUNCH_CHECK();
+    HDCR_CUDA_TRY(cudaEventRecord(c->ev[5], st));
+    return HDCR_OK;
+  }
   // z1 = S r
   HDCR_CUDA_TRY(cudaEventRecord(c->ev[0], st));
   HDCR_TRY(smooth<R>(H, c, prm, r, z, vs, st));
@@ -454,7 +474,8 @@ static int solve_entry(hdcr_coarse* co, const void* U, const void* b, void* x, c
       prm->smoother_order < 0 || !(prm->coarse_tol > 0.0) || prm->coarse_max < 1 ||
       (prm->smoother_kind != HDCR_SMOOTHER_CR && prm->smoother_kind != HDCR_SMOOTHER_CHEBYSHEV) ||
       (prm->coarse_solver != HDCR_COARSE_CR && prm->coarse_solver != HDCR_COARSE_DENSE &&
-       prm->coarse_solver != HDCR_COARSE_RECURSIVE)) {
+       prm->coarse_solver != HDCR_COARSE_RECURSIVE) ||
+      (prm->cycle != HDCR_CYCLE_SYMMETRIC && prm->cycle != HDCR_CYCLE_POST)) {
     set_error("hdcr_solve: bad parameters");
     return HDCR_ERR_BAD_ARG;
   }

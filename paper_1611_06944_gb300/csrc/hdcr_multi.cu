@@ -180,7 +180,7 @@ struct MultiCache {
   const void* key_Ainv = nullptr;
   const void* key_dws = nullptr;  // the dense solve's workspace the graph was captured with
   double key_lo = 0, key_hi = 0;
-  int key_order = -1;
+  int key_order = -1, key_cycle = -1;
 };
 
 template <typename R>
@@ -280,17 +280,23 @@ static int mvcycle(const hdcr_coarse* co, const FineOp<R>& H, MultiCache* c, con
   cpx<R>* e = (cpx<R>*)c->e;
   ChebWork<R>& w = *(ChebWork<R>*)c->chw;
   const int nb = num_blocks(N, 256, 8192);
-  // z1 = S r
-  HDCR_TRY(cheb_smoother<R>(H, r, z, c->cheb_c, prm->cheb_lo, prm->cheb_hi, w, st, fine));
-  // z2 = z1 + P A^{-1} P^dag (r - H z1)
-  HDCR_TRY(H.apply(z, t1, st));
-  (*fine)++;
-  msub_kernel<R><<<nb, 256, 0, st>>>(r, t1, t2, N);
-  count_launch();
-  HDCR_LAUNCH_CHECK();
-  HDCR_TRY(launch_restrict<R>(co->sub, t2, (cpx<R>*)c->c_rhs, c->nrhs, st));
-  HDCR_TRY(launch_dense_solve<R>(co, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, c->nrhs, st));
-  HDCR_TRY(launch_prolong<R>(co->sub, (const cpx<R>*)c->c_sol, z, z, c->nrhs, st));
+  if (prm->cycle == HDCR_CYCLE_POST) {
+    // z1 = P A^{-1} P^dag r;  z = z1 + S (r - H z1)
+    HDCR_TRY(launch_restrict<R>(co->sub, r, (cpx<R>*)c->c_rhs, c->nrhs, st));
+    HDCR_TRY(launch_dense_solve<R>(co, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, c->nrhs, st));
+    HDCR_TRY(launch_prolong<R>(co->sub, (const cpx<R>*)c->c_sol, (const cpx<R>*)nullptr, z, c->nrhs, st));
+  } else {
+    // z1 = S r;  z2 = z1 + P A^{-1} P^dag (r - H z1)
+    HDCR_TRY(cheb_smoother<R>(H, r, z, c->cheb_c, prm->cheb_lo, prm->cheb_hi, w, st, fine));
+    HDCR_TRY(H.apply(z, t1, st));
+    (*fine)++;
+    msub_kernel<R><<<nb, 256, 0, st>>>(r, t1, t2, N);
+    count_launch();
+    HDCR_LAUNCH_CHECK();
+    HDCR_TRY(launch_restrict<R>(co->sub, t2, (cpx<R>*)c->c_rhs, c->nrhs, st));
+    HDCR_TRY(launch_dense_solve<R>(co, (const cpx<R>*)c->c_rhs, (cpx<R>*)c->c_sol, c->nrhs, st));
+    HDCR_TRY(launch_prolong<R>(co->sub, (const cpx<R>*)c->c_sol, z, z, c->nrhs, st));
+  }
   // z = z2 + S (r - H z2)
   HDCR_TRY(H.apply(z, t1, st));
   (*fine)++;
@@ -392,7 +398,7 @@ static int solve_multi_impl(const hdcr_coarse* co, MultiCache* c, const void* U,
   // the graph bakes in U (FP64 inner), the dense inverse and the smoother: re-capture when they change
   const bool graph_ok = use_graph && c->exec && c->key_U == U && c->key_Ainv == co->Ainv && c->key_dws == co->dws &&
                         c->key_order == prm->smoother_order && c->key_lo == prm->cheb_lo &&
-                        c->key_hi == prm->cheb_hi;
+                        c->key_hi == prm->cheb_hi && c->key_cycle == prm->cycle;
   bool have_graph = graph_ok;
   int fine64 = 1, fine_in = 0, iters = 0, restarts = 0, status = HDCR_OK;
   while (!converged && iters < prm->max_outer) {
@@ -415,6 +421,7 @@ static int solve_multi_impl(const hdcr_coarse* co, MultiCache* c, const void* U,
           c->key_order = prm->smoother_order;
           c->key_lo = prm->cheb_lo;
           c->key_hi = prm->cheb_hi;
+          c->key_cycle = prm->cycle;
           have_graph = true;
         }
       }
@@ -529,9 +536,10 @@ extern "C" int hdcr_solve_multi(hdcr_coarse* co, const void* U, const void* b, v
   }
   if (!(prm->tol > 0.0) || prm->max_outer < 1 || prm->restart < 1 || prm->restart > 64 ||
       prm->smoother_kind != HDCR_SMOOTHER_CHEBYSHEV || prm->smoother_order < 1 || !(prm->cheb_lo > 0.0) ||
-      !(prm->cheb_hi > prm->cheb_lo) || prm->coarse_solver != HDCR_COARSE_DENSE) {
+      !(prm->cheb_hi > prm->cheb_lo) || prm->coarse_solver != HDCR_COARSE_DENSE ||
+      (prm->cycle != HDCR_CYCLE_SYMMETRIC && prm->cycle != HDCR_CYCLE_POST)) {
     set_error("hdcr_solve_multi: needs tol > 0, 1 <= restart <= 64, the Chebyshev smoother (order >= 1, "
-              "0 < cheb_lo < cheb_hi) and the dense coarse solve");
+              "0 < cheb_lo < cheb_hi), the dense coarse solve and a known cycle");
     return HDCR_ERR_BAD_ARG;
   }
   if (prm->inner_dtype != HDCR_C128 && prm->inner_dtype != HDCR_C64) {

@@ -92,8 +92,8 @@ def test_hdcr_solve_with_recursive_coarse_solve(hd, inner):
                             store_dtype=tdt)
     co = hd.build_coarse_op(sub, U, M5, mf, op_dtype=tdt)
     rng = synth.rng(1802)
-    n2 = rng.standard_normal((16, sub.Vc, 24)) + 1j * rng.standard_normal((16, sub.Vc, 24))
-    hd.build_level2(co, dev(n2), (2, 2, 2, 2), smooth_iters=10, cycle_smooth=8)
+    n2 = rng.standard_normal((24, sub.Vc, 24)) + 1j * rng.standard_normal((24, sub.Vc, 24))
+    hd.build_level2(co, dev(n2), (2, 2, 2, 2), smooth_iters=50, cycle_smooth=8)
     b = synth.gaussian_fermion(L, Ls, 1803)
     x, st = hd.hdcr_solve(co, U, dev(planes(b)), tol=1e-10, max_outer=100, restart=16, coarse_solver="recursive",
                           coarse_tol=1e-6, coarse_max=100, inner_dtype=tdt)
@@ -102,3 +102,5 @@ def test_hdcr_solve_with_recursive_coarse_solve(hd, inner):
     print(f"{inner}: HDCR with the recursive coarse solve: {st['iters']} outer iterations, "
           f"{st['coarse_matvecs']} coarse GCR iterations, true residual {res:.2e}")
     assert st["status"] == 0 and res <= 1.01e-10
+    # the recursive coarse solve reaches its tolerance instead of running to its cap
+    assert st["coarse_matvecs"] < 50 * st["iters"]

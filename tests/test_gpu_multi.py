@@ -70,13 +70,14 @@ def test_multi_point_sources_match_oracle(hd, inner):
         assert relerr(Xn[r], Xo[r]) <= max(1e-8, 3 * cond * 1e-10), r
 
 
-def test_multi_graph_replay_bitwise_equals_eager(hd):
+@pytest.mark.parametrize("cycle", ["symmetric", "post"])
+def test_multi_graph_replay_bitwise_equals_eager(hd, cycle):
     """The captured V-cycle replays the eager launch sequence: same iterates, same bits.
-    A second solve on the same handle reuses the captured graph."""
+    A second solve on the same handle reuses the captured graph (both cycles)."""
     L, Ls, block, nvec, mf = (4, 4, 2, 4), 8, (2, 2, 1, 2), 8, 0.05
     lat, Uh, U, sub, co = _setup(hd, L, Ls, block, nvec, mf, torch.complex64, seed=1010)
     Bd = dev(planes(synth.gaussian_fermion(L, Ls, 2010, count=5)))
-    kw = dict(tol=1e-10, inner_dtype=torch.complex64, restart=8, max_outer=2000)
+    kw = dict(tol=1e-10, inner_dtype=torch.complex64, restart=8, max_outer=2000, cycle=cycle)
     Xe, se = hd.hdcr_solve_multi(co, U, Bd, graph=False, **kw)
     Xg, sg = hd.hdcr_solve_multi(co, U, Bd, graph=True, **kw)
     Xg2, sg2 = hd.hdcr_solve_multi(co, U, Bd, graph=True, **kw)

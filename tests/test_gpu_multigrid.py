@@ -227,10 +227,12 @@ def test_hdcr_solve_tiny_workload(hd, inner, smoother, coarse, mf):
     assert st["coarse_matvecs"] > 0 and st["iters"] > 0
 
 
-def test_hdcr_vcycle_matches_oracle_first_iterate(hd):
+@pytest.mark.parametrize("cycle", ["symmetric", "post"])
+def test_hdcr_vcycle_matches_oracle_first_iterate(hd, cycle):
     """With the linear Chebyshev smoother the preconditioner is a fixed linear map (up to
     the FP32 dense coarse inverse), so the first FGCR iterate x1 = a B b, with a the
-    least-squares step, agrees with the oracle's V-cycle to the coarse inverse's accuracy."""
+    least-squares step, agrees with the oracle's V-cycle to the coarse inverse's accuracy
+    (both cycles: smoother before and after the coarse correction, or after only)."""
     L, Ls, block, nvec, mf = (4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.05
     g, U, noise, sub = _oracle_sub(L, Ls, block, nvec, 0.3, mf, 3600, iters=6)
     lat = hd.Lattice(L, Ls)
@@ -245,11 +247,12 @@ def test_hdcr_vcycle_matches_oracle_first_iterate(hd):
     p = mg.HDCRParams(M5=M5, mf=mf)
     S = lambda v: mg.chebyshev_smoother(U, v, p)
     Qc = lambda c: np.linalg.solve(Ad, c.ravel()).reshape(c.shape)
-    z = mg.vcycle(U, sub, A, b, p, S=S, Qc=Qc)
+    z = mg.vcycle(U, sub, A, b, p, S=S, Qc=Qc, cycle=cycle)
     w = dwf.apply_H(U, z, M5, mf)
     x1 = (np.vdot(w, b) / np.vdot(w, w)) * z
     # the GPU solve with max_outer = 1 leaves its first iterate in x via hdcr_solve_into
-    st = hd.hdcr_solve_into(co, dev(links(U)), dev(planes(b)), xd, tol=1e-14, max_outer=1, restart=1)
+    st = hd.hdcr_solve_into(co, dev(links(U)), dev(planes(b)), xd, tol=1e-14, max_outer=1, restart=1,
+                            cycle=cycle)
     assert st["status"] == -3
     assert relerr(natural(host(xd), L, Ls), x1) < 1e-4
 

@@ -106,5 +106,5 @@ def test_cr_needs_no_more_matvecs_than_cgne():
         _, info = cr(H, b, fixed_iters=2 * n_steps)
         r_cr = info.resid_history[-1]
         assert r_cr <= cgne[n_steps - 1] * (1 + 1e-8), (n_steps, r_cr, cgne[n_steps - 1])
-        # "about as many": here CR is better by under 1%, the paper's approximate equality
+        # CR needs roughly as many matvecs as CGNE: here it is better by under 1%
         assert r_cr >= 0.95 * cgne[n_steps - 1], (n_steps, r_cr, cgne[n_steps - 1])

@@ -200,6 +200,31 @@ def test_vcycle_equals_composite_M_outer():
     assert relerr(z.ravel(), Mo @ r.ravel()) < 1e-12
 
 
+def test_post_only_cycle_error_propagator():
+    """The post-smoothing cycle (coarse correction, then the smoother) has the error
+    propagator (1 - B H) = (1 - S H)(1 - Q H), the product of the two corrections in
+    that order; the symmetric cycle's is (1 - S H)(1 - Q H)(1 - S H).  Checked on
+    random errors v: v - B H v against the products applied to v."""
+    g, U, sub, A, Hd, P, Q, _ = _tiny_two_level()
+    N = Hd.shape[0]
+    Sm = 0.05 * Hd + 0.01 * np.eye(N)
+    S = lambda v: (Sm @ v.ravel()).reshape(v.shape)
+    Ad = mg.coarse_dense(A, g)
+    Qc = lambda c: np.linalg.solve(Ad, c.ravel()).reshape(c.shape)
+    p = mg.HDCRParams(M5=M5, mf=MF)
+    E_s, E_q = np.eye(N) - Sm @ Hd, np.eye(N) - Q @ Hd
+    rng = synth.rng(131)
+    for _ in range(3):
+        v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        Hv = (Hd @ v).reshape(g.fine_shape())
+        post = v - mg.vcycle(U, sub, A, Hv, p, S=S, Qc=Qc, cycle="post").ravel()
+        sym = v - mg.vcycle(U, sub, A, Hv, p, S=S, Qc=Qc, cycle="symmetric").ravel()
+        assert relerr(post, E_s @ (E_q @ v)) < 1e-11
+        assert relerr(sym, E_s @ (E_q @ (E_s @ v))) < 1e-11
+    with pytest.raises(ValueError):
+        mg.vcycle(U, sub, A, Hv, p, S=S, Qc=Qc, cycle="pre")
+
+
 def test_chiral_split_keeps_low_spectrum():
     """Section 4: the gamma5-compatible split eliminates near-zero coarse eigenvalues.
     Built from exact low eigenvectors of H, the coarse operator's smallest |eigenvalue|
