@@ -220,7 +220,7 @@ def hdcr_step(hd, lat, U, b, noise, inner="f64"):
     tdt = torch.complex128 if inner == "f64" else torch.complex64
     sub = hd.build_subspace(lat, U, noise, M5, MF, BLOCK, filter_dtype=torch.complex64, store_dtype=tdt,
                             **FILTER)
-    co = hd.build_coarse_op(sub, U, M5, MF, op_dtype=tdt)
+    co = hd.build_coarse_op(sub, U, M5, MF, op_dtype=tdt, fp32_build=tdt == torch.complex128)
     hd.coarse_invert(co)
     x, st = hd.hdcr_solve(co, U, b, inner_dtype=tdt, **SOLVE)
     F = hd.gauge_force(lat, x, hd.apply_gamma5_r5(lat, x))
@@ -244,7 +244,7 @@ def step_breakdown(hd, lat, U, b, noise) -> dict:
     sub = hd.build_subspace(lat, U, noise, M5, MF, BLOCK, filter_dtype=torch.complex64,
                             store_dtype=torch.complex128, **FILTER)
     t = tick("subspace_s", t)
-    co = hd.build_coarse_op(sub, U, M5, MF, op_dtype=torch.complex128)
+    co = hd.build_coarse_op(sub, U, M5, MF, op_dtype=torch.complex128, fp32_build=True)
     t = tick("coarse_op_s", t)
     hd.coarse_invert(co)
     t = tick("coarse_invert_s", t)
@@ -376,8 +376,9 @@ def run_ours(args, world, rank, local):
             "workload": "two-level FP64: 16^4 x 16 DWF, eps=0.5, M5=1.8, mf=0.01, 1 Gaussian source, "
                         "nvec=24, 4^4 blocks (4^4 coarse)",
             "plaquette": round(plaq, 4),
-            "step": "Chebyshev-filter subspace (order 300, FP32 filter, FP64 Gram-Schmidt) + FP64 coarse op "
-                    "+ dense coarse inverse + FP64 HDCR solve to 1e-10 + gauge force",
+            "step": "Chebyshev-filter subspace (order 300, FP32 filter, FP64 Gram-Schmidt) + coarse op "
+                    "(FP32-exact tensor-core build, stored FP64) + FP32 dense coarse inverse + FP64 HDCR solve "
+                    "(FP64 smoother and outer GCR) to 1e-10 + gauge force",
             "l2": "inputs larger than L2 (201 MB per FP64 field)",
             "parallelism": f"replicas x{world}",
         },
@@ -428,7 +429,7 @@ def run_e2e(hd, lat, Uh, bh, nh, stream) -> dict:
     e0.record(stream)
     sub = hd.build_subspace(lat, Up, npin, M5, MF, BLOCK, filter_dtype=torch.complex64,
                             store_dtype=torch.complex128, **FILTER)
-    co = hd.build_coarse_op(sub, Up, M5, MF, op_dtype=torch.complex128)
+    co = hd.build_coarse_op(sub, Up, M5, MF, op_dtype=torch.complex128, fp32_build=True)
     hd.coarse_invert(co)
     st = hd.hdcr_solve_into(co, Up, bp, xh, inner_dtype=torch.complex128, **SOLVE)
     hd.apply_gamma5_r5(lat, xh, wh)

@@ -70,6 +70,11 @@ extern "C" {
 /* hdcr_build_coarse_op only: complex float storage, projections with one pass of
  * TF32 tensor-core products (FP32 accumulation), relative error about 1e-3 */
 #define HDCR_C64_FAST 2
+/* hdcr_build_coarse_op only: complex double storage, built as C64 with the
+ * three-pass (FP32-exact) tensor-core products from the FP32-rounded basis and
+ * links, relative error about 1e-7.  For solves whose coarse correction is the
+ * FP32 dense inverse, which rounds A to FP32 anyway. */
+#define HDCR_C128_TC 4
 /* FP16 storage of a fermion field (the precision form's half-precision
  * storage; arithmetic stays FP32): 12*V5 half2 (FP16 re, im) in the field
  * layout below, followed by V5 FP32 scales, one per 5d site (x4, s) at index
@@ -330,7 +335,8 @@ int hdcr_prolong(const hdcr_subspace* sub, const void* coarse, void* fine, int d
  * (Eq. 4.5), nonzero only for b = a and the 8 nearest coarse neighbours (the
  * sparsity noted after Eq. 4.6), stored as A[a][leg][j][k] in ``op_dtype``
  * (HDCR_C64_FAST: stored as C64, built with single-pass TF32 products, for the
- * mixed-precision solve whose FP64 outer iteration recovers the accuracy).  Leg
+ * mixed-precision solve whose FP64 outer iteration recovers the accuracy;
+ * HDCR_C128_TC: stored as C128, built by the FP32-exact tensor-core path).  Leg
  * (mu, +-) collects the fine hops from block a into block a +- mu; on a coarse
  * extent of 2 the two legs of mu reach the same coarse site and both apply.  U
  * is C128 (converted internally when op_dtype is C64).  The subspace handle is

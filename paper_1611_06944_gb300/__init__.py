@@ -563,18 +563,26 @@ class CoarseOperator:
 
 
 def build_coarse_op(sub: Subspace, U: torch.Tensor, M5: float, mf: float,
-                    op_dtype: torch.dtype = torch.complex128, fast: bool = False,
+                    op_dtype: torch.dtype = torch.complex128, fast: bool = False, fp32_build: bool = False,
                     stream=None) -> CoarseOperator:
     """A^{ab}_{jk} = <phi_j^a|H|phi_k^b> for the 9 legs of every coarse site (Eq. 4.5).
     fast=True (complex64 only) builds with one pass of TF32 tensor-core products
-    (relative error ~1e-3) instead of the three that keep FP32 accuracy."""
+    (relative error ~1e-3) instead of the three that keep FP32 accuracy.
+    fp32_build=True (complex128 only) builds with the FP32-exact tensor-core path
+    from the FP32-rounded basis and stores complex128 (relative error ~1e-7): for a
+    solve whose coarse correction is the FP32 dense inverse."""
     if U.dtype != torch.complex128:
         raise TypeError("build_coarse_op takes complex128 links")
     if fast and op_dtype != torch.complex64:
         raise ValueError("fast=True builds a complex64 operator")
+    if fp32_build and op_dtype != torch.complex128:
+        raise ValueError("fp32_build=True builds a complex128 operator")
     h = ctypes.c_void_p()
     p = _params(M5, mf)
-    code = _lib.HDCR_C128 if op_dtype == torch.complex128 else (_lib.HDCR_C64_FAST if fast else _lib.HDCR_C64)
+    if op_dtype == torch.complex128:
+        code = _lib.HDCR_C128_TC if fp32_build else _lib.HDCR_C128
+    else:
+        code = _lib.HDCR_C64_FAST if fast else _lib.HDCR_C64
     _check(_L.hdcr_build_coarse_op(sub.handle, C_ref(p), _dev(U, "U", True), code, _stream(stream),
                                    ctypes.byref(h)), "build_coarse_op")
     return CoarseOperator(h, sub, op_dtype, M5, mf)

@@ -17,6 +17,7 @@ HDCR_OK = 0
 HDCR_C128 = 0
 HDCR_C64 = 1
 HDCR_C64_FAST = 2
+HDCR_C128_TC = 4
 HDCR_H16 = 3
 
 STATUS_NAMES = {

@@ -634,13 +634,15 @@ static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params
     set_error("hdcr_build_coarse_op: null pointer");
     return HDCR_ERR_BAD_ARG;
   }
-  if (op_dtype != HDCR_C128 && op_dtype != HDCR_C64 && op_dtype != HDCR_C64_FAST) {
+  if (op_dtype != HDCR_C128 && op_dtype != HDCR_C64 && op_dtype != HDCR_C64_FAST && op_dtype != HDCR_C128_TC) {
     set_error("hdcr_build_coarse_op: unknown dtype %d", op_dtype);
     return HDCR_ERR_BAD_ARG;
   }
-  // HDCR_C64_FAST: stored as C64, tensor-core products in one TF32 pass
+  // HDCR_C64_FAST: stored as C64, tensor-core products in one TF32 pass;
+  // HDCR_C128_TC: built as C64 with the three-pass (FP32-exact) products, stored as C128
   const int npass = op_dtype == HDCR_C64_FAST ? 1 : 3;
-  if (op_dtype == HDCR_C64_FAST) op_dtype = HDCR_C64;
+  const bool store_c128 = op_dtype == HDCR_C128_TC;
+  if (op_dtype == HDCR_C64_FAST || op_dtype == HDCR_C128_TC) op_dtype = HDCR_C64;
   if (sub->nvec > 64) {
     set_error("hdcr_build_coarse_op: nvec = %d above the supported 64", sub->nvec);
     return HDCR_ERR_BAD_ARG;
@@ -661,7 +663,8 @@ static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params
   // partial projections of the split tensor-core contractions (FP32 builds)
   // (two sets: the face legs run on their own stream)
   const size_t part_bytes = op_dtype == HDCR_C64 ? 2 * sizeof(cpx<float>) * TC_MAX_SPLIT * (size_t)bg.Vc * nvec * nvec : 0;
-  size_t bytes = cb * (size_t)fs * nvec + face_bytes + 256 + part_bytes;
+  const size_t a_bytes = cb * (size_t)bg.Vc * NLEGS * nvec * nvec;
+  size_t bytes = cb * (size_t)fs * nvec + face_bytes + 256 + part_bytes + (store_c128 ? a_bytes : 0);
   if (conv_phi) bytes += cb * (size_t)fs * nvec;
   if (conv_u) bytes += cb * (size_t)g.V4 * 36;
   std::lock_guard<std::mutex> lock(sub->build_mu);
@@ -681,6 +684,11 @@ static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params
   wp += 256;
   void* part = wp;
   wp += part_bytes;
+  void* A_build = nullptr;  // the FP32 operator before its conversion (HDCR_C128_TC)
+  if (store_c128) {
+    A_build = wp;
+    wp += a_bytes;
+  }
   cudaMemsetAsync(err, 0, sizeof(int), st);
   const void* phi = sub->vecs;
   if (conv_phi) {
@@ -698,12 +706,13 @@ static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params
   co->g = g;
   co->bg = bg;
   co->nvec = nvec;
-  co->dtype = op_dtype;
+  co->dtype = store_c128 ? HDCR_C128 : op_dtype;
   co->M5 = p->M5;
   co->mf = p->mf;
   cudaGetDevice(&co->device);
   int s = HDCR_OK;
-  cudaError_t e = cudaMalloc(&co->A, cb * (size_t)bg.Vc * NLEGS * nvec * nvec);
+  cudaError_t e = cudaMalloc(&co->A, dtype_complex_bytes(co->dtype) * (size_t)bg.Vc * NLEGS * nvec * nvec);
+  if (!store_c128) A_build = co->A;
   if (e == cudaSuccess) e = cudaMalloc(&co->nbr, sizeof(int) * bg.Vc * NLEGS);
   if (e != cudaSuccess) s = cuda_status(e, "coarse operator storage");
   if (s == HDCR_OK) {
@@ -730,8 +739,10 @@ static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params
                            (cpx<double>*)face_work, (cpx<double>*)co->A, co->nbr, nullptr, nullptr, err, 3, st);
     else
       s = build_op<float>(sub, p->M5, p->mf, (const cpx<float>*)Ub, (const cpx<float>*)phi, (cpx<float>*)Y,
-                          (cpx<float>*)face_work, (cpx<float>*)co->A, co->nbr, (cpx<float>*)part,
+                          (cpx<float>*)face_work, (cpx<float>*)A_build, co->nbr, (cpx<float>*)part,
                           (cpx<float>*)part + TC_MAX_SPLIT * (size_t)bg.Vc * nvec * nvec, err, npass, st);
+    if (s == HDCR_OK && store_c128)
+      s = launch_convert(A_build, HDCR_C64, co->A, HDCR_C128, (long long)bg.Vc * NLEGS * nvec * nvec, st);
   }
   if (s == HDCR_OK) {
     int herr = 0;

@@ -2,8 +2,11 @@
 //   noise -> a fixed number of CR steps on H x = 0 ("inverse iteration applied
 //   to Gaussian noise") -> normalise -> chiral split with Gamma5 = gamma5 R5
 //   -> restriction to blocks (Eq. 4.1) -> block orthonormalisation, so that
-//   P_S = sum |phi_k^b><phi_k^b| (Eq. 4.3) is a projector.
+//   P_S = sum |phi_k^b><phi_k^b| (Eq. 4.3) is a projector (Cholesky QR twice,
+//   Gram-Schmidt for ill-conditioned blocks).
 // All of it runs in FP64; the basis is then stored in the requested dtype.
+#include <vector>
+
 #include "host_io.cuh"
 #include "chebyshev.cuh"
 #include "coarse.cuh"
@@ -97,12 +100,14 @@ __device__ __forceinline__ void block_dot(const Geom& g, const BlockGeom& bg, in
   __syncthreads();
 }
 
-// Modified Gram-Schmidt, applied twice, inside each block (one CTA per block),
-// in the fixed order k = 0..nvec-1.  Rank deficiency sets *status.
+// Modified Gram-Schmidt, applied twice, inside each block (one CTA per block, the
+// blocks of ``list`` or all of them), in the fixed order k = 0..nvec-1.  Rank
+// deficiency sets *status.  Used for the blocks the Cholesky QR below leaves.
 __global__ void __launch_bounds__(GS_THREADS) block_gs_kernel(Geom g, BlockGeom bg, cpx<double>* vecs,
-                                                              int nvec, double rank_tol, int* status) {
+                                                              int nvec, double rank_tol, int* status,
+                                                              const int* list) {
   __shared__ double bcast[2];
-  const int a = blockIdx.x;
+  const int a = list ? list[blockIdx.x] : blockIdx.x;
   const long long fs = g.V5 * 12;
   for (int k = 0; k < nvec; ++k) {
     cpx<double>* vk = vecs + (long long)k * fs;
@@ -147,6 +152,266 @@ __global__ void __launch_bounds__(GS_THREADS) block_gs_kernel(Geom g, BlockGeom 
   }
 }
 
+// ------------------------------------------------------------------ Cholesky QR
+// The same orthonormalisation by two rounds of Cholesky QR per block: the Gram
+// matrix G = V^dag V of the block's nvec vectors, G = R^dag R (R upper triangular,
+// positive real diagonal), V <- V R^{-1}.  The QR factor with a positive real
+// diagonal is unique, so in exact arithmetic this is the Gram-Schmidt result; the
+// second round removes what the first left of the rounding (about cond(V)^2 eps).
+// It reads each vector twice per round instead of twice per pair of vectors, so
+// it runs at the FP64 rate instead of the memory rate.  A block whose pivot
+// falls below CQR_TOL of its diagonal entry (condition number above ~1e4) is
+// left to the Gram-Schmidt kernel, which also decides rank deficiency.
+constexpr int CQR_E = 96;         // elements (site x component) of a block per chunk
+constexpr int CQR_MAXV = 64;      // largest nvec handled (else Gram-Schmidt throughout)
+constexpr int CQR_TILES = 3;      // 2 x 2 Gram tiles per thread: (nvec/2)(nvec/2+1)/2 <= 3 * 256
+constexpr double CQR_TOL = 1e-8;
+
+// offset of element le of block a: elements ordered by the block's 4d sites, then
+// component and s, so one 4d site's 12 Ls elements are contiguous in the field
+__device__ __forceinline__ unsigned cqr_off(const Geom& g, const BlockGeom& bg, int a, long long le) {
+  const int per = 12 * g.Ls;
+  const long long r = le / per;
+  const int rem = (int)(le - r * per);
+  const long long i5 = block_site(g, bg, a, r * g.Ls);  // s = 0 of the block's 4d site r
+  return (unsigned)((i5 / g.Ls) * per + rem);
+}
+
+__device__ __forceinline__ void cqr_tile(int t, int nt, int* j, int* k) {
+  int row = 0;  // tiles (tj, tk), tj <= tk, row by row
+  while (t >= nt - row) {
+    t -= nt - row;
+    ++row;
+  }
+  *j = 2 * row;
+  *k = 2 * (row + t);
+}
+
+// part[a][q] = sum over share q of block a of conj(v_j) v_k (upper 2x2 tiles)
+__global__ void __launch_bounds__(GS_THREADS) cqr_gram_kernel(Geom g, BlockGeom bg, const cpx<double>* __restrict__ vecs,
+                                                              int nvec, int S, const int* __restrict__ skip,
+                                                              cpx<double>* __restrict__ part) {
+  extern __shared__ cpx<double> xs[];  // [nvec][CQR_E]
+  const int a = blockIdx.x, q = blockIdx.y;
+  if (skip[a]) return;
+  const long long fs = g.V5 * 12;
+  const long long ne = bg.K5 * 12;
+  const long long e0 = ne * q / S, e1 = ne * (q + 1) / S;
+  const int nt = nvec / 2, ntiles = nt * (nt + 1) / 2;
+  double acc[CQR_TILES][8];
+  int tj[CQR_TILES], tk[CQR_TILES];
+#pragma unroll
+  for (int i = 0; i < CQR_TILES; ++i) {
+    const int t = threadIdx.x + i * GS_THREADS;
+    tj[i] = tk[i] = -1;
+    if (t < ntiles) cqr_tile(t, nt, &tj[i], &tk[i]);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[i][m] = 0.0;
+  }
+  for (long long c0 = e0; c0 < e1; c0 += CQR_E) {
+    const int n = (int)(e1 - c0 < CQR_E ? e1 - c0 : CQR_E);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvec * CQR_E; i += GS_THREADS) {
+      const int k = i / CQR_E, e = i - k * CQR_E;
+      xs[i] = e < n ? vecs[(long long)k * fs + cqr_off(g, bg, a, c0 + e)] : cpx<double>(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < CQR_TILES; ++i) {
+      if (tj[i] < 0) continue;
+      const cpx<double>* x0 = xs + tj[i] * CQR_E;
+      const cpx<double>* x1 = x0 + CQR_E;
+      const cpx<double>* y0 = xs + tk[i] * CQR_E;
+      const cpx<double>* y1 = y0 + CQR_E;
+      double* A = acc[i];
+      for (int e = 0; e < n; ++e) {
+        const cpx<double> u0 = x0[e], u1 = x1[e], w0 = y0[e], w1 = y1[e];
+        A[0] = fma(u0.re, w0.re, fma(u0.im, w0.im, A[0]));
+        A[1] = fma(u0.re, w0.im, fma(-u0.im, w0.re, A[1]));
+        A[2] = fma(u0.re, w1.re, fma(u0.im, w1.im, A[2]));
+        A[3] = fma(u0.re, w1.im, fma(-u0.im, w1.re, A[3]));
+        A[4] = fma(u1.re, w0.re, fma(u1.im, w0.im, A[4]));
+        A[5] = fma(u1.re, w0.im, fma(-u1.im, w0.re, A[5]));
+        A[6] = fma(u1.re, w1.re, fma(u1.im, w1.im, A[6]));
+        A[7] = fma(u1.re, w1.im, fma(-u1.im, w1.re, A[7]));
+      }
+    }
+  }
+  cpx<double>* P = part + ((long long)a * S + q) * nvec * nvec;
+#pragma unroll
+  for (int i = 0; i < CQR_TILES; ++i) {
+    if (tj[i] < 0) continue;
+    P[tj[i] * nvec + tk[i]] = cpx<double>(acc[i][0], acc[i][1]);
+    P[tj[i] * nvec + tk[i] + 1] = cpx<double>(acc[i][2], acc[i][3]);
+    P[(tj[i] + 1) * nvec + tk[i]] = cpx<double>(acc[i][4], acc[i][5]);
+    P[(tj[i] + 1) * nvec + tk[i] + 1] = cpx<double>(acc[i][6], acc[i][7]);
+  }
+}
+
+// G = sum_q part[a][q] (fixed order), G = R^dag R, rinv[a] = R^{-1}; one warp per
+// block.  A pivot below CQR_TOL of its diagonal sets skip[a] (the block goes to
+// Gram-Schmidt).
+__global__ void __launch_bounds__(32) cqr_chol_kernel(int nvec, int S, const cpx<double>* __restrict__ part,
+                                                      cpx<double>* __restrict__ rinv, int* __restrict__ skip) {
+  extern __shared__ cpx<double> G[];  // [nvec][nvec]: G, then R in the upper triangle; diag G in d0
+  double* d0 = reinterpret_cast<double*>(G + nvec * nvec);
+  const int a = blockIdx.x, lane = threadIdx.x;
+  if (skip[a]) return;
+  const cpx<double>* P = part + (long long)a * S * nvec * nvec;
+  for (int i = lane; i < nvec * nvec; i += 32) {
+    const int j = i / nvec, k = i - j * nvec;
+    if (j > k) continue;
+    cpx<double> v(0.0, 0.0);
+    for (int q = 0; q < S; ++q) {
+      const cpx<double> w = P[(long long)q * nvec * nvec + i];
+      v.re += w.re;
+      v.im += w.im;
+    }
+    G[i] = v;
+    if (j == k) d0[j] = v.re;
+  }
+  __syncwarp();
+  bool ok = true;
+  for (int k = 0; k < nvec && ok; ++k) {
+    // pivot: G_kk - sum_{i<k} |R_ik|^2
+    double dk = G[k * nvec + k].re;
+    for (int i = 0; i < k; ++i) dk -= G[i * nvec + k].re * G[i * nvec + k].re + G[i * nvec + k].im * G[i * nvec + k].im;
+    ok = dk > CQR_TOL * d0[k] && d0[k] > 0.0;
+    if (!ok) break;
+    const double rkk = sqrt(dk);
+    __syncwarp();
+    // row k of R: R_kj = (G_kj - sum_{i<k} conj(R_ik) R_ij) / R_kk, j > k
+    for (int j = k + 1 + lane; j < nvec; j += 32) {
+      double re = G[k * nvec + j].re, im = G[k * nvec + j].im;
+      for (int i = 0; i < k; ++i) {
+        const cpx<double> r1 = G[i * nvec + k], r2 = G[i * nvec + j];
+        re -= r1.re * r2.re + r1.im * r2.im;
+        im -= r1.re * r2.im - r1.im * r2.re;
+      }
+      G[k * nvec + j] = cpx<double>(re / rkk, im / rkk);
+    }
+    __syncwarp();
+    if (lane == 0) G[k * nvec + k] = cpx<double>(rkk, 0.0);
+    __syncwarp();
+  }
+  if (!ok) {
+    if (lane == 0) skip[a] = 1;
+    return;
+  }
+  // R^{-1} column by column (lane j): X_jj = 1/R_jj, X_ij = -(sum_{m=i+1..j} R_im X_mj) / R_ii
+  cpx<double>* X = rinv + (long long)a * nvec * nvec;
+  for (int j = lane; j < nvec; j += 32) {
+    for (int i = j + 1; i < nvec; ++i) X[i * nvec + j] = cpx<double>(0.0, 0.0);
+    X[j * nvec + j] = cpx<double>(1.0 / G[j * nvec + j].re, 0.0);
+    for (int i = j - 1; i >= 0; --i) {
+      double re = 0.0, im = 0.0;
+      for (int m = i + 1; m <= j; ++m) {
+        const cpx<double> r = G[i * nvec + m], x = X[m * nvec + j];
+        re += r.re * x.re - r.im * x.im;
+        im += r.re * x.im + r.im * x.re;
+      }
+      const double inv = -1.0 / G[i * nvec + i].re;
+      X[i * nvec + j] = cpx<double>(re * inv, im * inv);
+    }
+  }
+}
+
+// v_k <- sum_{j<=k} v_j rinv_jk for the elements of share q of block a
+__global__ void __launch_bounds__(GS_THREADS) cqr_apply_kernel(Geom g, BlockGeom bg, cpx<double>* __restrict__ vecs,
+                                                               int nvec, int S, const int* __restrict__ skip,
+                                                               const cpx<double>* __restrict__ rinv) {
+  extern __shared__ cpx<double> sh[];  // rinv [nvec][nvec], then xs [nvec][CQR_E]
+  const int a = blockIdx.x, q = blockIdx.y;
+  if (skip[a]) return;
+  cpx<double>* Ri = sh;
+  cpx<double>* xs = sh + nvec * nvec;
+  const cpx<double>* X = rinv + (long long)a * nvec * nvec;
+  for (int i = threadIdx.x; i < nvec * nvec; i += GS_THREADS) Ri[i] = X[i];
+  const long long fs = g.V5 * 12;
+  const long long ne = bg.K5 * 12;
+  const long long e0 = ne * q / S, e1 = ne * (q + 1) / S;
+  for (long long c0 = e0; c0 < e1; c0 += CQR_E) {
+    const int n = (int)(e1 - c0 < CQR_E ? e1 - c0 : CQR_E);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvec * CQR_E; i += GS_THREADS) {
+      const int k = i / CQR_E, e = i - k * CQR_E;
+      if (e < n) xs[i] = vecs[(long long)k * fs + cqr_off(g, bg, a, c0 + e)];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvec * CQR_E; i += GS_THREADS) {
+      const int k = i / CQR_E, e = i - k * CQR_E;
+      if (e >= n) continue;
+      double re = 0.0, im = 0.0;
+      for (int j = 0; j <= k; ++j) {
+        const cpx<double> v = xs[j * CQR_E + e], r = Ri[j * nvec + k];
+        re = fma(v.re, r.re, fma(-v.im, r.im, re));
+        im = fma(v.re, r.im, fma(v.im, r.re, im));
+      }
+      vecs[(long long)k * fs + cqr_off(g, bg, a, c0 + e)] = cpx<double>(re, im);
+    }
+  }
+}
+
+// Two rounds of Cholesky QR over every block that allows it; *flagged receives the
+// blocks left for Gram-Schmidt (device list, count on the host).
+static int cholesky_qr2(const Geom& g, const BlockGeom& bg, cpx<double>* vecs, int nvec, cudaStream_t st,
+                        int** list_out, int* nlist) {
+  *list_out = nullptr;
+  *nlist = 0;
+  const int Vc = bg.Vc;
+  int dev = 0, sms = 0;
+  HDCR_CUDA_TRY(cudaGetDevice(&dev));
+  HDCR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int S = (4 * sms + Vc - 1) / Vc;  // shares of a block, so that the grid covers the SMs about four times
+  if (S < 1) S = 1;
+  if (S > 8) S = 8;
+  const size_t nn = (size_t)nvec * nvec;
+  cpx<double>* part = nullptr;
+  cpx<double>* rinv = nullptr;
+  int* skip = nullptr;
+  cudaError_t e = cudaMallocAsync(&part, sizeof(cpx<double>) * nn * Vc * S, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&rinv, sizeof(cpx<double>) * nn * Vc, st);
+  // skip flags [0, Vc), then the list of flagged blocks handed to the caller
+  if (e == cudaSuccess) e = cudaMallocAsync(&skip, sizeof(int) * (2 * (size_t)Vc + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(skip, 0, sizeof(int) * (2 * (size_t)Vc + 1), st);
+  const size_t smem_gram = sizeof(cpx<double>) * (size_t)nvec * CQR_E;
+  const size_t smem_chol = sizeof(cpx<double>) * nn + sizeof(double) * nvec;
+  const size_t smem_apply = sizeof(cpx<double>) * (nn + (size_t)nvec * CQR_E);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(cqr_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gram);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(cqr_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_chol);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(cqr_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_apply);
+  for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
+    cqr_gram_kernel<<<dim3(Vc, S), GS_THREADS, smem_gram, st>>>(g, bg, vecs, nvec, S, skip, part);
+    cqr_chol_kernel<<<Vc, 32, smem_chol, st>>>(nvec, S, part, rinv, skip);
+    cqr_apply_kernel<<<dim3(Vc, S), GS_THREADS, smem_apply, st>>>(g, bg, vecs, nvec, S, skip, rinv);
+    count_launches(3);
+    e = cudaGetLastError();
+  }
+  std::vector<int> hs(Vc);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), skip, sizeof(int) * Vc, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    std::vector<int> list;
+    for (int a = 0; a < Vc; ++a)
+      if (hs[a]) list.push_back(a);
+    if (!list.empty()) {
+      int* dl = skip + Vc;  // the second half of the flag buffer holds the list
+      e = cudaMemcpyAsync(dl, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      *list_out = dl;
+      *nlist = (int)list.size();
+    }
+  }
+  cudaFreeAsync(part, st);
+  cudaFreeAsync(rinv, st);
+  if (e != cudaSuccess || *nlist == 0) cudaFreeAsync(skip, st);
+  if (e != cudaSuccess) {
+    *list_out = nullptr;
+    return cuda_status(e, "block Cholesky QR");
+  }
+  return HDCR_OK;
+}
+
 // ---------------------------------------------------------------- host side
 // Takes ownership of ``vecs`` (freed on every failure, kept or converted on success).
 static int orthonormalise_and_store(const Geom& g, const BlockGeom& bg, cpx<double>* vecs, int nvec,
@@ -158,8 +423,24 @@ static int orthonormalise_and_store(const Geom& g, const BlockGeom& bg, cpx<doub
     return cuda_status(e0, "subspace status flag");
   }
   cudaMemsetAsync(dstatus, 0, sizeof(int), st);
-  block_gs_kernel<<<bg.Vc, GS_THREADS, 0, st>>>(g, bg, vecs, nvec, 1e-12, dstatus); count_launch();
+  // Cholesky QR where the blocks allow it, Gram-Schmidt for the rest (all of them
+  // when nvec is above the Cholesky kernels' limit)
+  int* list = nullptr;
+  int nlist = bg.Vc;
+  if (nvec <= CQR_MAXV) {
+    const int s = cholesky_qr2(g, bg, vecs, nvec, st, &list, &nlist);
+    if (s != HDCR_OK) {
+      cudaFree(dstatus);
+      cudaFree(vecs);
+      return s;
+    }
+  }
+  if (nlist > 0) {
+    block_gs_kernel<<<nlist, GS_THREADS, 0, st>>>(g, bg, vecs, nvec, 1e-12, dstatus, list);
+    count_launch();
+  }
   cudaError_t e = cudaGetLastError();
+  if (list) cudaFreeAsync(list - bg.Vc, st);  // the list sits behind the skip flags of cholesky_qr2
   int hstatus = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, dstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

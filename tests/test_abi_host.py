@@ -46,6 +46,21 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(_lib.SIGNATURES) == set(names)
 
 
+def test_binding_constants_match_the_header():
+    """Every #define HDCR_* integer of include/hdcr.h that the binding mirrors has the
+    same value there (dtype codes, smoother / coarse-solver / cycle kinds)."""
+    from paper_1611_06944_gb300 import _lib
+    defs = dict(re.findall(r"#define\s+(HDCR_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", open(HEADER).read()))
+    mirrored = [n for n in defs if hasattr(_lib, n)]
+    assert len(mirrored) >= 12
+    for n in mirrored:
+        assert getattr(_lib, n) == int(defs[n]), n
+    for n in ("HDCR_C128_TC", "HDCR_CYCLE_POST", "HDCR_COARSE_RECURSIVE"):
+        assert n in mirrored
+    dtypes = [int(defs[n]) for n in ("HDCR_C128", "HDCR_C64", "HDCR_C64_FAST", "HDCR_H16", "HDCR_C128_TC")]
+    assert len(set(dtypes)) == len(dtypes)
+
+
 def test_status_strings(lib):
     assert lib.hdcr_strerror(0) == b"ok"
     assert lib.hdcr_strerror(-2) == b"bad geometry"

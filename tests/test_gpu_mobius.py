@@ -67,6 +67,29 @@ def test_mobius_solves_match_oracle(hd):
     check(x, "cgne_rb")
 
 
+def test_mobius_hdcr_solve_with_scaled_windows(hd):
+    """HDCR on the Moebius operator (b5 = 2 through the Shamir form): b5 stretches the
+    spectrum of H, so the filter's upper edge (8 b5) and the smoother's window
+    ([b5^2, 64 b5^2] on H^2) are scaled with it; the solve then reaches a true
+    residual of 1e-10 of the oracle's Moebius operator (8^4 x 8, 4^4 blocks, nvec 24,
+    about 27 outer iterations)."""
+    L, Ls, mf, b5 = (8, 8, 8, 8), 8, 0.01, 2.0
+    lat = hd.Lattice(L, Ls)
+    Uh = synth.gauge_field(L, 0.5, 1900)
+    noise = dev(planes(synth.gaussian_fermion(L, Ls, 1901, count=12)))
+    b = synth.gaussian_fermion(L, Ls, 1903)
+    Ub, M5s, mfs = hd.mobius_to_shamir(dev(links(Uh)), M5, mf, b5)
+    sub = hd.build_subspace(lat, Ub, noise, M5s, mfs, (4, 4, 4, 4), kind="chebyshev", order=200,
+                            lam_cut=0.5 * b5, lam_max=8.0 * b5)
+    co = hd.build_coarse_op(sub, Ub, M5s, mfs)
+    x, st = hd.hdcr_solve(co, Ub, dev(planes(b)), tol=1e-10, max_outer=100, restart=8,
+                          cheb_lo=b5 * b5, cheb_hi=64.0 * b5 * b5)
+    xg = natural(host(x), L, Ls)
+    res = np.sqrt(dwf.norm2(b - dwf.apply_H_mobius(Uh, xg, M5, mf, b5)) / dwf.norm2(b))
+    assert st["status"] == 0 and res <= 1.01e-10
+    assert st["iters"] < 60
+
+
 def test_mobius_rejects_bad_scale(hd):
     U = dev(links(synth.gauge_field((2, 2, 2, 2), 0.5, 9500)))
     with pytest.raises(hd.HDCRError) as e:

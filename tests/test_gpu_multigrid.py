@@ -152,6 +152,36 @@ def test_subspace_errors(hd):
     assert e.value.status == -5
 
 
+@pytest.mark.parametrize("nvec", [24, 66])
+def test_block_orthonormalisation_matches_oracle(hd, nvec):
+    """subspace_from_vectors: the GPU's block orthonormalisation (two rounds of
+    Cholesky QR per block; modified Gram-Schmidt for blocks whose Cholesky pivot
+    collapses and for nvec > 64) against the oracle's modified Gram-Schmidt applied
+    twice.  Random vectors, except that in block 0 vector 1 is vector 0 plus 1e-6
+    noise (condition ~1e6: Gram-Schmidt) and in block 1 vector 3 is a combination of
+    vectors 0..2 plus 1e-3 noise (condition ~1e3: Cholesky QR).  The QR factor with a
+    positive real diagonal is unique, so the two agree to the rounding amplified by
+    the condition number."""
+    L, Ls, block = (4, 4, 4, 4), 4, (2, 2, 2, 2)
+    g = mg.Geometry(L, Ls, block)
+    rng = synth.rng(3300 + nvec)
+    shape = (nvec,) + synth.gaussian_fermion(L, Ls, 1).shape
+    v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    b0 = (slice(0, 2), slice(0, 2), slice(0, 2), slice(0, 2))      # (t, z, y, x) of block 0
+    b1 = (slice(0, 2), slice(0, 2), slice(0, 2), slice(2, 4))      # block 1: x in [2, 4)
+    noise = rng.standard_normal(v[0][b0].shape) + 1j * rng.standard_normal(v[0][b0].shape)
+    v[1][b0] = v[0][b0] + 1e-6 * noise
+    v[3][b1] = 0.5 * v[0][b1] - 0.3j * v[1][b1] + 0.7 * v[2][b1] + 1e-3 * noise
+    lat = hd.Lattice(L, Ls)
+    got = natural(host(hd.subspace_from_vectors(lat, block, dev(planes(v))).vectors()), L, Ls)
+    want = mg.from_blocks(g, mg.basis_from_vectors(g, v).Phi)
+    for k in range(nvec):
+        assert relerr(got[k], want[k]) < 1e-9, k
+    # every block orthonormal: <phi_j^a, phi_k^a> = delta_jk
+    Gb = np.einsum("jak,lak->ajl", np.conj(mg.to_blocks(g, got)), mg.to_blocks(g, got))
+    assert np.abs(Gb - np.eye(nvec)[None]).max() < 1e-12
+
+
 @pytest.mark.parametrize("fdt", ["c128", "c64"])
 def test_chebyshev_filter_subspace_matches_oracle(hd, fdt):
     L, Ls, block, nvec, mf = (4, 4, 4, 4), 8, (2, 2, 2, 2), 4, 0.01
