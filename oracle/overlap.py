@@ -83,3 +83,42 @@ def schur_last(hw_eigvals, beta, R, g5, V):
         K = (-1.0) ** i * lam - c[i - 1] ** 2 / K
     f = beta[0] * lam - c[n - 2] ** 2 / K if n > 1 else beta[0] * lam
     return R * g5 + (V * f) @ np.conj(V.T)
+
+
+# ------------------------------------------------ the two-level method on it
+def apply_cf_hop(U, psi, mu: int, sign: int, beta, bc_t: int = 1) -> np.ndarray:
+    """The part of the continued-fraction operator made of the single 4d hop reading
+    psi(x + sign*mu): component i gets (-1)^i (beta_0 on the last) times
+    gamma5 (-1/2) hop(mu, sign) of its own component (the couplings and R gamma5 are
+    site-local and belong to no hop)."""
+    s = diag_scales(beta)
+    h = dwf.spin_mul(dwf.GAMMA5, -0.5 * dwf.hop(U, psi, mu, sign, bc_t))
+    return h * s[:, None, None]
+
+
+def cf_coarse_op(U, sub, M5: float, beta, R: float, bc_t: int = 1) -> np.ndarray:
+    """Little operator of the continued-fraction operator on the block basis ``sub``
+    (an ``oracle.multigrid.Subspace`` whose fifth coordinate holds the N components):
+    A[a, d, j, k] = <phi_j^a | H_cf | phi_k^{a+d}>, the construction of Section 4
+    applied to H_cf.  As for the domain-wall operator, leg d = (mu, sign) keeps the
+    hops reading x + sign*mu that leave the block and the self leg keeps the rest
+    (the components' couplings and R gamma5 are site-local, so they stay in it)."""
+    from . import multigrid as mg
+    g = sub.geom
+    nvec = sub.nvec
+    A = np.zeros((g.Vc, mg.NLEGS, nvec, nvec), dtype=np.complex128)
+    phit = np.conj(np.transpose(sub.Phi, (1, 0, 2)))             # (Vc, j, K)
+    phis = [mg.from_blocks(g, sub.Phi[k]) for k in range(nvec)]
+
+    def project(Y):                                             # Y: (k, Vc, K)
+        return np.matmul(phit, np.transpose(Y, (1, 2, 0)))
+
+    Yself = np.stack([mg.to_blocks(g, apply_cf(U, p, M5, beta, R, bc_t)) for p in phis])
+    for mu in range(4):
+        for s in (+1, -1):
+            m = mg.crossing_mask(g, mu, s)[..., None, None, None]
+            Yd = np.stack([mg.to_blocks(g, m * apply_cf_hop(U, p, mu, s, beta, bc_t)) for p in phis])
+            Yself -= Yd
+            A[:, mg.leg_index(mu, s)] = project(Yd)
+    A[:, 0] = project(Yself)
+    return A
