@@ -498,6 +498,27 @@ int hdcr_apply_cf_overlap(const hdcr_geom* g, double M5, const hdcr_cf_params* c
 int hdcr_cf_cr_solve(const hdcr_geom* g, double M5, const hdcr_cf_params* cf, const void* U,
                      const void* b, void* x, int dtype, double tol, int max_iter,
                      hdcr_solve_stats* stats, void* stream);
+/* The two-level method on the continued-fraction operator (Section 4's
+ * construction with H_cf in place of H).
+ * hdcr_cf_filter: the subspace filter on H_cf, in place on one field x of
+ * ``dtype``: sp->kind HDCR_SUBSPACE_CR_SMOOTH (sp->order CR steps on H_cf x = 0)
+ * or HDCR_SUBSPACE_CHEBYSHEV (T_order(t(H_cf^2)), t mapping [lam_cut^2, lam_max^2]
+ * onto [-1, 1], then normalised); the other fields of sp are ignored.  The
+ * filtered fields, block-orthonormalised by hdcr_subspace_from_vectors on the same
+ * geometry (its Ls = the number of components), form the basis; there is no
+ * chiral split (H_cf has no Gamma5-like involution to split by).  Synchronises
+ * ``stream``.  Errors: BAD_ARG, CUDA, NO_MEMORY.
+ * hdcr_cf_build_coarse_op: A^{ab}_jk = <phi_j^a | H_cf | phi_k^b> on that basis
+ * (stored C128, legs as for hdcr_build_coarse_op: the hops leaving the block per
+ * leg, everything else, the components' couplings and R gamma5 included, in the
+ * self leg).  The handle keeps the operator: hdcr_solve (inner dtype C128),
+ * hdcr_apply_coarse, hdcr_coarse_invert and the coarse solves then run on H_cf;
+ * hdcr_solve_multi refuses it.  The basis must be stored C128; U is C128 (device
+ * or host).  Synchronises ``stream``.  Errors: BAD_ARG, CUDA, NO_MEMORY. */
+int hdcr_cf_filter(const hdcr_geom* g, double M5, const hdcr_cf_params* cf, const void* U, void* x,
+                   int dtype, const hdcr_subspace_params* sp, void* stream);
+int hdcr_cf_build_coarse_op(const hdcr_subspace* sub, double M5, const hdcr_cf_params* cf, const void* U,
+                            void* stream, hdcr_coarse** out);
 
 /* ---------------------------------------------------------------- gauge force
  * hdcr_gauge_force: the gauge-link gradient of a solve (not in the paper;

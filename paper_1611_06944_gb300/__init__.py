@@ -102,7 +102,7 @@ def load_library():
 __all__ = [
     "HDCRError", "Lattice", "probe_fma_rate", "tc_gemm_info", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info",
-    "apply_cf_overlap", "cf_cr_solve", "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
+    "apply_cf_overlap", "cf_cr_solve", "cf_filter", "build_cf_coarse_op", "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
     "build_level2", "level2_get", "coarse_solve_level2",
@@ -586,6 +586,36 @@ def build_coarse_op(sub: Subspace, U: torch.Tensor, M5: float, mf: float,
     _check(_L.hdcr_build_coarse_op(sub.handle, C_ref(p), _dev(U, "U", True), code, _stream(stream),
                                    ctypes.byref(h)), "build_coarse_op")
     return CoarseOperator(h, sub, op_dtype, M5, mf)
+
+
+def cf_filter(lat: Lattice, U: torch.Tensor, x: torch.Tensor, M5: float, beta, R: float, kind: str = "cr",
+              order: int = 10, lam_cut: float = 0.5, lam_max: float = 8.0, stream=None) -> torch.Tensor:
+    """The subspace filter on the continued-fraction operator, in place on the field x
+    (lat.Ls = len(beta) + 1 components): kind "cr" (order CR steps on H_cf x = 0) or
+    "chebyshev" (the low-pass filter of Fig. 1 on H_cf^2).  Returns x."""
+    if _nfields(lat, x, "x") != 1:
+        raise ValueError("cf_filter takes one field")
+    sp = _lib.hdcr_subspace_params()
+    sp.kind = {"cr": _lib.HDCR_SUBSPACE_CR_SMOOTH, "chebyshev": _lib.HDCR_SUBSPACE_CHEBYSHEV}[kind]
+    sp.order = int(order)
+    sp.lam_cut = float(lam_cut)
+    sp.lam_max = float(lam_max)
+    g = lat.c_geom()
+    _check(_L.hdcr_cf_filter(C_ref(g), float(M5), C_ref(_cf_params(beta, R)), _dev(U, "U"), _dev(x, "x"), _code(x),
+                             C_ref(sp), _stream(stream)), "cf_filter")
+    return x
+
+
+def build_cf_coarse_op(sub: Subspace, U: torch.Tensor, M5: float, beta, R: float, stream=None) -> CoarseOperator:
+    """The little operator of the continued-fraction operator on the complex128 basis
+    ``sub`` (built on its N-component geometry); hdcr_solve with the returned handle
+    runs the two-level method on H_cf."""
+    if U.dtype != torch.complex128:
+        raise TypeError("build_cf_coarse_op takes complex128 links")
+    h = ctypes.c_void_p()
+    _check(_L.hdcr_cf_build_coarse_op(sub.handle, float(M5), C_ref(_cf_params(beta, R)), _dev(U, "U", True),
+                                      _stream(stream), ctypes.byref(h)), "cf_build_coarse_op")
+    return CoarseOperator(h, sub, torch.complex128, M5, 0.0)
 
 
 def apply_coarse(co: CoarseOperator, c: torch.Tensor, stream=None) -> torch.Tensor:

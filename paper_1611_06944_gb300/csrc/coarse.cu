@@ -19,6 +19,7 @@
 // On a coarse extent of 2 the legs +mu and -mu reach the same coarse site and
 // are both kept.
 #include <algorithm>
+#include <vector>
 
 #include "host_io.cuh"
 #include "level2.cuh"
@@ -410,20 +411,31 @@ template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) restrict_kernel(Geom g, BlockGeom bg,
                                                                const cpx<R>* __restrict__ phi,
                                                                const cpx<R>* __restrict__ fine,
-                                                               cpx<R>* __restrict__ coarse, int nvec) {
+                                                               cpx<R>* __restrict__ coarse, int nvec,
+                                                               bool table) {
+  extern __shared__ int sx4[];  // the block's 4d sites (bvol of them), when ``table``
   const int a = blockIdx.x;
   const int k0 = blockIdx.y * RP_KC;
   const int r = blockIdx.z;
   const long long fs = g.V5 * 12;
   const cpx<R>* v = fine + (long long)r * fs;
+  if (table) {
+    for (int i = threadIdx.x; i < bg.bvol; i += RED_THREADS)
+      sx4[i] = (int)(block_site(g, bg, a, (long long)i * g.Ls) / g.Ls);
+    __syncthreads();
+  }
   double acc[2 * RP_KC];
 #pragma unroll
   for (int i = 0; i < 2 * RP_KC; ++i) acc[i] = 0.0;
-  const long long nel = bg.K5 * 12;
-  for (long long e = threadIdx.x; e < nel; e += RED_THREADS) {
-    const int c = (int)(e / bg.K5);
-    const long long l = e - (long long)c * bg.K5;
-    const long long off = fidx(g, c, block_site(g, bg, a, l));
+  // elements in the order (4d site of the block, component, s): one 4d site's 12 Ls
+  // elements are contiguous in the field, so the index is one 32-bit division and a
+  // table lookup
+  const int per = 12 * g.Ls;
+  const int nel = bg.bvol * per;
+  for (int e = threadIdx.x; e < nel; e += RED_THREADS) {
+    const int site = e / per;
+    const unsigned x4 = table ? (unsigned)sx4[site] : (unsigned)(block_site(g, bg, a, (long long)site * g.Ls) / g.Ls);
+    const unsigned off = x4 * (unsigned)per + (unsigned)(e - site * per);
     const cpx<R> q = ld(v + off);
 #pragma unroll
     for (int i = 0; i < RP_KC; ++i) {
@@ -470,8 +482,12 @@ __global__ void prolong_kernel(Geom g, BlockGeom bg, const cpx<R>* __restrict__ 
 template <typename R>
 int launch_restrict(const hdcr_subspace* sub, const cpx<R>* fine, cpx<R>* coarse, int nrhs, cudaStream_t st) {
   dim3 grid(sub->bg.Vc, (sub->nvec + RP_KC - 1) / RP_KC, nrhs);
-  restrict_kernel<R><<<grid, RED_THREADS, 0, st>>>(sub->g, sub->bg, (const cpx<R>*)sub->vecs, fine, coarse,
-                                                   sub->nvec); count_launch();
+  // the table of the block's 4d sites in shared memory when it fits (48 KB), else
+  // the sites are worked out per element
+  const bool table = sub->bg.bvol <= 12 * 1024;
+  const size_t smem = table ? sizeof(int) * (size_t)sub->bg.bvol : 0;
+  restrict_kernel<R><<<grid, RED_THREADS, smem, st>>>(sub->g, sub->bg, (const cpx<R>*)sub->vecs, fine, coarse,
+                                                      sub->nvec, table); count_launch();
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }
@@ -625,6 +641,30 @@ static int build_op(const hdcr_subspace* sub, double M5, double mf, const cpx<R>
 
 }  // namespace hdcr
 
+namespace hdcr {
+
+int fill_neighbour_table(const BlockGeom& bg, int* nbr, cudaStream_t st) {
+  std::vector<int> hn((size_t)bg.Vc * NLEGS);
+  for (int a = 0; a < bg.Vc; ++a) {
+    int c[4];
+    coarse_coords(bg, a, c);
+    hn[(size_t)a * NLEGS] = a;
+    for (int mu = 0; mu < 4; ++mu)
+      for (int sg = 0; sg < 2; ++sg) {
+        int d[4] = {c[0], c[1], c[2], c[3]};
+        d[mu] = (c[mu] + (sg == 0 ? 1 : -1) + bg.Lc[mu]) % bg.Lc[mu];
+        hn[(size_t)a * NLEGS + leg_of(mu, sg == 0 ? 1 : -1)] =
+            ((d[3] * bg.Lc[2] + d[2]) * bg.Lc[1] + d[1]) * bg.Lc[0] + d[0];
+      }
+  }
+  cudaError_t e = cudaMemcpyAsync(nbr, hn.data(), sizeof(int) * hn.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "coarse neighbour table");
+  return HDCR_OK;
+}
+
+}  // namespace hdcr
+
 using namespace hdcr;
 
 static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params* p, const void* U,
@@ -715,24 +755,7 @@ static int build_coarse_op_entry(const hdcr_subspace* sub, const hdcr_dwf_params
   if (!store_c128) A_build = co->A;
   if (e == cudaSuccess) e = cudaMalloc(&co->nbr, sizeof(int) * bg.Vc * NLEGS);
   if (e != cudaSuccess) s = cuda_status(e, "coarse operator storage");
-  if (s == HDCR_OK) {
-    int* hn = new int[bg.Vc * NLEGS];
-    for (int a = 0; a < bg.Vc; ++a) {
-      int c[4];
-      coarse_coords(bg, a, c);
-      hn[a * NLEGS] = a;
-      for (int mu = 0; mu < 4; ++mu)
-        for (int sg = 0; sg < 2; ++sg) {
-          int d[4] = {c[0], c[1], c[2], c[3]};
-          d[mu] = (c[mu] + (sg == 0 ? 1 : -1) + bg.Lc[mu]) % bg.Lc[mu];
-          hn[a * NLEGS + leg_of(mu, sg == 0 ? 1 : -1)] = ((d[3] * bg.Lc[2] + d[2]) * bg.Lc[1] + d[1]) * bg.Lc[0] + d[0];
-        }
-    }
-    e = cudaMemcpyAsync(co->nbr, hn, sizeof(int) * bg.Vc * NLEGS, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    delete[] hn;
-    if (e != cudaSuccess) s = cuda_status(e, "coarse neighbour table");
-  }
+  if (s == HDCR_OK) s = fill_neighbour_table(bg, co->nbr, st);
   if (s == HDCR_OK) {
     if (op_dtype == HDCR_C128)
       s = build_op<double>(sub, p->M5, p->mf, (const cpx<double>*)Ub, (const cpx<double>*)phi, (cpx<double>*)Y,
@@ -832,6 +855,7 @@ extern "C" void hdcr_coarse_destroy(hdcr_coarse* co) {
   if (co->Ainv) cudaFree(co->Ainv);
   if (co->dws) cudaFree(co->dws);
   level2_free(co->l2);
+  cf_coef_free(co->cf);
   delete co;
 }
 

@@ -72,6 +72,8 @@ struct hdcr_subspace {
 
 namespace hdcr {
 struct Level2;
+struct CFCoef;
+void cf_coef_free(CFCoef* cf);
 }
 
 struct hdcr_coarse {
@@ -86,6 +88,7 @@ struct hdcr_coarse {
   void* dws;    // workspace of the multi-right-hand-side dense solve (grown on demand)
   size_t dws_bytes;
   hdcr::Level2* l2;  // third level of the coarse solve (hdcr_coarse_build_level2), or null
+  hdcr::CFCoef* cf;  // set: built on the continued-fraction operator (hdcr_cf_build_coarse_op)
   double M5, mf;
   int device;
 };
@@ -101,6 +104,8 @@ int launch_prolong(const hdcr_subspace* sub, const cpx<R>* coarse, const cpx<R>*
                    int nrhs, cudaStream_t st);
 template <typename R>
 int launch_coarse_apply(const hdcr_coarse* co, const cpx<R>* in, cpx<R>* out, int nrhs, cudaStream_t st);
+// nbr[a][leg]: the coarse site each leg of site a reaches (device array of Vc * 9 ints)
+int fill_neighbour_table(const BlockGeom& bg, int* nbr, cudaStream_t st);
 
 template <typename R>
 struct CoarseOp {

@@ -320,12 +320,14 @@ static int solve_impl(const hdcr_coarse* co, SolveCache* c, const void* U, const
   const long long fs = c->fs;
   const int nb = num_blocks(fs, 256, 4096);
   FineOp<double> H64{co->g, co->M5, co->mf, (const cpx<double>*)U};
+  H64.cf = co->cf;
   const cpx<R>* Uin = (const cpx<R>*)U;
   if (sizeof(R) != 8) {
     HDCR_TRY(launch_convert(U, HDCR_C128, c->U_in, HDCR_C64, (long long)co->g.V4 * 36, st));
     Uin = (const cpx<R>*)c->U_in;
   }
   FineOp<R> Hin{co->g, co->M5, co->mf, Uin};
+  Hin.cf = co->cf;
   if (prm->smoother_kind == HDCR_SMOOTHER_CHEBYSHEV)
     c->cheb_c = cheb_inverse_coeffs(prm->cheb_lo, prm->cheb_hi, prm->smoother_order);
   double* scal = c->rb.scal;    // [0, 2*restart): MGS coefficients; 128: |w|^2; 130: a; 132: |r|^2; 133: |b|^2

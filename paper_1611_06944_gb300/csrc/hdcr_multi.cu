@@ -534,6 +534,10 @@ extern "C" int hdcr_solve_multi(hdcr_coarse* co, const void* U, const void* b, v
     set_error("hdcr_solve_multi: null pointer, b == x or nrhs outside 1..%d", MB_MAX_RHS);
     return HDCR_ERR_BAD_ARG;
   }
+  if (co->cf) {
+    set_error("hdcr_solve_multi: the batched solve runs the domain-wall operator only (use hdcr_solve)");
+    return HDCR_ERR_BAD_ARG;
+  }
   if (!(prm->tol > 0.0) || prm->max_outer < 1 || prm->restart < 1 || prm->restart > 64 ||
       prm->smoother_kind != HDCR_SMOOTHER_CHEBYSHEV || prm->smoother_order < 1 || !(prm->cheb_lo > 0.0) ||
       !(prm->cheb_hi > prm->cheb_lo) || prm->coarse_solver != HDCR_COARSE_DENSE ||

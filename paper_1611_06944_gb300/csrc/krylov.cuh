@@ -12,6 +12,13 @@ template <typename R>
 int launch_g5dwf_dot(const Geom& g, double M5, double mf, const cpx<R>* U, const cpx<R>* in,
                      cpx<R>* out, RedScratch rs, double* result, cudaStream_t st);
 
+// The continued-fraction overlap operator (overlap.cu): its coefficients, and
+// out = H_cf in (nrhs fields), with Re <in, out> into *dot when dot is set (nrhs 1).
+struct CFCoef;
+template <typename R>
+int launch_cf(const Geom& g, double M5, const CFCoef& cf, const cpx<R>* U, const cpx<R>* in, cpx<R>* out, int nrhs,
+              RedScratch rs, double* dot, cudaStream_t st);
+
 // An operator usable by cr_run: n() complex entries per vector, apply, and
 // apply with Re <in, out> reduced into a device double.
 template <typename R>
@@ -20,11 +27,16 @@ struct FineOp {
   double M5, mf;
   const cpx<R>* U;
   int nrhs = 1;  // fields a vector of this operator spans (one launch applies H to all)
+  // set: the continued-fraction operator of Section 3 (its N components where the
+  // domain-wall operator has s) instead of Gamma5 D_dwf; mf is then unused
+  const CFCoef* cf = nullptr;
   long long n() const { return g.V5 * 12 * nrhs; }  // complex entries of one vector
   int apply(const cpx<R>* in, cpx<R>* out, cudaStream_t st) const {
+    if (cf) return launch_cf<R>(g, M5, *cf, U, in, out, nrhs, RedScratch{nullptr, nullptr}, nullptr, st);
     return launch_g5dwf<R>(g, M5, mf, U, in, out, nrhs, st);
   }
   int apply_dot(const cpx<R>* in, cpx<R>* out, RedScratch rs, double* res, cudaStream_t st) const {
+    if (cf) return launch_cf<R>(g, M5, *cf, U, in, out, 1, rs, res, st);
     return launch_g5dwf_dot<R>(g, M5, mf, U, in, out, rs, res, st);
   }
 };
