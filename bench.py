@@ -811,11 +811,20 @@ def run_table1(args, world, rank, local):
 
     st_rb, t_rb = _sync_time(cgne)
     del xr
-    sub, t_sub = _sync_time(lambda: hd.build_subspace(lat, U, noise, M5, mf, BLOCK, kind="chebyshev", order=600,
-                                                      lam_cut=0.1, lam_max=8.0, filter_dtype=torch.complex64,
-                                                      store_dtype=torch.complex64))
-    co, t_co = _sync_time(lambda: hd.build_coarse_op(sub, U, M5, mf, op_dtype=torch.complex64, fast=True))
-    _, t_inv = _sync_time(lambda: hd.coarse_invert(co))
+
+    def setup():
+        sub, t_sub = _sync_time(lambda: hd.build_subspace(lat, U, noise, M5, mf, BLOCK, kind="chebyshev", order=600,
+                                                          lam_cut=0.1, lam_max=8.0, filter_dtype=torch.complex64,
+                                                          store_dtype=torch.complex64))
+        co, t_co = _sync_time(lambda: hd.build_coarse_op(sub, U, M5, mf, op_dtype=torch.complex64, fast=True))
+        _, t_inv = _sync_time(lambda: hd.coarse_invert(co))
+        return sub, co, t_sub, t_co, t_inv
+
+    if args.warmup > 0:  # one untimed setup: first-use costs (stencil tuner, cuBLAS handle, kernel attributes)
+        sub, co, *_ = setup()
+        co.close()
+        sub.close()
+    sub, co, t_sub, t_co, t_inv = setup()
     kw = dict(tol=1e-10, restart=8, max_outer=300, inner_dtype=torch.complex64)
     x = torch.zeros_like(b)
     for _ in range(args.warmup):

@@ -504,9 +504,9 @@ int hdcr_cf_cr_solve(const hdcr_geom* g, double M5, const hdcr_cf_params* cf, co
  * ``dtype``: sp->kind HDCR_SUBSPACE_CR_SMOOTH (sp->order CR steps on H_cf x = 0)
  * or HDCR_SUBSPACE_CHEBYSHEV (T_order(t(H_cf^2)), t mapping [lam_cut^2, lam_max^2]
  * onto [-1, 1], then normalised); the other fields of sp are ignored.  The
- * filtered fields, block-orthonormalised by hdcr_subspace_from_vectors on the same
- * geometry (its Ls = the number of components), form the basis; there is no
- * chiral split (H_cf has no Gamma5-like involution to split by).  Synchronises
+ * filtered fields, split by 4d chirality (hdcr_gamma5_split) and
+ * block-orthonormalised by hdcr_subspace_from_vectors on the same geometry (its
+ * Ls = the number of components), form the basis.  Synchronises
  * ``stream``.  Errors: BAD_ARG, CUDA, NO_MEMORY.
  * hdcr_cf_build_coarse_op: A^{ab}_jk = <phi_j^a | H_cf | phi_k^b> on that basis
  * (stored C128, legs as for hdcr_build_coarse_op: the hops leaving the block per
@@ -517,6 +517,13 @@ int hdcr_cf_cr_solve(const hdcr_geom* g, double M5, const hdcr_cf_params* cf, co
  * or host).  Synchronises ``stream``.  Errors: BAD_ARG, CUDA, NO_MEMORY. */
 int hdcr_cf_filter(const hdcr_geom* g, double M5, const hdcr_cf_params* cf, const void* U, void* x,
                    int dtype, const hdcr_subspace_params* sp, void* stream);
+/* plus = (1 + gamma5)/2 in, minus = (1 - gamma5)/2 in for nfields fields: the 4d
+ * chirality at every site and fifth coordinate (spins 0, 1 and 2, 3 of the chiral
+ * basis; no R5 reflection).  The split that makes the continued-fraction basis work:
+ * without it the two-level solve on H_cf stalls (measured); with the filtered fields
+ * split this way it converges.  Asynchronous on ``stream``.  Errors: BAD_ARG. */
+int hdcr_gamma5_split(const hdcr_geom* g, const void* in, void* plus, void* minus, int dtype, int nfields,
+                      void* stream);
 int hdcr_cf_build_coarse_op(const hdcr_subspace* sub, double M5, const hdcr_cf_params* cf, const void* U,
                             void* stream, hdcr_coarse** out);
 

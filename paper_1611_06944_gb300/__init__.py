@@ -102,7 +102,7 @@ def load_library():
 __all__ = [
     "HDCRError", "Lattice", "probe_fma_rate", "tc_gemm_info", "apply_g5dwf", "apply_gamma5_r5", "pack", "unpack",
     "convert", "cdot", "cdot_noalloc", "norm2", "stencil_tune", "stencil_tune_info",
-    "apply_cf_overlap", "cf_cr_solve", "cf_filter", "build_cf_coarse_op", "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
+    "apply_cf_overlap", "cf_cr_solve", "cf_filter", "build_cf_coarse_op", "gamma5_split", "build_cf_subspace", "h16_bytes", "encode_h16", "decode_h16", "apply_g5dwf_h16", "mobius_to_shamir", "cr_solve", "cr_solve_into", "library_path",
     "Subspace", "build_subspace", "subspace_from_vectors", "restrict", "prolong",
     "CoarseOperator", "build_coarse_op", "apply_coarse", "coarse_invert", "coarse_solve_dense",
     "build_level2", "level2_get", "coarse_solve_level2",
@@ -604,6 +604,32 @@ def cf_filter(lat: Lattice, U: torch.Tensor, x: torch.Tensor, M5: float, beta, R
     _check(_L.hdcr_cf_filter(C_ref(g), float(M5), C_ref(_cf_params(beta, R)), _dev(U, "U"), _dev(x, "x"), _code(x),
                              C_ref(sp), _stream(stream)), "cf_filter")
     return x
+
+
+def gamma5_split(lat: Lattice, v: torch.Tensor, stream=None):
+    """((1 + gamma5)/2 v, (1 - gamma5)/2 v): the 4d chirality of each site and fifth
+    coordinate (no R5 reflection) for every field of v."""
+    n = _nfields(lat, v, "v")
+    plus, minus = torch.empty_like(v), torch.empty_like(v)
+    g = lat.c_geom()
+    _check(_L.hdcr_gamma5_split(C_ref(g), _dev(v, "v"), _dev(plus, "plus"), _dev(minus, "minus"), _code(v), n,
+                                _stream(stream)), "gamma5_split")
+    return plus, minus
+
+
+def build_cf_subspace(lat: Lattice, U: torch.Tensor, noise: torch.Tensor, M5: float, beta, R: float, block,
+                      kind: str = "cr", order: int = 20, lam_cut: float = 0.3, lam_max: float = 10.0,
+                      stream=None) -> "Subspace":
+    """Section 4's subspace for the continued-fraction operator: the nvec/2 complex128
+    noise fields (copied) filtered by cf_filter, split by 4d chirality (plus halves
+    first, then minus), block-orthonormalised in FP64 (basis stored complex128)."""
+    if noise.dtype != torch.complex128:
+        raise TypeError("build_cf_subspace takes complex128 noise")
+    x = noise.clone()
+    for i in range(_nfields(lat, x, "noise")):
+        cf_filter(lat, U, x[i], M5, beta, R, kind=kind, order=order, lam_cut=lam_cut, lam_max=lam_max, stream=stream)
+    plus, minus = gamma5_split(lat, x, stream=stream)
+    return subspace_from_vectors(lat, block, torch.cat([plus, minus]).contiguous(), stream=stream)
 
 
 def build_cf_coarse_op(sub: Subspace, U: torch.Tensor, M5: float, beta, R: float, stream=None) -> CoarseOperator:

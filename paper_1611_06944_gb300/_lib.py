@@ -139,6 +139,7 @@ SIGNATURES = {
     "hdcr_cf_cr_solve": (_I, [_G, _D, C.POINTER(hdcr_cf_params), _P, _P, _P, _I, _D, _I, _ST, _P]),
     "hdcr_cf_filter": (_I, [_G, _D, C.POINTER(hdcr_cf_params), _P, _P, _I, C.POINTER(hdcr_subspace_params), _P]),
     "hdcr_cf_build_coarse_op": (_I, [_P, _D, C.POINTER(hdcr_cf_params), _P, _P, C.POINTER(_P)]),
+    "hdcr_gamma5_split": (_I, [_G, _P, _P, _P, _I, _I, _P]),
     "hdcr_gauge_force": (_I, [_G, _P, _P, _P, _I, _P]),
     "hdcr_gauge_grad": (_I, [_G, _P, _P, _P, _I, _P]),
 }

@@ -20,6 +20,11 @@ int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, co
 // prev <- 2 (a H in + b cur) - prev for nrhs fields (a Chebyshev step fused into the FP32 stencil)
 int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in,
                          const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st);
+// FP64 operator with one Chebyshev smoother step fused into its epilogue (dwf.cu):
+// prev <- nx = 2 (a H in + b cur) - prev, acc += ck nx (one field)
+int launch_g5dwf_cheb(const Geom& g, double M5, double mf, const cpx<double>* U, const cpx<double>* in,
+                      const cpx<double>* cur, cpx<double>* prev, cpx<double>* acc, double a, double b, double ck,
+                      cudaStream_t st);
 // FP32 operator on FP16-stored fields (dwf_h16.cu): nrhs fields of 52 V5 bytes each
 int launch_g5dwf_h16(const Geom& g, double M5, double mf, const cpx<float>* U, const void* in, void* out, int nrhs,
                      cudaStream_t st);

@@ -133,8 +133,19 @@ int cheb_smoother(const FineOp<R>& H, const cpx<R>* r, cpx<R>* out, const std::v
   cpx<R>* cur = w.t1;
   for (int k = 2; k <= order; ++k) {
     HDCR_TRY(H.apply(cur, w.h1, st));
-    HDCR_TRY(H.apply(w.h1, w.h2, st));
     mv += 2;
+    if constexpr (sizeof(R) == 8) {
+      if (!H.cf && H.nrhs == 1) {  // the step fused into the second application (domain-wall FP64)
+        HDCR_TRY(launch_g5dwf_cheb(H.g, H.M5, H.mf, (const cpx<double>*)H.U, (const cpx<double>*)w.h1,
+                                   (const cpx<double>*)cur, (cpx<double>*)prev, (cpx<double>*)out, (double)a,
+                                   (double)b, c[k], st));
+        cpx<R>* t = prev;
+        prev = cur;
+        cur = t;
+        continue;
+      }
+    }
+    HDCR_TRY(H.apply(w.h1, w.h2, st));
     cheb_step_kernel<R><<<nb, 256, 0, st>>>(w.h2, cur, prev, out, n, a, b, (R)c[k], 1); count_launch();
     HDCR_LAUNCH_CHECK();
     cpx<R>* t = prev;

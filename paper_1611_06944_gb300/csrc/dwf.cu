@@ -38,6 +38,48 @@ __global__ void __launch_bounds__(256, 2) g5dwf_kernel(Geom g, R diag, R mf, con
   store_g5r5<R, LS>(g, out, x4, s, acc);
 }
 
+// One step of the Chebyshev smoother's recurrence fused into the FP64 operator:
+// with h = H in at every element, prev <- nx = 2 (a h + b cur) - prev and
+// acc += ck nx (the same arithmetic, in the same order, as the separate step
+// kernel after a plain application, so the same bits).  The operator is
+// ALU-bound, so the extra field traffic of the epilogue costs little; the
+// separate pass over four fields does not happen.
+template <int LS>
+__global__ void __launch_bounds__(256, 2) g5dwf_cheb_kernel(Geom g, double diag, double mf,
+                                                            const cpx<double>* __restrict__ U,
+                                                            const cpx<double>* __restrict__ in,
+                                                            const cpx<double>* __restrict__ cur,
+                                                            cpx<double>* __restrict__ prev,
+                                                            cpx<double>* __restrict__ acc_out, double a, double b,
+                                                            double ck) {
+  const int ls = ls_of<LS>(g);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.V5) return;
+  const int i5 = (int)idx;
+  const int x4 = i5 / ls;
+  const int s = i5 - x4 * ls;
+  cpx<double> acc[4][3];
+  dwf_site<double, LS>(g, diag, mf, U, in, x4, s, acc);
+  const unsigned o0 = (unsigned)(x4 * 12 * ls + (ls - 1 - s));  // the R5 reflection of store_g5r5
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      cpx<double> h = acc[sp][c];
+      if (sp >= 2) h = cpx<double>(-h.re, -h.im);
+      const unsigned o = o0 + (3 * sp + c) * ls;
+      const cpx<double> cv = ld(cur + o), pv = ld(prev + o);
+      cpx<double> nx;
+      nx.re = 2.0 * fma(a, h.re, b * cv.re) - pv.re;
+      nx.im = 2.0 * fma(a, h.im, b * cv.im) - pv.im;
+      st(prev + o, nx);
+      cpx<double> av = ld(acc_out + o);
+      av.re = fma(ck, nx.re, av.re);
+      av.im = fma(ck, nx.im, av.im);
+      st(acc_out + o, av);
+    }
+}
+
 template <typename R>
 __global__ void gamma5_r5_kernel(Geom g, const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
                                  int nfields) {
@@ -162,6 +204,19 @@ int launch_g5dwf(const Geom& g, double M5, double mf, const void* U, const void*
 }
 template int launch_g5dwf<double>(const Geom&, double, double, const void*, const void*, void*, int,
                                   cudaStream_t);
+
+int launch_g5dwf_cheb(const Geom& g, double M5, double mf, const cpx<double>* U, const cpx<double>* in,
+                      const cpx<double>* cur, cpx<double>* prev, cpx<double>* acc, double a, double b, double ck,
+                      cudaStream_t st) {
+  const int threads = 256;
+  int slot;
+  stencil_timer_begin(0, g.V5, st, &slot);
+  HDCR_DISPATCH_LS(g.Ls, (g5dwf_cheb_kernel<LSC><<<num_blocks(g.V5, threads), threads, 0, st>>>(
+                             g, 5.0 - M5, mf, U, in, cur, prev, acc, a, b, ck)));
+  stencil_timer_end(slot, st);
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
+}
 template int launch_g5dwf<float>(const Geom&, double, double, const void*, const void*, void*, int,
                                  cudaStream_t);
 

@@ -247,6 +247,20 @@ __global__ void __launch_bounds__(256) cf_part_kernel(Geom g, R m0, CFCoef cf, c
   }
 }
 
+// plus = (1 + gamma5)/2 in, minus = (1 - gamma5)/2 in: the 4d chirality of every
+// site and fifth coordinate (the upper and the lower two spins in the chiral basis)
+template <typename R>
+__global__ void g5_split_kernel(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ plus, cpx<R>* __restrict__ minus,
+                                long long n, int ls) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)((e / ls) % 12);
+    const cpx<R> v = ld(in + e);
+    const cpx<R> z((R)0, (R)0);
+    st(plus + e, c < 6 ? v : z);
+    st(minus + e, c < 6 ? z : v);
+  }
+}
+
 constexpr int CFP_J = 4;  // basis vectors per projection CTA
 
 // Column k of the little operator from Y = (part of H_cf) phi_k: for block a and
@@ -467,4 +481,29 @@ extern "C" int hdcr_cf_build_coarse_op(const hdcr_subspace* sub, double M5, cons
   Staged su;  // links given in host memory are staged through the device
   HDCR_TRY(su.in(U, (size_t)sub->g.V4 * 36 * 16, st));
   return cf_build_impl(sub, M5, cf, (const cpx<double>*)su.ptr(), st, out);
+}
+
+extern "C" int hdcr_gamma5_split(const hdcr_geom* gp, const void* in, void* plus, void* minus, int dtype, int nfields,
+                                 void* stream) {
+  Geom g;
+  HDCR_TRY(make_geom(gp, &g));
+  if (!in || !plus || !minus || plus == minus || nfields < 1) {
+    set_error("hdcr_gamma5_split: bad pointers or nfields");
+    return HDCR_ERR_BAD_ARG;
+  }
+  const long long n = g.V5 * 12 * nfields;
+  cudaStream_t st = as_stream(stream);
+  if (dtype == HDCR_C128)
+    g5_split_kernel<double><<<num_blocks(n, 256, 8192), 256, 0, st>>>((const cpx<double>*)in, (cpx<double>*)plus,
+                                                                     (cpx<double>*)minus, n, g.Ls);
+  else if (dtype == HDCR_C64)
+    g5_split_kernel<float><<<num_blocks(n, 256, 8192), 256, 0, st>>>((const cpx<float>*)in, (cpx<float>*)plus,
+                                                                    (cpx<float>*)minus, n, g.Ls);
+  else {
+    set_error("hdcr_gamma5_split: unknown dtype %d", dtype);
+    return HDCR_ERR_BAD_ARG;
+  }
+  count_launch();
+  HDCR_LAUNCH_CHECK();
+  return HDCR_OK;
 }
