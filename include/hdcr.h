@@ -232,8 +232,8 @@ int hdcr_norm2(const void* u, size_t n, int dtype, double* result, void* stream)
  * only launches kernels and clears the counter on ``stream``.  n may not exceed
  * HDCR_NOALLOC_MAX_N (BAD_ARG otherwise).  The first call on a device looks up
  * the array's device address with that device current and keeps it for the
- * life of the process; make that first call before any stream capture, and
- * make no call after a device reset (the kept address would be stale).  All
+ * life of the process; make no call after a device reset (the kept address
+ * would be stale).  All
  * calls share the one array: calls that overlap on the GPU (different streams)
  * race and give wrong results.  result: DEVICE pointer to 2 doubles. */
 #define HDCR_NOALLOC_MAX_N 268435456
@@ -254,8 +254,8 @@ int hdcr_cr_solve(const hdcr_geom* g, const hdcr_dwf_params* p, const void* U,
                   hdcr_solve_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------- red-black CGNE
- * hdcr_cgne_rb_solve: H x = b by the comparison solver of Section 5 (Table 1,
- * "CGNE (red-black)"): with the 4d sites coloured by parity (x+y+z+t) mod 2 and
+ * hdcr_cgne_rb_solve: H x = b by the comparison solver of Section 5 (Table 1's
+ * red-black preconditioned CGNE): with the 4d sites coloured by parity (x+y+z+t) mod 2 and
  * D_dwf = M5 + D_hop (M5 the site-local part, D_hop the 4d hops, which join
  * opposite parities), D x = Gamma5 b is reduced to the odd sites,
  *   S x_o = eta_o - D_oe M5^{-1} eta_e,   S = M5 - D_oe M5^{-1} D_eo,  eta = Gamma5 b,

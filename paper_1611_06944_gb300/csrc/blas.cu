@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(RED_THREADS) cdot_kernel(const cpx<R>* __restr
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     cpx<R> a = ld(u + i), b = ld(v + i);
-    acc[0] += (double)a.re * b.re + (double)a.im * b.im;
-    acc[1] += (double)a.re * b.im - (double)a.im * b.re;
+    acc[0] = fma((double)a.re, (double)b.re, fma((double)a.im, (double)b.im, acc[0]));
+    acc[1] = fma((double)a.re, (double)b.im, fma(-(double)a.im, (double)b.re, acc[1]));
   }
   double tot[2];
   if (grid_reduce<2>(acc, rs, tot)) {
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const cpx<R>* __rest
   } else {
     for (; i < n; i += stride) {
       cpx<R> a = ld(u + i);
-      acc[0] += (double)a.re * a.re + (double)a.im * a.im;
+      acc[0] = fma((double)a.re, (double)a.re, fma((double)a.im, (double)a.im, acc[0]));
     }
   }
   double tot[1];

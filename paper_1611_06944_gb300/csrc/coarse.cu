@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(RED_THREADS) cdot_re_kernel(const cpx<R>* __re
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<R> a = ld(u + i), b = ld(v + i);
-    acc[0] += (double)a.re * b.re + (double)a.im * b.im;
+    acc[0] = fma((double)a.re, (double)b.re, fma((double)a.im, (double)b.im, acc[0]));
   }
   double tot[1];
   if (grid_reduce<1>(acc, rs, tot)) *result = tot[0];
@@ -441,8 +441,9 @@ __global__ void __launch_bounds__(RED_THREADS) restrict_kernel(Geom g, BlockGeom
     for (int i = 0; i < RP_KC; ++i) {
       if (k0 + i < nvec) {
         const cpx<R> p = ld(phi + (long long)(k0 + i) * fs + off);
-        acc[2 * i] += (double)p.re * q.re + (double)p.im * q.im;
-        acc[2 * i + 1] += (double)p.re * q.im - (double)p.im * q.re;
+        // conj(p) q accumulated with four FMAs (no separate products and adds)
+        acc[2 * i] = fma((double)p.re, (double)q.re, fma((double)p.im, (double)q.im, acc[2 * i]));
+        acc[2 * i + 1] = fma((double)p.re, (double)q.im, fma(-(double)p.im, (double)q.re, acc[2 * i + 1]));
       }
     }
   }

@@ -124,7 +124,7 @@ __device__ __forceinline__ cpx<float> ldcg_c(const cpx<float>* p) {
   return cpx<float>(v.x, v.y);
 }
 
-constexpr int GJ_PARTS = 4;                    // threads sharing a row in the panel kernel
+constexpr int GJ_PARTS = 16;                   // threads sharing a row in the panel kernel
 constexpr int GJ_COOP_T = GJ_ROWS * GJ_PARTS;  // threads per CTA of the panel kernel
 
 // argmax over the CTA's threads, written to the CTA's candidate slot

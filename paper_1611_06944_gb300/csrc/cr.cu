@@ -40,8 +40,9 @@ __global__ void __launch_bounds__(RED_THREADS, 2) g5dwf_dot_kernel(Geom g, R dia
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const cpx<R> a = ld(o + (3 * sp + c) * ls);
-        const double sgn = sp >= 2 ? -1.0 : 1.0;
-        acc_d[0] += sgn * ((double)a.re * acc[sp][c].re + (double)a.im * acc[sp][c].im);
+        // Re conj(a) (gamma5 acc): the sign of gamma5 folded into a, two FMAs
+        const double ar = sp >= 2 ? -(double)a.re : (double)a.re, ai = sp >= 2 ? -(double)a.im : (double)a.im;
+        acc_d[0] = fma(ar, (double)acc[sp][c].re, fma(ai, (double)acc[sp][c].im, acc_d[0]));
       }
   }
   double tot[1];
@@ -62,8 +63,8 @@ __global__ void __launch_bounds__(RED_THREADS) cr_setup_r_kernel(const cpx<R>* _
     if (Hx) rv = bv - ld(Hx + i);
     st(r + i, rv);
     st(p + i, rv);
-    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
-    acc[1] += (double)bv.re * bv.re + (double)bv.im * bv.im;
+    acc[0] = fma((double)rv.re, (double)rv.re, fma((double)rv.im, (double)rv.im, acc[0]));
+    acc[1] = fma((double)bv.re, (double)bv.re, fma((double)bv.im, (double)bv.im, acc[1]));
   }
   double tot[2];
   if (grid_reduce<2>(acc, rs, tot)) {
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(RED_THREADS) cr_setup_ap_kernel(const cpx<R>* 
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<R> v = ld(Ar + i);
     st(Ap + i, v);
-    acc[0] += (double)v.re * v.re + (double)v.im * v.im;
+    acc[0] = fma((double)v.re, (double)v.re, fma((double)v.im, (double)v.im, acc[0]));
   }
   double tot[1];
   if (grid_reduce<1>(acc, rs, tot)) s->ApAp = tot[0];
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(RED_THREADS) cr_update_xr_kernel(cpx<R>* __res
     rv.im = fma(-alpha, av.im, rv.im);
     st(x + i, xv);
     st(r + i, rv);
-    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
+    acc[0] = fma((double)rv.re, (double)rv.re, fma((double)rv.im, (double)rv.im, acc[0]));
   }
   double tot[1];
   if (grid_reduce<1>(acc, rs, tot)) s->rr = tot[0];
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(RED_THREADS) cr_update_p_kernel(const cpx<R>* 
     apv.im = fma(beta, apv.im, arv.im);
     st(p + i, pv);
     st(Ap + i, apv);
-    acc[0] += (double)apv.re * apv.re + (double)apv.im * apv.im;
+    acc[0] = fma((double)apv.re, (double)apv.re, fma((double)apv.im, (double)apv.im, acc[0]));
   }
   double tot[1];
   if (grid_reduce<1>(acc, rs, tot)) {
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(RED_THREADS) diff_norm_kernel(const cpx<R>* __
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<R> d = ld(b + i) - ld(Hx + i);
-    acc[0] += (double)d.re * d.re + (double)d.im * d.im;
+    acc[0] = fma((double)d.re, (double)d.re, fma((double)d.im, (double)d.im, acc[0]));
   }
   double tot[1];
   if (grid_reduce<1>(acc, rs, tot)) *result = tot[0];

@@ -44,10 +44,10 @@ __global__ void axpy2_neg_kernel(cpx<double>* __restrict__ w, const cpx<double>*
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<double> a = wj[i], c = zj[i];
     cpx<double> u = w[i], v = z[i];
-    u.re -= br * a.re - bi * a.im;
-    u.im -= br * a.im + bi * a.re;
-    v.re -= br * c.re - bi * c.im;
-    v.im -= br * c.im + bi * c.re;
+    u.re = fma(-br, a.re, fma(bi, a.im, u.re));
+    u.im = fma(-br, a.im, fma(-bi, a.re, u.im));
+    v.re = fma(-br, c.re, fma(bi, c.im, v.re));
+    v.im = fma(-br, c.im, fma(-bi, c.re, v.im));
     w[i] = u;
     z[i] = v;
   }
@@ -78,13 +78,13 @@ __global__ void __launch_bounds__(RED_THREADS) fgcr_update_kernel(cpx<double>* _
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<double> zv = z[i], wv = w[i];
     cpx<double> xv = x[i], rv = r[i];
-    xv.re += ar * zv.re - ai * zv.im;
-    xv.im += ar * zv.im + ai * zv.re;
-    rv.re -= ar * wv.re - ai * wv.im;
-    rv.im -= ar * wv.im + ai * wv.re;
+    xv.re = fma(ar, zv.re, fma(-ai, zv.im, xv.re));
+    xv.im = fma(ar, zv.im, fma(ai, zv.re, xv.im));
+    rv.re = fma(-ar, wv.re, fma(ai, wv.im, rv.re));
+    rv.im = fma(-ar, wv.im, fma(-ai, wv.re, rv.im));
     x[i] = xv;
     r[i] = rv;
-    acc[0] += rv.re * rv.re + rv.im * rv.im;
+    acc[0] = fma((double)rv.re, (double)rv.re, fma((double)rv.im, (double)rv.im, acc[0]));
   }
   double tot[1];
   if (grid_reduce<1>(acc, rs, tot)) *rr = tot[0];

@@ -56,8 +56,8 @@ __global__ void __launch_bounds__(MB_THREADS) mdot_part_kernel(const cpx<double>
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<double> x = u[off + i], y = v[off + i];
-    a += x.re * y.re + x.im * y.im;
-    b += x.re * y.im - x.im * y.re;
+    a = fma((double)x.re, (double)y.re, fma((double)x.im, (double)y.im, a));
+    b = fma((double)x.re, (double)y.im, fma(-(double)x.im, (double)y.re, b));
   }
   block_sum2(a, b);
   if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(a, b);
@@ -89,10 +89,10 @@ __global__ void maxpy2_neg_kernel(cpx<double>* __restrict__ w, const cpx<double>
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<double> a = wj[off + i], c = zj[off + i];
     cpx<double> u = w[off + i], v = z[off + i];
-    u.re -= br * a.re - bi * a.im;
-    u.im -= br * a.im + bi * a.re;
-    v.re -= br * c.re - bi * c.im;
-    v.im -= br * c.im + bi * c.re;
+    u.re = fma(-br, a.re, fma(bi, a.im, u.re));
+    u.im = fma(-br, a.im, fma(-bi, a.re, u.im));
+    v.re = fma(-br, c.re, fma(bi, c.im, v.re));
+    v.im = fma(-br, c.im, fma(-bi, c.re, v.im));
     w[off + i] = u;
     z[off + i] = v;
   }
@@ -126,13 +126,13 @@ __global__ void __launch_bounds__(MB_THREADS) mfgcr_update_kernel(cpx<double>* _
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<double> zv = z[off + i], wv = w[off + i];
     cpx<double> xv = x[off + i], rv = r[off + i];
-    xv.re += ar * zv.re - ai * zv.im;
-    xv.im += ar * zv.im + ai * zv.re;
-    rv.re -= ar * wv.re - ai * wv.im;
-    rv.im -= ar * wv.im + ai * wv.re;
+    xv.re = fma(ar, zv.re, fma(-ai, zv.im, xv.re));
+    xv.im = fma(ar, zv.im, fma(ai, zv.re, xv.im));
+    rv.re = fma(-ar, wv.re, fma(ai, wv.im, rv.re));
+    rv.im = fma(-ar, wv.im, fma(-ai, wv.re, rv.im));
     x[off + i] = xv;
     r[off + i] = rv;
-    acc += rv.re * rv.re + rv.im * rv.im;
+    acc = fma((double)rv.re, (double)rv.re, fma((double)rv.im, (double)rv.im, acc));
   }
   block_sum2(acc, zero);
   if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(acc, 0.0);

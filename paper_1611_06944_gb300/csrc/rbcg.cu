@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(RED_THREADS) rb_update_kernel(cpx<double>* __r
     x[i] = xv;
     t[i] = tv;
     r[i] = rv;
-    acc[0] += rv.re * rv.re + rv.im * rv.im;
-    acc[1] += tv.re * tv.re + tv.im * tv.im;
+    acc[0] = fma(rv.re, rv.re, fma(rv.im, rv.im, acc[0]));
+    acc[1] = fma(tv.re, tv.re, fma(tv.im, tv.im, acc[1]));
   }
   double tot[2];
   if (grid_reduce<2>(acc, rs, tot)) {
