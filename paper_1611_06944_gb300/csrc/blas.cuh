@@ -17,9 +17,11 @@ int launch_convert(const void* in, int idt, void* out, int odt, long long n, cud
 bool g5dwf_x2_ok(const Geom& g, const void* in, const void* out);
 int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in, cpx<float>* out,
                     int nrhs, RedScratch* rs, double* result, cudaStream_t st);
-// prev <- 2 (a H in + b cur) - prev for nrhs fields (a Chebyshev step fused into the FP32 stencil)
+// prev <- nx = 2 (a H in + b cur) - prev for nrhs fields (a Chebyshev step fused into the
+// FP32 stencil), and acc += ck nx when acc is set
 int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in,
-                         const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st);
+                         const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st,
+                         cpx<float>* acc = nullptr, float ck = 0.f);
 // FP64 operator with one Chebyshev smoother step fused into its epilogue (dwf.cu):
 // prev <- nx = 2 (a H in + b cur) - prev, acc += ck nx (one field)
 int launch_g5dwf_cheb(const Geom& g, double M5, double mf, const cpx<double>* U, const cpx<double>* in,

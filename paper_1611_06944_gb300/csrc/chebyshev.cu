@@ -144,6 +144,20 @@ int cheb_smoother(const FineOp<R>& H, const cpx<R>* r, cpx<R>* out, const std::v
         cur = t;
         continue;
       }
+    } else {
+      if (!H.cf && g5dwf_x2_ok(H.g, w.h1, prev) && g5dwf_x2_ok(H.g, cur, out)) {  // the same in FP32
+        int slot;
+        stencil_timer_begin(1, H.g.V5 * H.nrhs, st, &slot);
+        const int s = launch_g5dwf_x2_cheb(H.g, H.M5, H.mf, (const cpx<float>*)H.U, (const cpx<float>*)w.h1,
+                                           (const cpx<float>*)cur, (cpx<float>*)prev, (float)a, (float)b, H.nrhs,
+                                           st, (cpx<float>*)out, (float)c[k]);
+        stencil_timer_end(slot, st);
+        HDCR_TRY(s);
+        cpx<R>* t = prev;
+        prev = cur;
+        cur = t;
+        continue;
+      }
     }
     HDCR_TRY(H.apply(w.h1, w.h2, st));
     cheb_step_kernel<R><<<nb, 256, 0, st>>>(w.h2, cur, prev, out, n, a, b, (R)c[k], 1); count_launch();

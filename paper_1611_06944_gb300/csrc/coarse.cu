@@ -424,9 +424,12 @@ __global__ void __launch_bounds__(RED_THREADS) restrict_kernel(Geom g, BlockGeom
       sx4[i] = (int)(block_site(g, bg, a, (long long)i * g.Ls) / g.Ls);
     __syncthreads();
   }
-  double acc[2 * RP_KC];
+  // each thread sums its elements in R (FP32 for an FP32 basis: the result is
+  // stored in FP32, and FP64 arithmetic would bind the kernel to the slow FP64
+  // pipe); the threads' partial sums are added in FP64
+  R tacc[2 * RP_KC];
 #pragma unroll
-  for (int i = 0; i < 2 * RP_KC; ++i) acc[i] = 0.0;
+  for (int i = 0; i < 2 * RP_KC; ++i) tacc[i] = (R)0;
   // elements in the order (4d site of the block, component, s): one 4d site's 12 Ls
   // elements are contiguous in the field, so the index is one 32-bit division and a
   // table lookup
@@ -441,12 +444,15 @@ __global__ void __launch_bounds__(RED_THREADS) restrict_kernel(Geom g, BlockGeom
     for (int i = 0; i < RP_KC; ++i) {
       if (k0 + i < nvec) {
         const cpx<R> p = ld(phi + (long long)(k0 + i) * fs + off);
-        // conj(p) q accumulated with four FMAs (no separate products and adds)
-        acc[2 * i] = fma((double)p.re, (double)q.re, fma((double)p.im, (double)q.im, acc[2 * i]));
-        acc[2 * i + 1] = fma((double)p.re, (double)q.im, fma(-(double)p.im, (double)q.re, acc[2 * i + 1]));
+        // conj(p) q accumulated with four FMAs
+        tacc[2 * i] = fma(p.re, q.re, fma(p.im, q.im, tacc[2 * i]));
+        tacc[2 * i + 1] = fma(p.re, q.im, fma(-p.im, q.re, tacc[2 * i + 1]));
       }
     }
   }
+  double acc[2 * RP_KC];
+#pragma unroll
+  for (int i = 0; i < 2 * RP_KC; ++i) acc[i] = (double)tacc[i];
   block_reduce<2 * RP_KC>(acc);
   if (threadIdx.x == 0) {
 #pragma unroll

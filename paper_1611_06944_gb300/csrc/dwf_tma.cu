@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(2 * LX * TY * TZ, 1)
       {
         const long long ro = (long long)r * fsize + (unsigned)(x4 * 12 * LS + (LS - 2 - s0));
         dot += store_x2<EPI>(up, lo, a.out + ro, a.in + ro, EPI == X2_CHEB ? a.ch.cur + ro : nullptr, a.ch.a,
-                             a.ch.b, LS);
+                             a.ch.b, LS, EPI == X2_CHEB && a.ch.acc ? a.ch.acc + ro : nullptr, a.ch.ck);
       }
       if (t + 1 < t1) wait(3);
     }

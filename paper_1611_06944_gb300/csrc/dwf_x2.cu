@@ -80,7 +80,8 @@ __device__ __forceinline__ void site_pair(const Geom& g, const cpx<float>* __res
     local_x2(q, pv, nv, wl ? -mf : 1.f, wr ? -mf : 1.f, diag, up, lo);
   }
   const unsigned ob = base + (unsigned)(ls - 2 - s0);
-  *dot += store_x2<EPI>(up, lo, out + ob, in + ob, EPI == X2_CHEB ? ch.cur + ob : nullptr, ch.a, ch.b, ls);
+  *dot += store_x2<EPI>(up, lo, out + ob, in + ob, EPI == X2_CHEB ? ch.cur + ob : nullptr, ch.a, ch.b, ls,
+                        EPI == X2_CHEB && ch.acc ? ch.acc + ob : nullptr, ch.ck);
 }
 
 // blockDim = T::sites * Ls/2: thread (site, p) = (tid / (Ls/2), tid % (Ls/2)).
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(T::sites * 8, 64 / T::sites) g5dwf_x2_kernel(
       for (int r = r0; r < r1; ++r)
         if constexpr (EPI == X2_CHEB)
           site_pair<LS, EPI>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot,
-                             X2Cheb{ch.cur + r * fsize, ch.a, ch.b});
+                             X2Cheb{ch.cur + r * fsize, ch.a, ch.b, ch.acc ? ch.acc + r * fsize : nullptr, ch.ck});
         else
           site_pair<LS, EPI>(g, U, sm, site, x4, p, diag, mf, in + r * fsize, out + r * fsize, &dot, ch);
     }
@@ -343,7 +344,8 @@ int launch_g5dwf_x2(const Geom& g, double M5, double mf, const cpx<float>* U, co
 }
 
 int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* U, const cpx<float>* in,
-                         const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st) {
+                         const cpx<float>* cur, cpx<float>* prev, float a, float b, int nrhs, cudaStream_t st,
+                         cpx<float>* acc, float ck) {
   const float diag = (float)(5.0 - M5), fmf = (float)mf;
   int v, tiles, sites;
   HDCR_TRY(x2_pick(g, diag, fmf, U, in, prev, nrhs, false, st, &v));  // prev is read: no tuning here
@@ -352,8 +354,8 @@ int launch_g5dwf_x2_cheb(const Geom& g, double M5, double mf, const cpx<float>* 
     x2_variant_fits(v, g, in, prev, &tiles, &sites);
   }
   RedScratch none{nullptr, nullptr};
-  HDCR_TRY(x2_launch_variant<X2_CHEB>(v, g, tiles, diag, fmf, U, in, prev, nrhs, none, nullptr, X2Cheb{cur, a, b},
-                                      st));
+  HDCR_TRY(x2_launch_variant<X2_CHEB>(v, g, tiles, diag, fmf, U, in, prev, nrhs, none, nullptr,
+                                      X2Cheb{cur, a, b, acc, ck}, st));
   HDCR_LAUNCH_CHECK();
   return HDCR_OK;
 }

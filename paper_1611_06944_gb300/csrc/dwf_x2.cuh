@@ -193,10 +193,13 @@ __device__ __forceinline__ void local_x2(const float4 (&q)[12], const cpx<float>
 
 constexpr int X2_STORE = 0, X2_DOT = 1, X2_CHEB = 2;  // epilogues of the kernels
 
-// Chebyshev step of the epilogue X2_CHEB: out <- 2 (a H in + b cur) - out
+// Chebyshev step of the epilogue X2_CHEB: out <- nx = 2 (a H in + b cur) - out,
+// and, when acc is set, acc += ck nx (the smoother's running sum)
 struct X2Cheb {
   const cpx<float>* cur;
   float a, b;
+  cpx<float>* acc = nullptr;
+  float ck = 0.f;
 };
 
 // Writes the pair to its output sites: out(Ls-1-s) = gamma5 acc(s), i.e. the pair
@@ -204,11 +207,11 @@ struct X2Cheb {
 // out, in and ch.cur (component stride ls).  X2_DOT returns Re <in, H in> of the
 // two output sites (products summed in FP32 within each spin half, where the
 // terms share the sign of Gamma5, the halves combined in FP64); X2_CHEB writes
-// 2 (a H in + b cur) - prev over prev = out.
+// 2 (a H in + b cur) - prev over prev = out and adds ck times it to acc when set.
 template <int EPI>
 __device__ __forceinline__ double store_x2(const cx2 (&up)[2][3], const cx2 (&lo)[2][3], cpx<float>* o,
                                            const cpx<float>* i, const cpx<float>* cur, float ca, float cb,
-                                           int ls) {
+                                           int ls, cpx<float>* acc = nullptr, float ck = 0.f) {
   float d[2] = {0.f, 0.f};
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
@@ -218,6 +221,11 @@ __device__ __forceinline__ double store_x2(const cx2 (&up)[2][3], const cx2 (&lo
       const float4 cv = ld4(cur + c * ls), pv = ld4(o + c * ls);
       r = make_float4(2.f * fmaf(ca, r.x, cb * cv.x) - pv.x, 2.f * fmaf(ca, r.y, cb * cv.y) - pv.y,
                       2.f * fmaf(ca, r.z, cb * cv.z) - pv.z, 2.f * fmaf(ca, r.w, cb * cv.w) - pv.w);
+      if (acc) {
+        const float4 av = ld4(acc + c * ls);
+        *reinterpret_cast<float4*>(acc + c * ls) =
+            make_float4(fmaf(ck, r.x, av.x), fmaf(ck, r.y, av.y), fmaf(ck, r.z, av.z), fmaf(ck, r.w, av.w));
+      }
     }
     *reinterpret_cast<float4*>(o + c * ls) = r;
     if (EPI == X2_DOT) {

@@ -23,12 +23,12 @@ def hd():
     return hd
 
 
-def _setup(hd, L, Ls, block, nvec, mf, tdt, seed=1000):
+def _setup(hd, L, Ls, block, nvec, mf, tdt, seed=1000, order=100, lam_cut=0.3):
     lat = hd.Lattice(L, Ls)
     Uh = synth.gauge_field(L, 0.3, seed)
     U = dev(links(Uh))
     noise = dev(planes(synth.gaussian_fermion(L, Ls, seed + 2001, count=nvec // 2)))
-    sub = hd.build_subspace(lat, U, noise, M5, mf, block, kind="chebyshev", order=100, lam_cut=0.3,
+    sub = hd.build_subspace(lat, U, noise, M5, mf, block, kind="chebyshev", order=order, lam_cut=lam_cut,
                             store_dtype=tdt)
     co = hd.build_coarse_op(sub, U, M5, mf, op_dtype=tdt)
     return lat, Uh, U, sub, co
@@ -73,9 +73,11 @@ def test_multi_point_sources_match_oracle(hd, inner):
 @pytest.mark.parametrize("cycle", ["symmetric", "post"])
 def test_multi_graph_replay_bitwise_equals_eager(hd, cycle):
     """The captured V-cycle replays the eager launch sequence: same iterates, same bits.
-    A second solve on the same handle reuses the captured graph (both cycles)."""
-    L, Ls, block, nvec, mf = (4, 4, 2, 4), 8, (2, 2, 1, 2), 8, 0.05
-    lat, Uh, U, sub, co = _setup(hd, L, Ls, block, nvec, mf, torch.complex64, seed=1010)
+    A second solve on the same handle reuses the captured graph (both cycles).  The basis
+    (24 vectors, filter order 200) is good enough for both cycles to converge in tens of
+    iterations; with 8 vectors of order 100 the post-smoothing cycle takes thousands."""
+    L, Ls, block, nvec, mf = (4, 4, 2, 4), 8, (2, 2, 1, 2), 24, 0.05
+    lat, Uh, U, sub, co = _setup(hd, L, Ls, block, nvec, mf, torch.complex64, seed=1010, order=200, lam_cut=0.5)
     Bd = dev(planes(synth.gaussian_fermion(L, Ls, 2010, count=5)))
     kw = dict(tol=1e-10, inner_dtype=torch.complex64, restart=8, max_outer=2000, cycle=cycle)
     Xe, se = hd.hdcr_solve_multi(co, U, Bd, graph=False, **kw)
