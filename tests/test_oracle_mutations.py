@@ -375,3 +375,79 @@ def test_cf_without_gamma5_on_the_kernel_is_caught(monkeypatch):
     from oracle import overlap as ov
     monkeypatch.setattr(ov, "apply_HW", lambda U, psi, M5, bc_t=1: dwf.wilson(U, psi, M5, bc_t))
     assert _cf_printed_error() > 1e-3
+
+
+# ------------------------------------- two-level pieces on the continued fraction, cycle shapes
+def _cf_galerkin_error():
+    """max over two random coarse vectors of |A c - P^dag H_cf P c| / |P^dag H_cf P c| on a
+    3^4 coarse lattice (the pin of test_oracle_overlap_coarse)."""
+    from oracle import overlap as ov
+    L, N, block, nvec, beta, R = (6, 6, 6, 6), 3, (2, 2, 2, 2), 4, [1.2, 0.7], 0.3
+    g = mg.Geometry(L, N, block)
+    U = synth.gauge_field(L, 0.5, 710)
+    sub = mg.basis_from_vectors(g, synth.gaussian_fermion(L, N, 711, count=nvec))
+    A = ov.cf_coarse_op(U, sub, 1.8, beta, R)
+    rng = synth.rng(712)
+    err = 0.0
+    for _ in range(2):
+        c = rng.standard_normal((g.Vc, nvec)) + 1j * rng.standard_normal((g.Vc, nvec))
+        want = mg.restrict(sub, ov.apply_cf(U, mg.prolong(sub, c), 1.8, beta, R))
+        err = max(err, relerr(mg.coarse_apply(A, g, c), want))
+    return err
+
+
+def test_unmutated_cf_coarse_oracle_passes():
+    assert _cf_galerkin_error() < 1e-13
+
+
+def test_cf_hop_without_component_factor_is_caught(monkeypatch):
+    """The hop part of H_cf without the component's factor (-1)^i / beta_0 puts the wrong
+    hops into the legs and leaves their difference in the self leg."""
+    from oracle import overlap as ov
+
+    def bad(U, psi, mu, sign, beta, bc_t=1):
+        return dwf.spin_mul(dwf.GAMMA5, -0.5 * dwf.hop(U, psi, mu, sign, bc_t))
+
+    monkeypatch.setattr(ov, "apply_cf_hop", bad)
+    assert _cf_galerkin_error() > 1e-3
+
+
+def test_cf_leg_with_the_wrong_crossing_mask_is_caught(monkeypatch):
+    """The face of the opposite side taken as the block crossing of a hop."""
+    orig = mg.crossing_mask
+    monkeypatch.setattr(mg, "crossing_mask", lambda g, mu, sign: orig(g, mu, -sign))
+    assert _cf_galerkin_error() > 1e-3
+
+
+def _post_cycle_error(cycle="post"):
+    """|v - B H v - (1 - S H)(1 - Q H) v| / |.| for one random v with a linear S and exact Q."""
+    from test_oracle_multigrid import _tiny_two_level, M5 as M5m, MF as MFm
+    g, U, sub, A, Hd, P, Q, _ = _tiny_two_level()
+    N = Hd.shape[0]
+    Sm = 0.05 * Hd + 0.01 * np.eye(N)
+    S = lambda v: (Sm @ v.ravel()).reshape(v.shape)
+    Ad = mg.coarse_dense(A, g)
+    Qc = lambda c: np.linalg.solve(Ad, c.ravel()).reshape(c.shape)
+    p = mg.HDCRParams(M5=M5m, mf=MFm)
+    v = synth.rng(131).standard_normal(N) + 1j * synth.rng(132).standard_normal(N)
+    got = v - mg.vcycle(U, sub, A, (Hd @ v).reshape(g.fine_shape()), p, S=S, Qc=Qc, cycle=cycle).ravel()
+    want = (np.eye(N) - Sm @ Hd) @ ((np.eye(N) - Q @ Hd) @ v)
+    return relerr(got, want)
+
+
+def test_unmutated_post_cycle_passes():
+    assert _post_cycle_error() < 1e-11
+
+
+def test_post_cycle_smoothing_r_instead_of_the_residual_is_caught(monkeypatch):
+    """Smoothing the input r instead of r - H z1 (the residual after the coarse step)."""
+    orig = mg.vcycle
+
+    def bad(U, sub, A, r, p, S=None, Qc=None, cycle="symmetric"):
+        if cycle != "post":
+            return orig(U, sub, A, r, p, S=S, Qc=Qc, cycle=cycle)
+        z1 = mg.prolong(sub, Qc(mg.restrict(sub, r)))
+        return z1 + S(r)
+
+    monkeypatch.setattr(mg, "vcycle", bad)
+    assert _post_cycle_error() > 1e-3
