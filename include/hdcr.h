@@ -119,9 +119,11 @@ unsigned long long hdcr_launch_count(void);
 /* Stencil timer: hdcr_stencil_timer(1) resets and starts recording CUDA
  * events around every application of H (on the launching stream, at most
  * 16384 launches); hdcr_stencil_timer(0) stops.  hdcr_stencil_timer_read adds
- * up the recorded launches of one precision (HDCR_C128, HDCR_C64 or HDCR_H16): total
- * device milliseconds, number of launches and 5d sites processed.  It waits
- * for the recorded events. */
+ * up the recorded launches of one precision (HDCR_C128, HDCR_C64 or HDCR_H16;
+ * HDCR_TIMER_C128_CHEB: the FP64 applications that carry a fused Chebyshev
+ * smoother step, which HDCR_C128 leaves out): total device milliseconds, number
+ * of launches and 5d sites processed.  It waits for the recorded events. */
+#define HDCR_TIMER_C128_CHEB 100
 int hdcr_stencil_timer(int enable);
 int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* launches, long long* sites);
 /* Every application of H of one precision since the timer was started,

@@ -47,17 +47,20 @@ def stencil_timer(enable: bool) -> None:
     _check(_L.hdcr_stencil_timer(1 if enable else 0), "stencil_timer")
 
 
-def stencil_timer_read(dtype: torch.dtype) -> dict:
+def stencil_timer_read(dtype, fused_cheb: bool = False) -> dict:
     """Stencil launches of one precision since the timer started: device ms, launches and
-    5d sites of those that carry events, and all launches and sites (``all_*``)."""
+    5d sites of those that carry events, and all launches and sites (``all_*``).
+    fused_cheb=True (complex128): the FP64 applications carrying a fused Chebyshev
+    smoother step, which the plain complex128 count leaves out."""
+    code = _lib.HDCR_TIMER_C128_CHEB if fused_cheb else _dt(dtype)
     ms = ctypes.c_double()
     nl = ctypes.c_longlong()
     ns = ctypes.c_longlong()
-    _check(_L.hdcr_stencil_timer_read(_dt(dtype), ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ns)),
+    _check(_L.hdcr_stencil_timer_read(code, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ns)),
            "stencil_timer_read")
     al = ctypes.c_longlong()
     asites = ctypes.c_longlong()
-    _check(_L.hdcr_stencil_timer_count(_dt(dtype), ctypes.byref(al), ctypes.byref(asites)), "stencil_timer_count")
+    _check(_L.hdcr_stencil_timer_count(code, ctypes.byref(al), ctypes.byref(asites)), "stencil_timer_count")
     return {"ms": ms.value, "launches": nl.value, "sites": ns.value, "all_launches": al.value,
             "all_sites": asites.value}
 

@@ -18,6 +18,7 @@ HDCR_C128 = 0
 HDCR_C64 = 1
 HDCR_C64_FAST = 2
 HDCR_C128_TC = 4
+HDCR_TIMER_C128_CHEB = 100
 HDCR_H16 = 3
 
 STATUS_NAMES = {

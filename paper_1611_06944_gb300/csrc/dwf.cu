@@ -41,9 +41,10 @@ __global__ void __launch_bounds__(256, 2) g5dwf_kernel(Geom g, R diag, R mf, con
 // One step of the Chebyshev smoother's recurrence fused into the FP64 operator:
 // with h = H in at every element, prev <- nx = 2 (a h + b cur) - prev and
 // acc += ck nx (the same arithmetic, in the same order, as the separate step
-// kernel after a plain application, so the same bits).  The operator is
-// ALU-bound, so the extra field traffic of the epilogue costs little; the
-// separate pass over four fields does not happen.
+// kernel after a plain application, so the same bits).  The separate pass over
+// four fields does not happen; the epilogue's own loads are not hidden behind
+// the FP64 arithmetic, so a launch takes about 0.2 ms longer than a plain one
+// (16^4 x 16), a small net gain.
 template <int LS>
 __global__ void __launch_bounds__(256, 2) g5dwf_cheb_kernel(Geom g, double diag, double mf,
                                                             const cpx<double>* __restrict__ U,
@@ -138,11 +139,11 @@ struct StencilTimer {
   std::mutex mu;
   bool enabled = false;
   std::vector<cudaEvent_t> ev;  // 2 per launch
-  std::vector<int> kind;        // 0 = FP64, 1 = FP32, 2 = FP16 storage
+  std::vector<int> kind;        // 0 = FP64, 1 = FP32, 2 = FP16 storage, 3 = FP64 with a smoother step
   std::vector<long long> sites;
   int used = 0;
-  long long all_launches[3] = {0, 0, 0};  // every launch while enabled, timed or not
-  long long all_sites[3] = {0, 0, 0};
+  long long all_launches[4] = {0, 0, 0, 0};  // every launch while enabled, timed or not
+  long long all_sites[4] = {0, 0, 0, 0};
 };
 StencilTimer g_timer;
 }  // namespace
@@ -210,7 +211,7 @@ int launch_g5dwf_cheb(const Geom& g, double M5, double mf, const cpx<double>* U,
                       cudaStream_t st) {
   const int threads = 256;
   int slot;
-  stencil_timer_begin(0, g.V5, st, &slot);
+  stencil_timer_begin(3, g.V5, st, &slot);
   HDCR_DISPATCH_LS(g.Ls, (g5dwf_cheb_kernel<LSC><<<num_blocks(g.V5, threads), threads, 0, st>>>(
                              g, 5.0 - M5, mf, U, in, cur, prev, acc, a, b, ck)));
   stencil_timer_end(slot, st);
@@ -380,25 +381,29 @@ extern "C" int hdcr_stencil_timer(int enable) {
   return HDCR_OK;
 }
 
+static int timer_kind(int dtype) {
+  return dtype == HDCR_C128 ? 0 : dtype == HDCR_C64 ? 1 : dtype == HDCR_H16 ? 2 : dtype == HDCR_TIMER_C128_CHEB ? 3 : -1;
+}
+
 extern "C" int hdcr_stencil_timer_count(int dtype, long long* launches, long long* sites) {
-  if (!launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64 && dtype != HDCR_H16)) {
+  const int k = timer_kind(dtype);
+  if (!launches || !sites || k < 0) {
     set_error("hdcr_stencil_timer_count: bad arguments");
     return HDCR_ERR_BAD_ARG;
   }
   std::lock_guard<std::mutex> lock(g_timer.mu);
-  const int k = dtype == HDCR_C128 ? 0 : dtype == HDCR_C64 ? 1 : 2;
   *launches = g_timer.all_launches[k];
   *sites = g_timer.all_sites[k];
   return HDCR_OK;
 }
 
 extern "C" int hdcr_stencil_timer_read(int dtype, double* total_ms, long long* launches, long long* sites) {
-  if (!total_ms || !launches || !sites || (dtype != HDCR_C128 && dtype != HDCR_C64 && dtype != HDCR_H16)) {
+  const int want = timer_kind(dtype);
+  if (!total_ms || !launches || !sites || want < 0) {
     set_error("hdcr_stencil_timer_read: bad arguments");
     return HDCR_ERR_BAD_ARG;
   }
   std::lock_guard<std::mutex> lock(g_timer.mu);
-  const int want = dtype == HDCR_C128 ? 0 : dtype == HDCR_C64 ? 1 : 2;
   double ms = 0.0;
   long long nl = 0, ns = 0;
   for (int i = 0; i < g_timer.used; ++i) {
