@@ -82,7 +82,7 @@ def bytes_per_site(real_bytes: int, Ls: int) -> float:
 
 # DRAM traffic of one FP64 / FP32 / FP16-storage stencil launch at 16^4 x 16 from ncu, with the hash of
 # the stencil sources it was measured on (reported as null once the sources change)
-NCU_TRAFFIC = {"f64": 451.50e6, "f32": 202.60e6, "h16": 106.01e6, "src_hash": "12ad5967315e61c8"}
+NCU_TRAFFIC = {"f64": 449.67e6, "f32": 202.18e6, "h16": 106.18e6, "src_hash": "272691dffa098572"}
 
 
 def stencil_src_hash() -> str:
