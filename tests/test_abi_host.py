@@ -134,3 +134,54 @@ def test_new_entry_points_reject_bad_arguments_on_host(lib):
     assert lib.hdcr_solve_multi(None, fake, fake, fake2, 2, ctypes.byref(prm), 1, ctypes.byref(st), None) == -1
     h = ctypes.c_void_p()
     assert lib.hdcr_build_coarse_op(None, ctypes.byref(p), fake, _lib.HDCR_C64_FAST, None, ctypes.byref(h)) == -1
+
+
+def test_overlap_and_level2_entry_points_reject_bad_arguments_on_host(lib):
+    """Argument checks of the continued-fraction calls (component count against Ls,
+    positive beta, filter parameters), the 4d chirality split, the third level and the
+    solve's cycle and timer codes, all before any CUDA call."""
+    from paper_1611_06944_gb300 import _lib
+    fake = ctypes.c_void_p(0x1000)
+    fake2 = ctypes.c_void_p(0x2000)
+    fake3 = ctypes.c_void_p(0x3000)
+    st = _lib.hdcr_solve_stats()
+    g5 = _geom(Ls=5)
+    cf = _lib.hdcr_cf_params()
+    cf.ncomp = 5
+    for i, b in enumerate((1.3, 0.9, 1.7, 0.6)):
+        cf.beta[i] = b
+    cf.R = 0.3
+    g4 = _geom(Ls=4)
+    assert lib.hdcr_apply_cf_overlap(ctypes.byref(g4), 1.8, ctypes.byref(cf), fake, fake2, fake3, 0, 1, None) == -1
+    cf.beta[2] = -1.0
+    assert lib.hdcr_apply_cf_overlap(ctypes.byref(g5), 1.8, ctypes.byref(cf), fake, fake2, fake3, 0, 1, None) == -1
+    cf.beta[2] = 1.7
+    assert lib.hdcr_apply_cf_overlap(ctypes.byref(g5), 1.8, ctypes.byref(cf), fake, fake2, fake2, 0, 1, None) == -1
+    assert lib.hdcr_cf_cr_solve(ctypes.byref(g5), 1.8, ctypes.byref(cf), fake, fake2, fake3, 0, 0.0, 10,
+                                ctypes.byref(st), None) == -1
+    sp = _lib.hdcr_subspace_params()
+    sp.kind = _lib.HDCR_SUBSPACE_CHEBYSHEV
+    sp.order = 10
+    sp.lam_cut, sp.lam_max = 0.5, 0.4                   # lam_max must exceed lam_cut
+    assert lib.hdcr_cf_filter(ctypes.byref(g5), 1.8, ctypes.byref(cf), fake, fake2, 0, ctypes.byref(sp), None) == -1
+    sp.kind = 7
+    assert lib.hdcr_cf_filter(ctypes.byref(g5), 1.8, ctypes.byref(cf), fake, fake2, 0, ctypes.byref(sp), None) == -1
+    h = ctypes.c_void_p()
+    assert lib.hdcr_cf_build_coarse_op(None, 1.8, ctypes.byref(cf), fake, None, ctypes.byref(h)) == -1
+    # the chirality split: distinct outputs, a known dtype, at least one field
+    assert lib.hdcr_gamma5_split(ctypes.byref(g5), fake, fake2, fake2, 0, 1, None) == -1
+    assert lib.hdcr_gamma5_split(ctypes.byref(g5), fake, fake2, fake3, 3, 1, None) == -1
+    assert lib.hdcr_gamma5_split(ctypes.byref(g5), fake, fake2, fake3, 0, 0, None) == -1
+    # the third level and the solve need a coarse handle
+    l2 = _lib.hdcr_level2_params()
+    assert lib.hdcr_coarse_build_level2(None, ctypes.byref(l2), fake, None) == -1
+    it = ctypes.c_int()
+    assert lib.hdcr_coarse_solve_level2(None, fake, fake2, 1e-6, 10, ctypes.byref(it), None) == -1
+    prm = _lib.hdcr_solve_params()
+    prm.cycle = 5
+    assert lib.hdcr_solve(None, fake, fake2, fake3, ctypes.byref(prm), ctypes.byref(st), None) == -1
+    # the stencil timer knows FP64, FP32, FP16 storage and the fused FP64 smoother step only
+    ms, nl, ns = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+    assert lib.hdcr_stencil_timer_read(_lib.HDCR_TIMER_C128_CHEB, ctypes.byref(ms), ctypes.byref(nl),
+                                       ctypes.byref(ns)) == 0
+    assert lib.hdcr_stencil_timer_read(7, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ns)) == -1

@@ -152,8 +152,10 @@ def test_subspace_errors(hd):
     assert e.value.status == -5
 
 
-@pytest.mark.parametrize("nvec", [24, 66])
-def test_block_orthonormalisation_matches_oracle(hd, nvec):
+@pytest.mark.parametrize("nvec,L,Ls,block", [(24, (4, 4, 4, 4), 4, (2, 2, 2, 2)),
+                                             (66, (4, 4, 4, 4), 4, (2, 2, 2, 2)),
+                                             (10, (6, 4, 4, 2), 5, (3, 2, 2, 1))])   # ragged block, odd Ls
+def test_block_orthonormalisation_matches_oracle(hd, nvec, L, Ls, block):
     """subspace_from_vectors: the GPU's block orthonormalisation (two rounds of
     Cholesky QR per block; modified Gram-Schmidt for blocks whose Cholesky pivot
     collapses and for nvec > 64) against the oracle's modified Gram-Schmidt applied
@@ -162,13 +164,13 @@ def test_block_orthonormalisation_matches_oracle(hd, nvec):
     vectors 0..2 plus 1e-3 noise (condition ~1e3: Cholesky QR).  The QR factor with a
     positive real diagonal is unique, so the two agree to the rounding amplified by
     the condition number."""
-    L, Ls, block = (4, 4, 4, 4), 4, (2, 2, 2, 2)
     g = mg.Geometry(L, Ls, block)
     rng = synth.rng(3300 + nvec)
     shape = (nvec,) + synth.gaussian_fermion(L, Ls, 1).shape
     v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
-    b0 = (slice(0, 2), slice(0, 2), slice(0, 2), slice(0, 2))      # (t, z, y, x) of block 0
-    b1 = (slice(0, 2), slice(0, 2), slice(0, 2), slice(2, 4))      # block 1: x in [2, 4)
+    bx, by, bz, bt = block
+    b0 = (slice(0, bt), slice(0, bz), slice(0, by), slice(0, bx))            # (t, z, y, x) of block 0
+    b1 = (slice(0, bt), slice(0, bz), slice(0, by), slice(bx, 2 * bx))       # block 1: the next in x
     noise = rng.standard_normal(v[0][b0].shape) + 1j * rng.standard_normal(v[0][b0].shape)
     v[1][b0] = v[0][b0] + 1e-6 * noise
     v[3][b1] = 0.5 * v[0][b1] - 0.3j * v[1][b1] + 0.7 * v[2][b1] + 1e-3 * noise
