@@ -18,9 +18,9 @@
 //
 // One CTA per block and share of K (a few CTAs split a long K; a second kernel
 // adds their partial results in a fixed order).  K streams through shared
-// memory in chunks of 32; each thread loads its share of the next two chunks
-// into registers while
-// the current one is split, stored in the canonical no-swizzle K-major layout
+// memory in chunks of 32; each thread keeps its share of the next three chunks
+// in flight in registers while the current one is split, stored in the
+// canonical no-swizzle K-major layout
 // (8-row x 16-byte core matrices) and handed to the MMA issued by thread 0.
 // Two shared-memory stages alternate; an mbarrier per stage, signalled by
 // tcgen05.commit, says when it may be refilled, so each chunk needs one CTA
@@ -130,7 +130,7 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // one 16-byte row of a core matrix each.  t -> v8 = t & 7, q = (t >> 3) & 7,
 // v = 8 (t >> 6) + v8: the eight threads of a quarter warp write eight rows of
 // one core matrix (no bank conflicts) and read eight 32-byte sectors.
-// The loads run two chunks ahead in registers.
+// The loads run three chunks ahead in registers.
 template <int TPT, int M, int NPASS, int TCP_NST = tcp_nst(M, NPASS)>
 __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kernel(TcSrc S,
                                                                                   cpx<float>* __restrict__ A,
@@ -285,11 +285,12 @@ __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kern
   constexpr int OPS = NPASS == 3 ? 2 : 1;  // hi (+ lo) tiles per operand
   long long flushed = 0;  // segments added into C so far
   float4 xa[TPT][2], ya[TPT][2], xb[TPT][2], yb[TPT][2], xc[TPT][2], yc[TPT][2];
-  if (nchunks > 0) load(xa, ya);
-  if (nchunks > 1) load(xb, yb);
   long long issued = -1;  // last chunk whose MMAs were committed
-  for (long long ch = 0; ch < nchunks; ++ch) {
-    if (ch + 2 < nchunks) load(xc, yc);
+  // One chunk: refill its stage from the registers (xv, yv), reload them with chunk
+  // ch + 3, hand the stage to the MMA.  The three register sets keep their roles
+  // (the loop below is unrolled three times), so no register copy waits on a
+  // load in flight.  Returns false once a wait has timed out.
+  auto step = [&](long long ch, float4 (&xv)[TPT][2], float4 (&yv)[TPT][2]) -> bool {
     const int s = (int)(ch % TCP_NST);
     unsigned char* st = dsm + s * stage_bytes;
     // every thread waits itself for the MMAs that last read this stage (chunk ch - NST)
@@ -308,16 +309,17 @@ __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kern
     for (int i = 0; i < TPT; ++i) {
       const int v = v0 + 32 * i;
       if (v < nvec) {
-        const float4 x0 = xa[i][0], x1 = xa[i][1], y0 = ya[i][0], y1 = ya[i][1];
+        const float4 x0 = xv[i][0], x1 = xv[i][1], y0 = yv[i][0], y1 = yv[i][1];
         put(st, st + a_bytes, v, x0.x, x0.z, x1.x, x1.z);
         put(st, st + a_bytes, nvec + v, x0.y, x0.w, x1.y, x1.w);
         put(qb, qb + qbytes, v, y0.x, y0.z, y1.x, y1.z);
         put(qb, qb + qbytes, nvec + v, y0.y, y0.w, y1.y, y1.w);
       }
     }
+    if (ch + 3 < nchunks) load(xv, yv);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (abort_flag) break;
+    if (abort_flag) return false;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ahi = smem0 + s * stage_bytes, alo = ahi + a_bytes;
@@ -338,15 +340,17 @@ __global__ void __launch_bounds__(TCP_THREADS, TPT == 1 ? 2 : 1) tc_project_kern
                    : "memory");
     }
     issued = ch;
-#pragma unroll
-    for (int i = 0; i < TPT; ++i)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        xa[i][h] = xb[i][h];
-        ya[i][h] = yb[i][h];
-        xb[i][h] = xc[i][h];
-        yb[i][h] = yc[i][h];
-      }
+    return true;
+  };
+  // chunks 0, 1, 2 in flight before the first step; chunk c is always loaded into
+  // set c % 3
+  if (nchunks > 0) load(xa, ya);
+  if (nchunks > 1) load(xb, yb);
+  if (nchunks > 2) load(xc, yc);
+  for (long long ch = 0; ch < nchunks; ch += 3) {
+    if (!step(ch, xa, ya)) break;
+    if (ch + 1 >= nchunks || !step(ch + 1, xb, yb)) break;
+    if (ch + 2 >= nchunks || !step(ch + 2, xc, yc)) break;
   }
   // wait for the last committed chunk (its commit covers every earlier MMA)
   bool done = issued >= 0;
