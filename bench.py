@@ -60,7 +60,10 @@ SEED_GAUGE, SEED_SRC, SEED_NOISE = 1001, 2001, 3001
 # solve (18 outer iterations, 814 fine applications, for four noise seeds), 175
 # needs 20 and 150 stalls; cut 0.3 (0.25 needs 24 iterations, 0.5 at order 200 stalls)
 FILTER = dict(kind="chebyshev", order=200, lam_cut=0.3, lam_max=8.0)
-SOLVE = dict(tol=1e-10, restart=8, smoother="chebyshev", smoother_order=10, cheb_lo=1.0, cheb_hi=64.0,
+# FGCR restart 24: longer than the ~17 outer iterations the solve takes, so the
+# search space is never thrown away (restart 8: 18 iterations, 814 applications;
+# 24 or 32: 17, 767)
+SOLVE = dict(tol=1e-10, restart=24, smoother="chebyshev", smoother_order=10, cheb_lo=1.0, cheb_hi=64.0,
              coarse_solver="dense", max_outer=200)
 # Algorithmic floating-point operations per 5d site of one application of H (real
 # adds and multiplies, an FMA counted as 2): the Wilson hopping term in its
