@@ -403,8 +403,11 @@ __global__ void tc_reduce_kernel(const cpx<float>* __restrict__ part, int nsplit
 
 int tc_project_splits(const TcSrc& S) {
   // enough CTAs for about four per SM, at least 16 chunks each
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 152;
   const long long nch = (S.K + TCP_KC - 1) / TCP_KC;
-  long long sp = (4 * 152 + S.bg.Vc - 1) / S.bg.Vc;
+  long long sp = (4LL * sms + S.bg.Vc - 1) / S.bg.Vc;
   if (sp > nch / 16) sp = nch / 16;
   if (sp > TC_MAX_SPLIT) sp = TC_MAX_SPLIT;
   return sp < 1 ? 1 : (int)sp;
@@ -418,34 +421,20 @@ int launch_tc_project(const TcSrc& S, cpx<float>* A, int nvec, int leg, cpx<floa
   }
   const int m = tcp_m(nvec), np = tcp_np(nvec);
   const int smem = tcp_smem_bytes(m, np, npass);
-  static int configured = -1;
-  int dev = 0;
-  HDCR_CUDA_TRY(cudaGetDevice(&dev));
-  if (configured != dev) {
-    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<1, 64, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tcp_smem_bytes(64, tcp_np(32), 3)));
-    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<2, 128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tcp_smem_bytes(128, tcp_np(64), 3)));
-    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<1, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tcp_smem_bytes(64, tcp_np(32), 1)));
-    HDCR_CUDA_TRY(cudaFuncSetAttribute(tc_project_kernel<2, 128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tcp_smem_bytes(128, tcp_np(64), 1)));
-    configured = dev;
-  }
+  // the kernel for this size, allowed the dynamic shared memory of its largest nvec
+  // (set on every call: the setting is per device, the value the same for every
+  // caller, and the call is cheap beside the launch)
+  void (*kern)(TcSrc, cpx<float>*, int, int, cpx<float>*, int*);
+  if (npass == 3)
+    kern = nvec <= 32 ? tc_project_kernel<1, 64, 3> : tc_project_kernel<2, 128, 3>;
+  else
+    kern = nvec <= 32 ? tc_project_kernel<1, 64, 1> : tc_project_kernel<2, 128, 1>;
+  const int smem_max = nvec <= 32 ? tcp_smem_bytes(64, tcp_np(32), npass) : tcp_smem_bytes(128, tcp_np(64), npass);
+  HDCR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   const int sp = part ? tc_project_splits(S) : 1;
   const dim3 grid(S.bg.Vc, sp);
   cpx<float>* pp = sp > 1 ? part : nullptr;
-  if (npass == 3) {
-    if (nvec <= 32)
-      tc_project_kernel<1, 64, 3><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
-    else
-      tc_project_kernel<2, 128, 3><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
-  } else {
-    if (nvec <= 32)
-      tc_project_kernel<1, 64, 1><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
-    else
-      tc_project_kernel<2, 128, 1><<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
-  }
+  kern<<<grid, TCP_THREADS, smem, st>>>(S, A, nvec, leg, pp, err);
   count_launch();
   HDCR_LAUNCH_CHECK();
   if (sp > 1) {
