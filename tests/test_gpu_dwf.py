@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-# (L, Ls, bc_t, eps): config-1 size, a ragged odd lattice spanning several
+# (L, Ls, bc_t, eps): the tiny 4^4 x 8 workload, a ragged odd lattice spanning several
 # thread blocks with a partial last block, and two multi-block cases
 CASES = [
     ((4, 4, 4, 4), 8, 1, 0.3),

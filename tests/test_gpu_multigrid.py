@@ -30,7 +30,7 @@ def _oracle_sub(L, Ls, block, nvec, eps, mf, seed, iters=10, bc=1):
     return g, U, noise, sub
 
 
-# config-1 size (2^4 coarse, legs alias) and a ragged block shape
+# the tiny 4^4 x 8 workload (2^4 coarse, legs alias) and a ragged block shape
 SUBSPACE_CASES = [
     ((4, 4, 4, 4), 8, (2, 2, 2, 2), 8, 0.3, 0.01, 1),
     ((6, 4, 2, 4), 5, (3, 2, 1, 2), 4, 0.5, 0.05, -1),
@@ -307,7 +307,7 @@ def test_hdcr_solve_reports_cap(hd):
 
 
 @pytest.mark.parametrize("L,Ls,block,nvec,lam_cut,seeds", [
-    ((4, 4, 4, 4), 8, (2, 2, 2, 2), 24, 0.5, (1000, 2000, 3000)),   # config 1's lattice, eps = 0.3
+    ((4, 4, 4, 4), 8, (2, 2, 2, 2), 24, 0.5, (1000, 2000, 3000)),   # the tiny 4^4 x 8 workload, eps = 0.3
     ((8, 8, 8, 8), 8, (4, 4, 4, 4), 24, 0.5, (1100, 2100, 3100)),   # a mid-size lattice, eps = 0.5
 ])
 def test_hdcr_needs_fewer_fine_matvecs_than_cr(hd, L, Ls, block, nvec, lam_cut, seeds):
