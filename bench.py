@@ -465,8 +465,8 @@ def run_e2e(hd, lat, Uh, bh, nh, stream) -> dict:
             "true_resid": st["true_resid"]}
 
 
-# applications of H in one solve of the step as measured on GB300 (18 outer iterations)
-SOLVE_MATVECS = 814
+# applications of H in one solve of the step as measured on GB300 (17 outer iterations)
+SOLVE_MATVECS = 767
 
 
 def step_matvecs(solve_mv: int) -> int:
