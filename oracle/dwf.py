@@ -106,7 +106,7 @@ def shift_links(Umu: np.ndarray, mu: int, sign: int) -> np.ndarray:
 
 # ------------------------------------------------------------- the operator
 def hop(U: np.ndarray, psi: np.ndarray, mu: int, sign: int, bc_t: int) -> np.ndarray:
-    """One Wilson hop of D_W (without the -1/2):
+    """One Wilson hop of D_W (Section 3's kernel, as read in the header; without the -1/2):
 
     sign=+1: (1 - gamma_mu) U_mu(x) psi(x + mu)
     sign=-1: (1 + gamma_mu) U_mu(x - mu)^dag psi(x - mu)
@@ -119,7 +119,8 @@ def hop(U: np.ndarray, psi: np.ndarray, mu: int, sign: int, bc_t: int) -> np.nda
 
 
 def wilson(U, psi, M5: float, bc_t: int = 1) -> np.ndarray:
-    """4d Wilson operator with mass -M5, applied independently at each s."""
+    """4d Wilson operator with mass -M5 (the kernel of Section 3's D_dwf, read as in the
+    header), applied independently at each s."""
     out = (4.0 - M5) * psi
     for mu in range(4):
         out = out - 0.5 * (hop(U, psi, mu, +1, bc_t) + hop(U, psi, mu, -1, bc_t))
@@ -127,7 +128,8 @@ def wilson(U, psi, M5: float, bc_t: int = 1) -> np.ndarray:
 
 
 def d5(psi: np.ndarray, mf: float) -> np.ndarray:
-    """Fifth-dimension hop with the mass mf at the walls (no gauge links in s)."""
+    """Fifth-dimension part of Section 3's D_dwf (read as in the header), with the mass mf
+    at the walls (no gauge links in s)."""
     up = np.roll(psi, -1, axis=-3)           # psi(s + 1)
     up[..., -1, :, :] *= -mf                 # psi(Ls) = -mf psi(0)
     dn = np.roll(psi, +1, axis=-3)           # psi(s - 1)
@@ -136,7 +138,7 @@ def d5(psi: np.ndarray, mf: float) -> np.ndarray:
 
 
 def ddwf(U, psi, M5: float, mf: float, bc_t: int = 1) -> np.ndarray:
-    """D_dwf = D_W + D_5."""
+    """D_dwf = D_W + D_5 (Section 3, the Shamir operator as read in the header)."""
     return wilson(U, psi, M5, bc_t) + d5(psi, mf)
 
 
@@ -149,12 +151,13 @@ def ddwf_mobius(U, psi, M5: float, mf: float, b5: float, bc_t: int = 1) -> np.nd
 
 
 def apply_H_mobius(U, psi, M5: float, mf: float, b5: float, bc_t: int = 1) -> np.ndarray:
-    """H = Gamma5 D for the Moebius (c5 = 0) operator."""
+    """H = Gamma5 D for the Moebius (c5 = 0) operator (Section 3 names Moebius with c = 0
+    beside the Shamir operator)."""
     return gamma5_r5(ddwf_mobius(U, psi, M5, mf, b5, bc_t))
 
 
 def gamma5_r5(psi: np.ndarray) -> np.ndarray:
-    """Gamma5 = gamma5 R5: reflect s -> Ls-1-s and multiply by gamma5."""
+    """Gamma5 = gamma5 R5 (Section 3): reflect s -> Ls-1-s and multiply by gamma5."""
     return spin_mul(GAMMA5, psi[..., ::-1, :, :])
 
 
@@ -175,7 +178,7 @@ def apply_D(U, psi, M5, mf, bc_t=1):
 
 
 def apply_H_at(U, psi, sites, M5: float, mf: float, bc_t: int = 1) -> np.ndarray:
-    """(H psi)(x, s) at a few 5d sites only, written out term by term.
+    """(H psi)(x, s) of Section 3 at a few 5d sites only, written out term by term.
 
     ``sites``: iterable of (x, y, z, t, s).  Returns an array (len(sites), 4, 3).
     Used to check full-size lattices where a whole-field apply is too slow.

@@ -26,7 +26,8 @@ from . import dwf
 
 
 def gauge_force(U, x, w, bc_t: int = 1) -> np.ndarray:
-    """F with dL = Re sum tr(dU F); shape (4, Lt, Lz, Ly, Lx, 3, 3), F[mu, ..., p, q] = F_pq."""
+    """F with dL = Re sum tr(dU F), derived in the header from the Section 3 operator (the paper
+    has no gradient); shape (4, Lt, Lz, Ly, Lx, 3, 3), F[mu, ..., p, q] = F_pq."""
     F = np.zeros_like(U)
     for mu in range(4):
         xf = dwf.shift_fermion(x, mu, +1, bc_t)
@@ -40,7 +41,8 @@ def gauge_force(U, x, w, bc_t: int = 1) -> np.ndarray:
 
 
 def solve_gradient(U, x, y, bc_t: int = 1):
-    """Gradients of L = Re(eta^dag x), H x = b, given x and the adjoint solution y (H y = eta).
+    """Gradients of L = Re(eta^dag x), H x = b, given x and the adjoint solution y (H y = eta),
+    as derived in the header (the paper has no gradient).
 
     Returns (grad_U, grad_b) in the torch convention: grad_U = F^dag per link,
     grad_b = y.

@@ -75,12 +75,14 @@ class CoarseGeometry:
 
 
 def gamma5_coarse(nvec: int) -> np.ndarray:
-    """Gamma5c on one coarse site: +1 for the nvec/2 P_+ basis vectors, -1 for the rest."""
+    """Gamma5c on one coarse site (step 2 of the header): +1 for the nvec/2 P_+ basis vectors,
+    -1 for the rest."""
     return np.concatenate([np.ones(nvec // 2), -np.ones(nvec // 2)])
 
 
 def neighbour(c: np.ndarray, g: CoarseGeometry, mu: int, sign: int) -> np.ndarray:
-    """c(a + sign*mu) on the periodic coarse lattice; c is (..., Vc, nvec)."""
+    """c(a + sign*mu) on the periodic coarse lattice (the neighbour a leg of Eq. 4.5 reaches);
+    c is (..., Vc, nvec)."""
     lead = c.shape[:-2]
     cs = c.reshape(lead + g.shape() + (g.nvec,))
     ax = len(lead) + 3 - mu
@@ -88,7 +90,7 @@ def neighbour(c: np.ndarray, g: CoarseGeometry, mu: int, sign: int) -> np.ndarra
 
 
 def apply_leg(A: np.ndarray, g: CoarseGeometry, c: np.ndarray, mu: int, sign: int) -> np.ndarray:
-    """The one leg (mu, sign) of the 9-point coarse stencil: y[a] = A[a, leg] c[a + sign mu]."""
+    """The one leg (mu, sign) of the 9-point coarse stencil of Eq. 4.5: y[a] = A[a, leg] c[a + sign mu]."""
     return np.einsum("ajk,ak->aj", A[:, leg_index(mu, sign)], neighbour(c, g, mu, sign))
 
 
@@ -103,7 +105,8 @@ def apply_A(A: np.ndarray, g: CoarseGeometry, c: np.ndarray) -> np.ndarray:
 
 # ----------------------------------------------------------- level-2 blocks
 def to_blocks(g: CoarseGeometry, c: np.ndarray) -> np.ndarray:
-    """Coarse vector(s) (..., Vc, nvec) -> (..., Vc2, K2)."""
+    """Coarse vector(s) (..., Vc, nvec) -> (..., Vc2, K2): the block restriction of Eq. 4.1
+    on the coarse lattice (step 3 of the header)."""
     lead = c.shape[:-2]
     bx, by, bz, bt = g.block
     X2, Y2, Z2, T2 = g.L2
@@ -125,7 +128,8 @@ def from_blocks(g: CoarseGeometry, b: np.ndarray) -> np.ndarray:
 
 
 def crossing_mask(g: CoarseGeometry, mu: int, sign: int) -> np.ndarray:
-    """(Vc, 1): coarse sites whose neighbour a + sign*mu lies in another level-2 block."""
+    """(Vc, 1): coarse sites whose neighbour a + sign*mu lies in another level-2 block (the
+    hops that make the legs of step 4)."""
     Xc, Yc, Zc, Tc = g.Lc
     coords = np.indices((Tc, Zc, Yc, Xc))
     c = coords[3 - mu]
@@ -134,7 +138,8 @@ def crossing_mask(g: CoarseGeometry, mu: int, sign: int) -> np.ndarray:
 
 
 def block_orthonormalise(Phi: np.ndarray, rank_tol: float = 1e-12) -> np.ndarray:
-    """Modified Gram-Schmidt (twice) inside every level-2 block, order k = 0..n2-1."""
+    """Step 3 (the projector of Eq. 4.3 on the coarse lattice, a reading): modified Gram-Schmidt
+    (twice) inside every level-2 block, order k = 0..n2-1."""
     Phi = Phi.copy()
     n2, Vc2, _ = Phi.shape
     for a in range(Vc2):
@@ -152,7 +157,8 @@ def block_orthonormalise(Phi: np.ndarray, rank_tol: float = 1e-12) -> np.ndarray
 
 
 def chiral_split(vs: np.ndarray, nvec: int) -> np.ndarray:
-    """(h, Vc, nvec) -> (2h, Vc, nvec): [P+ v_0..P+ v_{h-1}, P- v_0..P- v_{h-1}] with
+    """Step 2 (the chiral split of Section 4 with the coarse Gamma5):
+    (h, Vc, nvec) -> (2h, Vc, nvec): [P+ v_0..P+ v_{h-1}, P- v_0..P- v_{h-1}] with
     P+- = (1 +- Gamma5c)/2."""
     g5 = gamma5_coarse(nvec)
     plus = 0.5 * (vs + vs * g5)
@@ -172,17 +178,17 @@ def build_level2(A: np.ndarray, g: CoarseGeometry, noise: np.ndarray, smooth_ite
 
 
 def basis_from_vectors(g: CoarseGeometry, vectors: np.ndarray) -> np.ndarray:
-    """Level-2 basis from given coarse vectors (n2, Vc, nvec), block-orthonormalised."""
+    """Level-2 basis from given coarse vectors (n2, Vc, nvec), block-orthonormalised (step 3)."""
     return block_orthonormalise(to_blocks(g, vectors))
 
 
 def restrict(g: CoarseGeometry, Phi2: np.ndarray, c: np.ndarray) -> np.ndarray:
-    """P2^dag c: c2[B, j] = <phi2_j^B, c>."""
+    """P2^dag c: c2[B, j] = <phi2_j^B, c> (Eq. 4.3 on the coarse lattice, to level-2 coordinates)."""
     return np.einsum("jbk,...bk->...bj", np.conj(Phi2), to_blocks(g, c))
 
 
 def prolong(g: CoarseGeometry, Phi2: np.ndarray, c2: np.ndarray) -> np.ndarray:
-    """P2 c2 = sum_{B, j} c2[B, j] phi2_j^B."""
+    """P2 c2 = sum_{B, j} c2[B, j] phi2_j^B (Eq. 4.3 on the coarse lattice, back to coarse vectors)."""
     return from_blocks(g, np.einsum("jbk,...bj->...bk", Phi2, c2))
 
 
@@ -205,7 +211,8 @@ def level2_op(A: np.ndarray, g: CoarseGeometry, Phi2: np.ndarray) -> np.ndarray:
 
 
 def level2_neighbour(idx: np.ndarray, g: CoarseGeometry, mu: int, sign: int) -> np.ndarray:
-    """Level-2 block index B + sign*mu (periodic) for an array of block indices."""
+    """Level-2 block index B + sign*mu (periodic) for an array of block indices (the block a
+    leg of step 4 reaches)."""
     X2, Y2, Z2, T2 = g.L2
     c = [idx % X2, (idx // X2) % Y2, (idx // (X2 * Y2)) % Z2, idx // (X2 * Y2 * Z2)]
     c[mu] = (c[mu] + sign) % g.L2[mu]
@@ -213,7 +220,7 @@ def level2_neighbour(idx: np.ndarray, g: CoarseGeometry, mu: int, sign: int) -> 
 
 
 def level2_dense(A2: np.ndarray, g: CoarseGeometry) -> np.ndarray:
-    """A2 as a dense (Vc2*n2)^2 matrix (legs reaching the same block add up)."""
+    """A2 of step 4 as a dense (Vc2*n2)^2 matrix (legs reaching the same block add up)."""
     Vc2, _, n2, _ = A2.shape
     D = np.zeros((Vc2 * n2, Vc2 * n2), dtype=np.complex128)
     for B in range(Vc2):
@@ -226,7 +233,7 @@ def level2_dense(A2: np.ndarray, g: CoarseGeometry) -> np.ndarray:
 
 
 def apply_A2(A2: np.ndarray, g: CoarseGeometry, c2: np.ndarray) -> np.ndarray:
-    """The 9-point level-2 stencil on (Vc2, n2) vectors."""
+    """The 9-point level-2 stencil (A2 of step 4) on (Vc2, n2) vectors."""
     idx = np.arange(g.Vc2)
     y = np.einsum("bjk,bk->bj", A2[:, 0], c2)
     for mu in range(4):

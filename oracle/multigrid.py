@@ -102,7 +102,8 @@ class Geometry:
 
 # ----------------------------------------------------------- block reshapes
 def to_blocks(g: Geometry, psi: np.ndarray) -> np.ndarray:
-    """Fine field(s) (..., Lt,Lz,Ly,Lx,Ls,4,3) -> (..., Vc, K)."""
+    """Fine field(s) (..., Lt,Lz,Ly,Lx,Ls,4,3) -> (..., Vc, K): the block restriction of Eq. 4.1
+    laid out per block (step 3 of the header)."""
     lead = psi.shape[:-7]
     bx, by, bz, bt = g.block
     Xc, Yc, Zc, Tc = g.Lc
@@ -126,7 +127,8 @@ def from_blocks(g: Geometry, blk: np.ndarray) -> np.ndarray:
 
 
 def crossing_mask(g: Geometry, mu: int, sign: int) -> np.ndarray:
-    """Sites x (4d, shape (Lt,Lz,Ly,Lx)) whose neighbour x + sign*mu lies in another block."""
+    """Sites x (4d, shape (Lt,Lz,Ly,Lx)) whose neighbour x + sign*mu lies in another block
+    (the hops that connect neighbouring blocks, the sparsity noted after Eq. 4.6)."""
     Lx, Ly, Lz, Lt = g.L
     coords = np.indices((Lt, Lz, Ly, Lx))        # t, z, y, x
     c = coords[3 - mu]
@@ -136,14 +138,16 @@ def crossing_mask(g: Geometry, mu: int, sign: int) -> np.ndarray:
 
 # ------------------------------------------------------------------ subspace
 def smooth_noise(U, x0, M5, mf, bc_t=1, iters: int = 10):
-    """Inverse-iteration-like smoothing: ``iters`` CR steps on H x = 0 from x0, normalised."""
+    """Inverse-iteration-like smoothing (Section 4, option i; step 1 of the header):
+    ``iters`` CR steps on H x = 0 from x0, normalised."""
     H = lambda v: dwf.apply_H(U, v, M5, mf, bc_t)
     x, _ = cr(H, np.zeros_like(x0), x0=x0, fixed_iters=iters)
     return x / np.sqrt(dwf.norm2(x))
 
 
 def chiral_split(vs: np.ndarray) -> np.ndarray:
-    """(h, fine...) -> (2h, fine...): [P_+ v_0..P_+ v_{h-1}, P_- v_0..P_- v_{h-1}],
+    """Chiral split of Section 4 (step 2 of the header).
+    (h, fine...) -> (2h, fine...): [P_+ v_0..P_+ v_{h-1}, P_- v_0..P_- v_{h-1}],
     P_pm = (1 pm Gamma5)/2 with Gamma5 = gamma5 R5."""
     g = dwf.gamma5_r5(vs)
     plus = 0.5 * (vs + g)
@@ -152,7 +156,8 @@ def chiral_split(vs: np.ndarray) -> np.ndarray:
 
 
 def block_orthonormalise(Phi: np.ndarray, rank_tol: float = 1e-12) -> np.ndarray:
-    """Modified Gram-Schmidt (twice) inside every block, order k = 0..nvec-1.
+    """Block orthonormalisation so that P_S of Eq. 4.3 is a projector (step 4 of the header,
+    a reading): modified Gram-Schmidt (twice) inside every block, order k = 0..nvec-1.
 
     Phi: (nvec, Vc, K).  Returns a new array whose vectors are orthonormal in
     each block.  Raises RankDeficient when a vector has nothing left.
@@ -194,7 +199,8 @@ def build_subspace(U, noise, geom: Geometry, M5, mf, bc_t=1, smooth_iters: int =
 
 
 def basis_from_vectors(geom: Geometry, vectors: np.ndarray) -> Subspace:
-    """Subspace from given full fine vectors (already split), block-orthonormalised."""
+    """Subspace from given full fine vectors (already split), block-orthonormalised
+    (steps 3-4 of the header: Eq. 4.1, Eq. 4.3)."""
     return Subspace(geom, block_orthonormalise(to_blocks(geom, vectors)))
 
 
@@ -206,7 +212,8 @@ def restrict(sub: Subspace, v: np.ndarray) -> np.ndarray:
 
 
 def prolong(sub: Subspace, c: np.ndarray) -> np.ndarray:
-    """P c: v = sum_{a,j} c[a, j] phi_j^a."""
+    """P c: v = sum_{a,j} c[a, j] phi_j^a (Eq. 4.3: the basis of P_S, from coarse coordinates
+    back to the fine field)."""
     vb = np.einsum("jak,...aj->...ak", sub.Phi, c)
     return from_blocks(sub.geom, vb)
 
@@ -244,14 +251,16 @@ def coarse_op(U, sub: Subspace, M5, mf, bc_t=1) -> np.ndarray:
 
 
 def coarse_neighbour(c: np.ndarray, g: Geometry, mu: int, sign: int) -> np.ndarray:
-    """c(a + sign*mu) on the periodic coarse lattice; c is (Vc, nvec)."""
+    """c(a + sign*mu) on the periodic coarse lattice; c is (Vc, nvec) (the coarse neighbour
+    a leg of Eq. 4.5 reaches)."""
     cs = c.reshape(g.coarse_shape() + c.shape[1:])
     ax = 3 - mu
     return np.roll(cs, -sign, axis=ax).reshape(c.shape)
 
 
 def coarse_apply(A: np.ndarray, g: Geometry, c: np.ndarray) -> np.ndarray:
-    """9-point coarse stencil: y[a] = sum_d A[a, d] c[a + d]."""
+    """9-point coarse stencil: y[a] = sum_d A[a, d] c[a + d] (A of Eq. 4.5 with the sparsity
+    noted after Eq. 4.6)."""
     y = np.einsum("ajk,ak->aj", A[:, 0], c)
     for mu in range(4):
         for s in (+1, -1):
@@ -260,7 +269,7 @@ def coarse_apply(A: np.ndarray, g: Geometry, c: np.ndarray) -> np.ndarray:
 
 
 def coarse_dense(A: np.ndarray, g: Geometry) -> np.ndarray:
-    """The coarse operator as a dense (Vc*nvec)^2 matrix (legs that alias are summed)."""
+    """The coarse operator of Eq. 4.5 as a dense (Vc*nvec)^2 matrix (legs that alias are summed)."""
     Vc, _, nvec, _ = A.shape
     D = np.zeros((Vc * nvec, Vc * nvec), dtype=np.complex128)
     idx = np.arange(Vc)
@@ -294,7 +303,8 @@ class HDCRParams:
 
 
 def smoother(U, r, p: HDCRParams):
-    """S r: a fixed number of CR steps on H z = r from z = 0."""
+    """S r: a fixed number of CR steps on H z = r from z = 0 (the CR smoother read in step 7
+    of the header; Section 4 uses the Chebyshev one below)."""
     H = lambda v: dwf.apply_H(U, v, p.M5, p.mf, p.bc_t)
     z, _ = cr(H, r, fixed_iters=p.smoother_steps)
     return z

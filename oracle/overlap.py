@@ -32,7 +32,8 @@ from . import dwf
 
 
 def couplings(beta) -> np.ndarray:
-    """The N - 1 off-diagonal scalars for N = len(beta) + 1 components."""
+    """The N - 1 off-diagonal scalars of the Section 3 continued-fraction matrix for
+    N = len(beta) + 1 components."""
     b = np.asarray(beta, dtype=float)
     n = len(b)
     c = np.empty(n)
@@ -43,7 +44,8 @@ def couplings(beta) -> np.ndarray:
 
 
 def diag_scales(beta) -> np.ndarray:
-    """The factor of H on each diagonal block: (-1)^i, and beta_0 on the last."""
+    """The factor of H on each diagonal block of the Section 3 continued-fraction matrix:
+    (-1)^i, and beta_0 on the last."""
     n = len(beta) + 1
     s = np.array([(-1.0) ** i for i in range(n)])
     s[-1] = beta[0]
@@ -51,12 +53,12 @@ def diag_scales(beta) -> np.ndarray:
 
 
 def apply_HW(U, psi, M5: float, bc_t: int = 1) -> np.ndarray:
-    """H_W = gamma5 D_W on every component."""
+    """H_W = gamma5 D_W on every component (the Hermitian Wilson kernel of Section 3)."""
     return dwf.spin_mul(dwf.GAMMA5, dwf.wilson(U, psi, M5, bc_t))
 
 
 def apply_cf(U, psi, M5: float, beta, R: float, bc_t: int = 1) -> np.ndarray:
-    """The continued-fraction operator on an N-component field (N = len(beta) + 1)."""
+    """The continued-fraction operator of Section 3 on an N-component field (N = len(beta) + 1)."""
     n = psi.shape[-3]
     if n != len(beta) + 1:
         raise ValueError("the field must have len(beta) + 1 components")
@@ -72,7 +74,7 @@ def apply_cf(U, psi, M5: float, beta, R: float, bc_t: int = 1) -> np.ndarray:
 
 
 def schur_last(hw_eigvals, beta, R, g5, V):
-    """The Schur complement on the last component from the continued fraction of
+    """The Schur complement of the Section 3 matrix on the last component from the continued fraction of
     the eigenvalues of H (V its eigenvectors as columns, g5 gamma5 as a matrix in
     the same basis as V's rows): R g5 + V diag(f(lambda)) V^dag."""
     c = couplings(beta)
@@ -87,7 +89,7 @@ def schur_last(hw_eigvals, beta, R, g5, V):
 
 # ------------------------------------------------ the two-level method on it
 def apply_cf_hop(U, psi, mu: int, sign: int, beta, bc_t: int = 1) -> np.ndarray:
-    """The part of the continued-fraction operator made of the single 4d hop reading
+    """The part of the Section 3 continued-fraction operator made of the single 4d hop reading
     psi(x + sign*mu): component i gets (-1)^i (beta_0 on the last) times
     gamma5 (-1/2) hop(mu, sign) of its own component (the couplings and R gamma5 are
     site-local and belong to no hop)."""

@@ -36,30 +36,33 @@ from . import dwf
 
 
 def parity_mask(L) -> np.ndarray:
-    """Boolean (Lt, Lz, Ly, Lx) array: True on odd 4d sites (x + y + z + t odd)."""
+    """Boolean (Lt, Lz, Ly, Lx) array: True on odd 4d sites (x + y + z + t odd): the site
+    colouring of the red-black CGNE of Section 5, as the header reads it."""
     Lx, Ly, Lz, Lt = L
     t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly), np.arange(Lx), indexing="ij")
     return ((x + y + z + t) % 2) == 1
 
 
 def on_parity(psi: np.ndarray, odd: np.ndarray, parity: int) -> np.ndarray:
-    """psi with the sites of the other parity set to zero."""
+    """psi with the sites of the other parity set to zero (the red-black split of the header)."""
     keep = odd if parity == 1 else ~odd
     return psi * keep[..., None, None, None]
 
 
 def m5_apply(psi: np.ndarray, M5: float, mf: float) -> np.ndarray:
-    """M5 psi = (4 - M5) psi + D_5 psi (site-local)."""
+    """M5 psi = (4 - M5) psi + D_5 psi (site-local; the diagonal block of the red-black
+    decomposition in the header)."""
     return (4.0 - M5) * psi + dwf.d5(psi, mf)
 
 
 def dhop_apply(U, psi: np.ndarray, M5: float, bc_t: int = 1) -> np.ndarray:
-    """The 4d hopping part of D_dwf: D_W psi - (4 - M5) psi."""
+    """The 4d hopping part of D_dwf: D_W psi - (4 - M5) psi (the off-diagonal blocks D_eo,
+    D_oe of the red-black decomposition in the header)."""
     return dwf.wilson(U, psi, M5, bc_t) - (4.0 - M5) * psi
 
 
 def m5_matrix(Ls: int, M5: float, mf: float) -> np.ndarray:
-    """(4, Ls, Ls): per spin, the matrix of M5 over the fifth coordinate."""
+    """(4, Ls, Ls): per spin, the matrix of M5 over the fifth coordinate (for M5^{-1}, see the header)."""
     out = np.zeros((4, Ls, Ls), dtype=np.complex128)
     for s in range(Ls):
         e = np.zeros((1, 1, 1, 1, Ls, 4, 3), dtype=np.complex128)
@@ -70,7 +73,7 @@ def m5_matrix(Ls: int, M5: float, mf: float) -> np.ndarray:
 
 
 def m5_inverse(psi: np.ndarray, M5: float, mf: float) -> np.ndarray:
-    """M5^{-1} psi with the inverted Ls x Ls matrices (per spin)."""
+    """M5^{-1} psi with the inverted Ls x Ls matrices (per spin), as the header reads it."""
     Ls = psi.shape[-3]
     Minv = np.linalg.inv(m5_matrix(Ls, M5, mf))  # (4, Ls, Ls)
     # out[..., s, sp, c] = sum_s' Minv[sp, s, s'] psi[..., s', sp, c]
@@ -78,7 +81,8 @@ def m5_inverse(psi: np.ndarray, M5: float, mf: float) -> np.ndarray:
 
 
 def schur_apply(U, v: np.ndarray, odd: np.ndarray, M5: float, mf: float, bc_t: int = 1) -> np.ndarray:
-    """S v = M5 v - D_oe M5^{-1} D_eo v on the odd sites (v supported on odd sites)."""
+    """Schur complement of the red-black reading in the header: S v = M5 v - D_oe M5^{-1} D_eo v
+    on the odd sites (v supported on odd sites)."""
     a = on_parity(dhop_apply(U, v, M5, bc_t), odd, 0)
     b = m5_inverse(a, M5, mf)
     c = on_parity(dhop_apply(U, b, M5, bc_t), odd, 1)
@@ -86,13 +90,14 @@ def schur_apply(U, v: np.ndarray, odd: np.ndarray, M5: float, mf: float, bc_t: i
 
 
 def schur_dag_apply(U, v, odd, M5, mf, bc_t=1):
-    """S^dag v = Gamma5 S Gamma5 v."""
+    """S^dag v = Gamma5 S Gamma5 v (the Gamma5-hermiticity of the Section 3 operator, which S inherits)."""
     return dwf.gamma5_r5(schur_apply(U, dwf.gamma5_r5(v), odd, M5, mf, bc_t))
 
 
 def cgne_rb_solve(U, b: np.ndarray, M5: float, mf: float, bc_t: int = 1, tol: float = 1e-10,
                   maxiter: int = 100000):
-    """H x = b by red-black CGNE.  Returns (x, iterations, |b - H x| / |b|)."""
+    """H x = b by red-black CGNE, the comparison solver of Section 5 (Table 1), in the
+    reading of the header.  Returns (x, iterations, |b - H x| / |b|)."""
     L = (U.shape[4], U.shape[3], U.shape[2], U.shape[1])
     odd = parity_mask(L)
     eta = dwf.gamma5_r5(b)  # D x = Gamma5 b
